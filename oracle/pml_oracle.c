@@ -1,0 +1,469 @@
+/*
+ * Plain FP64 CPU oracle for the reflectionless discrete PML (Chern, arXiv 1804.01390).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference legs may load this code.  It shares no source with the
+ * CUDA library (paper_1804_01390_gb300/csrc) and the library never calls it.
+ *
+ * Everything here is written to be checked against the paper by eye:
+ *   - semi-discrete operator A of eq:DiscretePML (Sec. 1.1.2, Eq. 3a-3c), evaluated
+ *     vertex by vertex with periodic index wrap (the paper truncates the layer with a
+ *     periodic box, Sec. 1.1.3);
+ *   - classic four-stage Runge-Kutta (Sec. 1.1.3 names RK4), stage by stage;
+ *   - the spring-mass energy eq:Energy (Sec. 1.1.5);
+ *   - the discrete adjoint of one RK4 step (reverse of the stage graph, with the
+ *     transpose of A written out from the entries of A).
+ * Compiled with -O2 -ffp-contract=off so every product and sum is rounded once, in
+ * source order.
+ *
+ * Conventions (readings of the paper, listed in the design doc):
+ *   - axis a has T[a] vertices 0..T[a]-1, periodic; the physical vertices are
+ *     w..w+N-1 and the layer vertices the other 2w;
+ *   - sigma_a[e] is edge-centred: it belongs to the edge (e, e+1 mod T) - this is the
+ *     placement of s_j in eq:VertexPositions and of sigma(j) in eq:IntroSolution;
+ *   - Phi_a is supported where sigma_a[i_a] != 0 and Psi_a where sigma_a[i_a - 1] != 0
+ *     (Sec. 1.1.2, the support statement after Eq. 3); elsewhere they are held at 0.
+ *     Outside that support they only ever appear multiplied by a zero sigma.
+ *
+ * State layout: one contiguous array of nf = 2 + 2*ndim fields of n = T0*T1*T2
+ * doubles: [U, V, Phi_0, Psi_0, Phi_1, Psi_1, Phi_2, Psi_2]; vertex (x, y, z) sits at
+ * flat index x + T0*(y + T1*z).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    int ndim;
+    int64_t T[3];
+    double h;
+    const double *sig[3];
+} orc_grid;
+
+typedef struct {
+    int ns;
+    const int64_t *idx;  /* flat vertex index of each source */
+    const double *amp;   /* amplitude a_s */
+    double f_peak;       /* Ricker peak frequency (1/time) */
+    double t_delay;      /* Ricker centre time */
+} orc_src;
+
+static void grid_from_args(orc_grid *g, int ndim, const int64_t *T, double h, const double *sig_concat)
+{
+    int a;
+    g->ndim = ndim;
+    g->h = h;
+    for (a = 0; a < 3; a++) g->T[a] = (a < ndim) ? T[a] : 1;
+    {
+        const double *p = sig_concat;
+        for (a = 0; a < 3; a++) {
+            g->sig[a] = (a < ndim) ? p : NULL;
+            if (a < ndim) p += g->T[a];
+        }
+    }
+}
+
+static int64_t grid_n(const orc_grid *g) { return g->T[0] * g->T[1] * g->T[2]; }
+
+static void to_coords(const orc_grid *g, int64_t i, int64_t c[3])
+{
+    c[0] = i % g->T[0];
+    c[1] = (i / g->T[0]) % g->T[1];
+    c[2] = i / (g->T[0] * g->T[1]);
+}
+
+static int64_t to_flat(const orc_grid *g, const int64_t c[3])
+{
+    return c[0] + g->T[0] * (c[1] + g->T[1] * c[2]);
+}
+
+/* flat index of the vertex c + s*e_a, wrapping periodically along axis a */
+static int64_t shifted(const orc_grid *g, const int64_t c[3], int a, int s)
+{
+    int64_t d[3];
+    d[0] = c[0]; d[1] = c[1]; d[2] = c[2];
+    d[a] = ((d[a] + s) % g->T[a] + g->T[a]) % g->T[a];
+    return to_flat(g, d);
+}
+
+/* Ricker time function g(t) = (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2). */
+double orc_ricker(double t, double f_peak, double t_delay)
+{
+    double a = ORC_PI * ORC_PI * f_peak * f_peak * (t - t_delay) * (t - t_delay);
+    return (1.0 - 2.0 * a) * exp(-a);
+}
+
+/*
+ * Damping profile along one axis (edge-centred, length T = N + 2w).
+ * d_e = max(a-1-e, e-b, 0) with a = w, b = w+N-1 is the depth of edge e in the
+ * layer (0 on the physical edges and on the two interface edges, w on the wrap edge).
+ *   kind 0: constant  sigma_max * [d_e > 0]               (paper Fig. HalfSpaceGauss)
+ *   kind 1: power law sigma_max * (d_e / w)^order        (quadratic ramp: order 2)
+ *   kind 2: random    sigma_max * u_e * [d_e > 0], u_e = draws[e] in [0,1)
+ *                                                        (paper Fig. HalfSpaceRand)
+ * Returns 0, or -1 on bad arguments.
+ */
+int orc_sigma_profile(int64_t N, int64_t w, int kind, double sigma_max, double order,
+                      const double *draws, double *out)
+{
+    int64_t T = N + 2 * w, e;
+    int64_t a = w, b = w + N - 1;
+    if (N < 1 || w < 0) return -1;
+    for (e = 0; e < T; e++) {
+        int64_t d = 0;
+        if (a - 1 - e > d) d = a - 1 - e;
+        if (e - b > d) d = e - b;
+        if (d == 0) { out[e] = 0.0; continue; }
+        if (kind == 0) out[e] = sigma_max;
+        else if (kind == 1) out[e] = sigma_max * pow((double)d / (double)w, order);
+        else if (kind == 2) out[e] = sigma_max * draws[e];
+        else return -1;
+    }
+    return 0;
+}
+
+/*
+ * Integer layout tables along one axis of length T (bit-exact reference for the
+ * library's own tables):
+ *   phi_active[i] = sigma[i] != 0              (support of Phi, Sec. 1.1.2)
+ *   psi_active[i] = sigma[i-1 mod T] != 0      (support of Psi)
+ *   interior[i]   = 1 when the damping on the four edges i-2, i-1, i, i+1 is zero,
+ *                   i.e. no PML term enters the V equation at i-1, i or i+1, and i
+ *                   belongs to the contiguous run of such vertices that contains
+ *                   the vertex `centre`.  On such vertices one RK4 step of Eq. 3
+ *                   reduces exactly to one RK4 step of eq:DiscreteWaveEquation.
+ */
+void orc_layout_axis(const double *sig, int64_t T, int64_t centre,
+                     uint8_t *phi_active, uint8_t *psi_active, uint8_t *interior)
+{
+    int64_t i, k;
+    uint8_t *free4 = (uint8_t *)malloc((size_t)T);
+    for (i = 0; i < T; i++) {
+        phi_active[i] = (uint8_t)(sig[i] != 0.0);
+        psi_active[i] = (uint8_t)(sig[(i - 1 + T) % T] != 0.0);
+        interior[i] = 0;
+    }
+    for (i = 0; i < T; i++) {
+        int ok = 1;
+        for (k = -2; k <= 1; k++)
+            if (sig[((i + k) % T + T) % T] != 0.0) ok = 0;
+        free4[i] = (uint8_t)ok;
+    }
+    if (free4[centre]) {
+        int64_t lo = centre, hi = centre, steps = 0;
+        while (steps < T - 1 && free4[(lo - 1 + T) % T]) { lo--; steps++; }
+        while (steps < T - 1 && free4[(hi + 1) % T]) { hi++; steps++; }
+        for (i = lo; i <= hi; i++) interior[(i % T + T) % T] = 1;
+    }
+    free(free4);
+}
+
+/*
+ * out = A y + b(t): the right-hand side of eq:DiscretePML (Eq. 3a-3c) in first-order
+ * form with V = dU/dt:
+ *   dU/dt   = V
+ *   dV/dt   = sum_a (U(i+e_a) - 2U(i) + U(i-e_a))/h^2
+ *           + sum_a (sigma_a[i_a] Psi_a(i+e_a) - sigma_a[i_a-1] Phi_a(i-e_a))/h   (+ sources)
+ *   dPhi_a/dt = -1/2 (sigma_a[i_a-1] Phi_a(i-e_a) + sigma_a[i_a] Phi_a(i))
+ *               - (U(i+e_a) - U(i-e_a))/(2h)        where sigma_a[i_a]   != 0, else 0
+ *   dPsi_a/dt = -1/2 (sigma_a[i_a-1] Psi_a(i) + sigma_a[i_a] Psi_a(i+e_a))
+ *               - (U(i+e_a) - U(i-e_a))/(2h)        where sigma_a[i_a-1] != 0, else 0
+ * Sources add amp_s * g(t) to dV/dt at their vertex.
+ */
+static void rhs(const orc_grid *g, const double *y, double *out, const orc_src *src, double t)
+{
+    const int64_t n = grid_n(g);
+    const double h = g->h;
+    const double *U = y, *V = y + n;
+    double *oU = out, *oV = out + n;
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; i++) {
+        int64_t c[3];
+        int a;
+        double lap = 0.0, pml = 0.0;
+        to_coords(g, i, c);
+        oU[i] = V[i];
+        for (a = 0; a < g->ndim; a++) {
+            int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
+            lap += (U[ip] - 2.0 * U[i] + U[im]) / (h * h);
+        }
+        for (a = 0; a < g->ndim; a++) {
+            const double *Phi = y + (2 + 2 * a) * n, *Psi = y + (3 + 2 * a) * n;
+            double *oPhi = out + (2 + 2 * a) * n, *oPsi = out + (3 + 2 * a) * n;
+            const int64_t Ta = g->T[a];
+            const double s_i = g->sig[a][c[a]];
+            const double s_im = g->sig[a][(c[a] - 1 + Ta) % Ta];
+            int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
+            double dU = (U[ip] - U[im]) / (2.0 * h);
+            pml += (s_i * Psi[ip] - s_im * Phi[im]) / h;
+            oPhi[i] = (s_i != 0.0) ? -0.5 * (s_im * Phi[im] + s_i * Phi[i]) - dU : 0.0;
+            oPsi[i] = (s_im != 0.0) ? -0.5 * (s_im * Psi[i] + s_i * Psi[ip]) - dU : 0.0;
+        }
+        oV[i] = lap + pml;
+    }
+    if (src) {
+        int s;
+        for (s = 0; s < src->ns; s++)
+            oV[src->idx[s]] += src->amp[s] * orc_ricker(t, src->f_peak, src->t_delay);
+    }
+}
+
+/* Public single evaluation of A y (+ b(t) when src_ns > 0). */
+void orc_rhs(int ndim, const int64_t *T, double h, const double *sig, const double *y, double *out,
+             int src_ns, const int64_t *src_idx, const double *src_amp, double f_peak, double t_delay,
+             double t)
+{
+    orc_grid g;
+    orc_src s;
+    grid_from_args(&g, ndim, T, h, sig);
+    s.ns = src_ns; s.idx = src_idx; s.amp = src_amp; s.f_peak = f_peak; s.t_delay = t_delay;
+    rhs(&g, y, out, src_ns > 0 ? &s : NULL, t);
+}
+
+/*
+ * nsteps classic RK4 steps of dy/dt = A y + b(t) (Sec. 1.1.3), starting at step index
+ * step0 (time t = step0*dt).  Butcher tableau c = (0, 1/2, 1/2, 1),
+ * b = (1/6, 1/3, 1/3, 1/6).  When nr > 0, trace[k*nr + r] receives U at receiver r
+ * after step k+1.  Returns 0, or -1 when scratch cannot be allocated.
+ */
+int orc_rk4(int ndim, const int64_t *T, double h, const double *sig, double *y, int64_t nsteps,
+            double dt, int64_t step0, int src_ns, const int64_t *src_idx, const double *src_amp,
+            double f_peak, double t_delay, int nr, const int64_t *rec_idx, double *trace)
+{
+    orc_grid g;
+    orc_src s;
+    int64_t n, len, k, j;
+    double *k1, *k2, *k3, *k4, *Y;
+    grid_from_args(&g, ndim, T, h, sig);
+    s.ns = src_ns; s.idx = src_idx; s.amp = src_amp; s.f_peak = f_peak; s.t_delay = t_delay;
+    n = grid_n(&g);
+    len = (2 + 2 * (int64_t)ndim) * n;
+    k1 = (double *)malloc(sizeof(double) * (size_t)len);
+    k2 = (double *)malloc(sizeof(double) * (size_t)len);
+    k3 = (double *)malloc(sizeof(double) * (size_t)len);
+    k4 = (double *)malloc(sizeof(double) * (size_t)len);
+    Y = (double *)malloc(sizeof(double) * (size_t)len);
+    if (!k1 || !k2 || !k3 || !k4 || !Y) {
+        free(k1); free(k2); free(k3); free(k4); free(Y);
+        return -1;
+    }
+    for (k = 0; k < nsteps; k++) {
+        const double t = (double)(step0 + k) * dt;
+        const orc_src *sp = src_ns > 0 ? &s : NULL;
+        rhs(&g, y, k1, sp, t);
+#pragma omp parallel for schedule(static)
+        for (j = 0; j < len; j++) Y[j] = y[j] + 0.5 * dt * k1[j];
+        rhs(&g, Y, k2, sp, t + 0.5 * dt);
+#pragma omp parallel for schedule(static)
+        for (j = 0; j < len; j++) Y[j] = y[j] + 0.5 * dt * k2[j];
+        rhs(&g, Y, k3, sp, t + 0.5 * dt);
+#pragma omp parallel for schedule(static)
+        for (j = 0; j < len; j++) Y[j] = y[j] + dt * k3[j];
+        rhs(&g, Y, k4, sp, t + dt);
+#pragma omp parallel for schedule(static)
+        for (j = 0; j < len; j++)
+            y[j] = y[j] + dt / 6.0 * (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]);
+        if (nr > 0) {
+            int r;
+            for (r = 0; r < nr; r++) trace[k * nr + r] = y[rec_idx[r]];
+        }
+    }
+    free(k1); free(k2); free(k3); free(k4); free(Y);
+    return 0;
+}
+
+/*
+ * Spring-mass energy eq:Energy (Sec. 1.1.5):
+ *   E = 1/2 sum_i V(i)^2 + 1/2 sum_i sum_a ((U(i+e_a) - U(i))/h)^2
+ * with i over the box lo[a] <= i_a <= hi[a] (inclusive; the physical window).  The
+ * forward difference at the last window vertex reads the next vertex, which may lie
+ * in the layer (or wrap around when the window is the whole periodic box).
+ */
+double orc_energy(int ndim, const int64_t *T, double h, const double *y, const int64_t *lo,
+                  const int64_t *hi)
+{
+    orc_grid g;
+    int64_t n, i;
+    double kin = 0.0, ela = 0.0;
+    g.ndim = ndim; g.h = h;
+    g.T[0] = T[0]; g.T[1] = ndim > 1 ? T[1] : 1; g.T[2] = ndim > 2 ? T[2] : 1;
+    g.sig[0] = g.sig[1] = g.sig[2] = NULL;
+    n = grid_n(&g);
+    for (i = 0; i < n; i++) {
+        int64_t c[3];
+        int a, inside = 1;
+        to_coords(&g, i, c);
+        for (a = 0; a < ndim; a++)
+            if (c[a] < lo[a] || c[a] > hi[a]) inside = 0;
+        if (!inside) continue;
+        kin += y[n + i] * y[n + i];
+        for (a = 0; a < ndim; a++) {
+            double d = (y[shifted(&g, c, a, +1)] - y[i]) / h;
+            ela += d * d;
+        }
+    }
+    return 0.5 * kin + 0.5 * ela;
+}
+
+/*
+ * Norms of field U over the inclusive window lo..hi: out[0] = max |U|,
+ * out[1] = sqrt(sum U^2), out[2] = sqrt(sum (U - ref)^2) (0 when ref is NULL).
+ */
+void orc_norms(int ndim, const int64_t *T, const double *U, const double *ref, const int64_t *lo,
+               const int64_t *hi, double *out)
+{
+    orc_grid g;
+    int64_t n, i;
+    double mx = 0.0, s2 = 0.0, d2 = 0.0;
+    g.ndim = ndim; g.h = 1.0;
+    g.T[0] = T[0]; g.T[1] = ndim > 1 ? T[1] : 1; g.T[2] = ndim > 2 ? T[2] : 1;
+    n = grid_n(&g);
+    for (i = 0; i < n; i++) {
+        int64_t c[3];
+        int a, inside = 1;
+        to_coords(&g, i, c);
+        for (a = 0; a < ndim; a++)
+            if (c[a] < lo[a] || c[a] > hi[a]) inside = 0;
+        if (!inside) continue;
+        if (fabs(U[i]) > mx) mx = fabs(U[i]);
+        s2 += U[i] * U[i];
+        if (ref) d2 += (U[i] - ref[i]) * (U[i] - ref[i]);
+    }
+    out[0] = mx; out[1] = sqrt(s2); out[2] = sqrt(d2);
+}
+
+/*
+ * out = A^T ybar: the transpose of the operator in rhs(), collected entry by entry
+ * (every coefficient A[r][c] of rhs() contributes A[r][c]*ybar[r] to out[c]):
+ *   (A^T ybar)_U(i)   = sum_a (Vb(i+e) - 2Vb(i) + Vb(i-e))/h^2
+ *                      + sum_a (Phib_a(i+e) - Phib_a(i-e))/(2h) + (Psib_a(i+e) - Psib_a(i-e))/(2h)
+ *   (A^T ybar)_V(i)   = Ub(i)
+ *   (A^T ybar)_Phi(i) = -sigma[i] Vb(i+e)/h - 1/2 sigma[i] (Phib(i+e) + Phib(i))
+ *   (A^T ybar)_Psi(i) = +sigma[i-1] Vb(i-e)/h - 1/2 sigma[i-1] (Psib(i) + Psib(i-e))
+ * Phib/Psib are first restricted to the supports (the rows of A outside the support
+ * are zero), so the U row only sees supported entries.
+ */
+static void rhs_transpose(const orc_grid *g, const double *yb, double *out)
+{
+    const int64_t n = grid_n(g);
+    const double h = g->h;
+    const double *Ub = yb, *Vb = yb + n;
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; i++) {
+        int64_t c[3];
+        int a;
+        double acc = 0.0;
+        to_coords(g, i, c);
+        out[n + i] = Ub[i];
+        for (a = 0; a < g->ndim; a++) {
+            int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
+            acc += (Vb[ip] - 2.0 * Vb[i] + Vb[im]) / (h * h);
+        }
+        for (a = 0; a < g->ndim; a++) {
+            const double *Phib = yb + (2 + 2 * a) * n, *Psib = yb + (3 + 2 * a) * n;
+            double *oPhi = out + (2 + 2 * a) * n, *oPsi = out + (3 + 2 * a) * n;
+            const int64_t Ta = g->T[a];
+            const int64_t ia = c[a];
+            const int64_t iap = (ia + 1) % Ta, iam = (ia - 1 + Ta) % Ta, iamm = (ia - 2 + Ta) % Ta;
+            const double s_i = g->sig[a][ia], s_im = g->sig[a][iam];
+            int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
+            /* supported adjoint entries (Phi support: sigma[j] != 0; Psi: sigma[j-1] != 0) */
+            double phib_p = (g->sig[a][iap] != 0.0) ? Phib[ip] : 0.0;
+            double phib_m = (g->sig[a][iam] != 0.0) ? Phib[im] : 0.0;
+            double phib_0 = (s_i != 0.0) ? Phib[i] : 0.0;
+            double psib_p = (s_i != 0.0) ? Psib[ip] : 0.0;        /* support of Psi(i+1): sigma[i] */
+            double psib_m = (g->sig[a][iamm] != 0.0) ? Psib[im] : 0.0; /* Psi(i-1): sigma[i-2] */
+            double psib_0 = (s_im != 0.0) ? Psib[i] : 0.0;
+            acc += (phib_p - phib_m) / (2.0 * h) + (psib_p - psib_m) / (2.0 * h);
+            oPhi[i] = (s_i != 0.0) ? -s_i * Vb[ip] / h - 0.5 * s_i * (phib_p + phib_0) : 0.0;
+            oPsi[i] = (s_im != 0.0) ? s_im * Vb[im] / h - 0.5 * s_im * (psib_0 + psib_m) : 0.0;
+        }
+        out[i] = acc;
+    }
+}
+
+void orc_rhs_transpose(int ndim, const int64_t *T, double h, const double *sig, const double *yb,
+                       double *out)
+{
+    orc_grid g;
+    grid_from_args(&g, ndim, T, h, sig);
+    rhs_transpose(&g, yb, out);
+}
+
+/*
+ * Discrete adjoint of nsteps RK4 steps, run backwards from step index step_end.
+ * For k = 0..nsteps-1 the forward state index is m = step_end - k:
+ *   1. ybar_U(x_r) += residual[k*nr + r]   (dJ/dU_m at the receivers)
+ *   2. reverse the RK4 step m-1 -> m (times t = (m-1)dt, t+dt/2, t+dt):
+ *        kb1 = dt/6 yb, kb2 = dt/3 yb, kb3 = dt/3 yb, kb4 = dt/6 yb
+ *        Y4b = A^T kb4;  yb += Y4b;  kb3 += dt   * Y4b
+ *        Y3b = A^T kb3;  yb += Y3b;  kb2 += dt/2 * Y3b
+ *        Y2b = A^T kb2;  yb += Y2b;  kb1 += dt/2 * Y2b
+ *        Y1b = A^T kb1;  yb += Y1b
+ *      and for each source: grad_amp[s] += g(t) kb1_V + g(t+dt/2) (kb2_V + kb3_V)
+ *                                          + g(t+dt) kb4_V  at x_s.
+ * yb holds dJ/dy_{step_end} on entry and dJ/dy_{step_end - nsteps} on exit.
+ * Returns 0, or -1 when scratch cannot be allocated.
+ */
+int orc_adjoint(int ndim, const int64_t *T, double h, const double *sig, double *yb,
+                int64_t nsteps, double dt, int64_t step_end, int src_ns, const int64_t *src_idx,
+                double f_peak, double t_delay, double *grad_amp, int nr, const int64_t *rec_idx,
+                const double *residual)
+{
+    orc_grid g;
+    int64_t n, len, k, j;
+    double *kb1, *kb2, *kb3, *kb4, *Yb, *yb_out;
+    grid_from_args(&g, ndim, T, h, sig);
+    n = grid_n(&g);
+    len = (2 + 2 * (int64_t)ndim) * n;
+    kb1 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb2 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb3 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb4 = (double *)malloc(sizeof(double) * (size_t)len);
+    Yb = (double *)malloc(sizeof(double) * (size_t)len);
+    yb_out = (double *)malloc(sizeof(double) * (size_t)len);
+    if (!kb1 || !kb2 || !kb3 || !kb4 || !Yb || !yb_out) {
+        free(kb1); free(kb2); free(kb3); free(kb4); free(Yb); free(yb_out);
+        return -1;
+    }
+    for (k = 0; k < nsteps; k++) {
+        const int64_t m = step_end - k;
+        const double t = (double)(m - 1) * dt;
+        if (nr > 0) {
+            int r;
+            for (r = 0; r < nr; r++) yb[rec_idx[r]] += residual[k * nr + r];
+        }
+        for (j = 0; j < len; j++) {
+            kb1[j] = dt / 6.0 * yb[j];
+            kb2[j] = dt / 3.0 * yb[j];
+            kb3[j] = dt / 3.0 * yb[j];
+            kb4[j] = dt / 6.0 * yb[j];
+            yb_out[j] = yb[j];
+        }
+        rhs_transpose(&g, kb4, Yb);
+        for (j = 0; j < len; j++) { yb_out[j] += Yb[j]; kb3[j] += dt * Yb[j]; }
+        rhs_transpose(&g, kb3, Yb);
+        for (j = 0; j < len; j++) { yb_out[j] += Yb[j]; kb2[j] += 0.5 * dt * Yb[j]; }
+        rhs_transpose(&g, kb2, Yb);
+        for (j = 0; j < len; j++) { yb_out[j] += Yb[j]; kb1[j] += 0.5 * dt * Yb[j]; }
+        rhs_transpose(&g, kb1, Yb);
+        for (j = 0; j < len; j++) yb_out[j] += Yb[j];
+        if (src_ns > 0 && grad_amp) {
+            int s;
+            for (s = 0; s < src_ns; s++) {
+                const int64_t v = n + src_idx[s];
+                grad_amp[s] += orc_ricker(t, f_peak, t_delay) * kb1[v]
+                             + orc_ricker(t + 0.5 * dt, f_peak, t_delay) * (kb2[v] + kb3[v])
+                             + orc_ricker(t + dt, f_peak, t_delay) * kb4[v];
+            }
+        }
+        memcpy(yb, yb_out, sizeof(double) * (size_t)len);
+    }
+    free(kb1); free(kb2); free(kb3); free(kb4); free(Yb); free(yb_out);
+    return 0;
+}
