@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the discrete-PML RK4 step (grid-point updates per second).
+
+One "step" = one RK4 step of the whole periodic box (interior + layer) of the 2D
+workload with an 8192^2 physical domain and a 32-cell quadratic layer on every side
+(T = 8256^2 vertices), 16 seeded Gaussian pulses, dt = 0.5 h.  The headline runs the
+FP32 path; FP64 and the adjoint step are reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With --gpus N > 1 launch under torchrun: every rank runs an independent replica of the
+workload on its own GPU (the method has no exchange step on one box), the timed region
+is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s (GPts/s) and % HBM roofline, FP32 vs FP64, fwd and adjoint"
+UNIT = "GPts/s"
+NOMINAL_FP64_TFLOPS = 1.25          # GB300 dense FP64 (nominal, no tensor-core path)
+FP64_FLOP_PER_POINT = 38            # interior kernel: 4 differences (5 flop) + 2 outputs (9 flop)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ------------------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device=None):
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------
+# measurements
+# ------------------------------------------------------------------------------------
+
+def _workload():
+    from paper_1804_01390_gb300 import workloads as wk
+    return wk.cfg2()
+
+
+def timed_steps(solver, steps, warmup, ws, profile=False):
+    """Device time (ms) of `steps` RK4 steps on the solver's stream, after warm-up."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    solver.step(warmup)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    if profile:
+        _lib.pml_profile_enable(solver.ctx, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(solver.stream)
+    solver.step(steps)
+    e1.record(solver.stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = None
+    if profile:
+        prof = _lib.pml_profile_read(solver.ctx)
+        _lib.pml_profile_enable(solver.ctx, 0)
+    return ms, prof
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_1804_01390_gb300 import workloads as wk
+    from paper_1804_01390_gb300.solver import PMLSolver
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = _workload()
+    pts = wl.points
+    u0 = wk.initial_field(wl, dtype=np.float32)
+    K, W = args.steps, args.warmup
+    hbm_peak, peak_kind = _peaks()
+
+    # ---- FP32 headline: inputs resident in HBM ------------------------------------
+    s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev)
+    u_dev = torch.from_numpy(u0).to(dev)
+    s.set_initial(u_dev)
+    clk = ClockSampler(local)
+    clk.start()
+    ms, prof = timed_steps(s, K, W, ws, profile=True)
+    clk.stop()
+    ms_max = max_over_ranks(ms, ws, dev)
+    value = pts * K * ws / (ms_max / 1e3) / 1e9
+    (ms_k, n_k) = prof
+    interior_pts = int(np.prod([n - 2 for n in wl.N]))
+    bytes_per_launch = interior_pts * 4 * 4               # U, V read + written, FP32
+    avg_launch_s = ms_k[0] / max(n_k[0], 1) / 1e3
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    launches = int(n_k.sum())
+    layer_share = float(ms_k[1] / max(ms_k.sum(), 1e-30))
+
+    # ---- FP32 end to end through the C ABI with host buffers ------------------------
+    s.close()
+    del s
+    torch.cuda.synchronize()
+    e2e = None
+    if not args.no_e2e:
+        from paper_1804_01390_gb300 import _lib
+        s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev)
+        u_host = torch.from_numpy(u0).pin_memory()
+        out_host = torch.empty_like(u_host).pin_memory()
+        s.set_initial(u_host)
+        s.step(W)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        _lib.pml_set_initial(s.ctx, u_host.data_ptr(), None, 0)
+        _lib.pml_step(s.ctx, K)
+        _lib.pml_read_field(s.ctx, 0, out_host.data_ptr(), 0)
+        t1 = time.perf_counter()
+        barrier(ws)
+        e_ms = max_over_ranks((t1 - t0) * 1e3, ws, dev)
+        nb = u_host.numel() * 4
+        e2e = {"value": pts * K * ws / (e_ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb / K,
+               "d2h_bytes_per_step": nb / K, "ms": e_ms,
+               "how": "pml_set_initial(host pinned U0) + pml_step(K) + pml_read_field(host U), wall clock"}
+        s.close()
+        del s
+
+    # ---- FP64 ------------------------------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        K64 = max(K // 10, 10)
+        s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=64, device=dev)
+        s.set_initial(torch.from_numpy(u0.astype(np.float64)).to(dev))
+        ms64, prof64 = timed_steps(s, K64, min(W, 3), ws, profile=True)
+        ms64 = max_over_ranks(ms64, ws, dev)
+        v64 = pts * K64 * ws / (ms64 / 1e3) / 1e9
+        m64, n64 = prof64
+        t_int = m64[0] / max(n64[0], 1) / 1e3
+        tflops = interior_pts * FP64_FLOP_PER_POINT / t_int / 1e12
+        fp64 = {"value": v64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
+                "roofline": {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS,
+                             "unit": "TFLOP/s", "frac": tflops / NOMINAL_FP64_TFLOPS,
+                             "peak_kind": "nominal GB300 FP64", "flop_per_point": FP64_FLOP_PER_POINT}}
+        s.close()
+        del s
+
+    # ---- adjoint (FP32) --------------------------------------------------------------
+    adj = None
+    if not args.no_adjoint:
+        import torch as _t
+        s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev, adjoint=True)
+        s.set_initial(_t.from_numpy(u0).to(dev))
+        s.adjoint_reset()
+        from paper_1804_01390_gb300 import _lib
+        Ka = max(K // 2, 10)
+        _lib.pml_adjoint_step(s.ctx, min(W, 3), None, None, None)
+        _t.cuda.synchronize()
+        barrier(ws)
+        e0 = _t.cuda.Event(enable_timing=True)
+        e1 = _t.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        _lib.pml_adjoint_step(s.ctx, Ka, None, None, None)
+        e1.record(s.stream)
+        _t.cuda.synchronize()
+        barrier(ws)
+        msa = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        adj = {"value": pts * Ka * ws / (msa / 1e3) / 1e9, "unit": UNIT, "steps": Ka,
+               "ms_per_step": msa / Ka, "dtype": "f32"}
+        s.close()
+        del s
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2D 8192^2 interior + 32-cell quadratic PML (T = 8256^2), 16 seeded "
+                                   "Gaussian pulses, RK4 dt = 0.5h", "grid": list(wl.T), "pml_width": wl.w,
+                       "l2": "inputs larger than L2 (U and V are 272 MB each; 1.09 GB state read + written "
+                             "per step)", "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_interior2d<float>", "bytes_per_launch": bytes_per_launch,
+                         "avg_launch_ms": avg_launch_s * 1e3, "layer_time_share": layer_share},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ------------------------------------------------------------------------------------
+
+def _oracle_sample(N=1024, w=32):
+    """A bounded sample of the workload: the same layer (w = 32, quadratic, sigma_max 2)
+    around a 1024^2 physical domain, Gaussian pulses from the same recipe."""
+    import oracle
+    from paper_1804_01390_gb300 import workloads as wk
+    wl = wk.cfg2(N=N, w=w, npulses=4)
+    sig = [oracle.sigma_profile(n, w, oracle.KIND_POWER, 2.0, 2.0) for n in wl.N]
+    g = oracle.Grid(wl.T, 1.0, sig)
+    y = g.zeros_state()
+    y[0] = wk.initial_field(wl).reshape(-1)
+    return oracle, g, y, wl
+
+
+def cpu_baseline(seconds=10.0):
+    oracle, g, y, wl = _oracle_sample()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    oracle.rk4(g, y, 1, wl.dt, openmp=True)   # warm-up (page-in, thread pool)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and steps < 1000:
+        y, _ = oracle.rk4(g, y, 1, wl.dt, step0=steps, openmp=True)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": g.n * steps / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d RK4 steps of the FP64 C oracle (OpenMP build) on a %dx%d box: the same "
+                      "32-cell quadratic layer around a 1024^2 domain" % (steps, g.T[0], g.T[1]),
+            "seconds": dt}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    oracle, g, y, wl = _oracle_sample()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    for k in range(args.warmup):
+        y, _ = oracle.rk4(g, y, 1, wl.dt, step0=k, openmp=True)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        y, _ = oracle.rk4(g, y, 1, wl.dt, step0=args.warmup + k, openmp=True)
+    dt = time.perf_counter() - t0
+    value = g.n * args.steps / dt / 1e9
+    sample = ("each step: one RK4 step of the FP64 C oracle (OpenMP build) on a %dx%d box, the same "
+              "32-cell quadratic layer around a 1024^2 domain" % (g.T[0], g.T[1]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "2D 8192^2 interior + 32-cell quadratic PML (T = 8256^2), 16 seeded "
+                                   "Gaussian pulses, RK4 dt = 0.5h", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 2000
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

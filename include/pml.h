@@ -1,0 +1,237 @@
+/*
+ * pml.h -- C ABI of the GB300 (sm_103a) implementation of the reflectionless discrete
+ * perfectly matched layer of A. Chern, "A Reflectionless Discrete Perfectly Matched
+ * Layer" (arXiv 1804.01390).
+ *
+ * What the library computes
+ * -------------------------
+ * The semi-discrete PML system eq:DiscretePML (Sec. 1.1.2, Eq. 3a-3c) on a periodic box
+ * (the paper truncates the layer periodically, Sec. 1.1.3), written in first-order form
+ * with V = dU/dt:
+ *
+ *   dU/dt     = V
+ *   dV/dt     = sum_a (U(i+e_a) - 2U(i) + U(i-e_a)) / h^2
+ *             + sum_a (sigma_a[i_a] Psi_a(i+e_a) - sigma_a[i_a - 1] Phi_a(i-e_a)) / h   + sources
+ *   dPhi_a/dt = -(sigma_a[i_a-1] Phi_a(i-e_a) + sigma_a[i_a] Phi_a(i)) / 2 - (U(i+e_a) - U(i-e_a)) / (2h)
+ *   dPsi_a/dt = -(sigma_a[i_a-1] Psi_a(i) + sigma_a[i_a] Psi_a(i+e_a)) / 2 - (U(i+e_a) - U(i-e_a)) / (2h)
+ *
+ * advanced in time by the classic four-stage Runge-Kutta method (RK4, Sec. 1.1.3).
+ * Phi_a lives where sigma_a[i_a] != 0 and Psi_a where sigma_a[i_a - 1] != 0 (the support
+ * statement after Eq. 3); elsewhere both are identically zero.
+ *
+ * Geometry
+ * --------
+ * Axis a has N[a] physical ("interior") vertices and a layer of w vertices on each side:
+ * T[a] = N[a] + 2w vertices indexed 0..T[a]-1, periodic.  Physical vertices are
+ * w..w+N[a]-1.  sigma_a[e] is edge-centred: it belongs to the edge (e, e+1 mod T[a])
+ * (the vertical gap s_j of eq:VertexPositions; the factors of eq:IntroSolution).  The
+ * depth of edge e in the layer is d_e = max(w-1-e, e-(w+N-1), 0).
+ *
+ * Dense field arrays exchanged through this ABI are row-major [T2][T1][T0] (x fastest),
+ * of the context's precision (float for 32, double for 64).  In 2D T2 = 1.
+ *
+ * Conventions of every call
+ * -------------------------
+ *  - Every call returns a pml_status and never aborts; pml_last_error() gives text.
+ *  - The caller owns every buffer it passes in.  "on_device" = 1 means the pointer is
+ *    device memory of the context's device, 0 means host memory.
+ *  - Work is enqueued on the CUDA stream given at creation.  Calls that return data to
+ *    the host (pml_read_field with a host pointer, pml_norms, pml_sync) synchronise that
+ *    stream; the others return as soon as the work is enqueued.  Errors of enqueued
+ *    kernels are reported by the next synchronising call.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PML_H_
+#define PML_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pml_ctx pml_ctx;
+
+typedef enum {
+    PML_OK = 0,
+    PML_EINVAL = 1,      /* invalid argument                                          */
+    PML_ENOMEM = 2,      /* allocation failed or workspace too small                   */
+    PML_ECUDA = 3,       /* a CUDA runtime/driver call failed                          */
+    PML_ESTATE = 4,      /* call not valid in the context's current state              */
+    PML_EUNSTABLE = 5,   /* dt beyond the RK4 stability limit sqrt(2/d) h              */
+    PML_ENONFINITE = 6,  /* non-finite value found in inputs or in the state           */
+    PML_ETIMEOUT = 7     /* a bounded device-side wait gave up (kernel error flag set) */
+} pml_status;
+
+typedef struct {
+    int ndim;        /* 2 or 3                                                    */
+    int64_t n[3];    /* physical (interior) vertices per axis; n[2] ignored in 2D */
+} pml_grid;
+
+enum {
+    PML_SIGMA_CONSTANT = 0, /* sigma_max * [d_e > 0]             (Fig. HalfSpaceGauss)   */
+    PML_SIGMA_POWER = 1,    /* sigma_max * (d_e / w)^order       (order 2: quadratic ramp) */
+    PML_SIGMA_RANDOM = 2,   /* sigma_max * u_e * [d_e > 0], u_e = user[a][e] in [0,1)
+                               (Fig. HalfSpaceRand)                                       */
+    PML_SIGMA_USER = 3      /* sigma_a[e] = user[a][e] as given; must be >= 0, finite and
+                               zero on the physical edges w-1 .. w+N-1                   */
+};
+
+typedef struct {
+    int kind;                /* PML_SIGMA_*                                    */
+    double sigma_max;        /* in units of 1/h times h, i.e. the paper's sigma */
+    double order;            /* exponent of PML_SIGMA_POWER                     */
+    const double *user[3];   /* host arrays of length T[a] for RANDOM / USER    */
+} pml_sigma_profile;
+
+/* fields of pml_read_field */
+enum { PML_FIELD_U = 0, PML_FIELD_V = 1 };
+#define PML_FIELD_PHI(a) (2 + 2 * (a))
+#define PML_FIELD_PSI(a) (3 + 2 * (a))
+
+/* flags of pml_create */
+enum {
+    PML_FLAG_ADJOINT = 1     /* also allocate the adjoint state (pml_adjoint_*) */
+};
+
+/*
+ * Bytes of device workspace pml_create needs for this problem.  Pass a buffer of at
+ * least that size (256-byte aligned, e.g. a torch uint8 tensor) to pml_create, or pass
+ * NULL there to let the library cudaMalloc (and later cudaFree) it.
+ */
+pml_status pml_workspace_bytes(const pml_grid *grid, int pml_width, int precision, int flags,
+                               size_t *bytes);
+
+/*
+ * Create a solver for eq:DiscretePML on the periodic box N + 2w (Sec. 1.1.3).
+ *   grid       physical vertices per axis (2D or 3D)
+ *   h, dt      grid spacing and RK4 time step; dt must satisfy dt <= sqrt(2/ndim) h, the
+ *              RK4 stability limit of the undamped discrete wave equation (else
+ *              PML_EUNSTABLE)
+ *   pml_width  w >= 0 layer vertices per side (w = 0: plain periodic wave equation)
+ *   profile    damping profile (see PML_SIGMA_*); applied on every axis
+ *   precision  32 (FP32 state, FP32 arithmetic) or 64 (FP64)
+ *   cuda_stream  cudaStream_t the library enqueues on (NULL = legacy default stream)
+ *   workspace, workspace_bytes  caller-owned device buffer (see pml_workspace_bytes) or
+ *              NULL/0 for library-owned memory
+ *   flags      PML_FLAG_*
+ * The state is zero after creation and the step counter is 0.
+ */
+pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width,
+                      const pml_sigma_profile *profile, int precision, void *cuda_stream,
+                      void *workspace, size_t workspace_bytes, int flags, pml_ctx **out);
+
+/*
+ * Set the state: U = u0, V = v0 (NULL -> 0), Phi = Psi = 0, step counter = 0
+ * (the paper's runs start at rest in the layer, Sec. 1.1.3).  u0 / v0 are dense
+ * T-grids of the context's precision.
+ */
+pml_status pml_set_initial(pml_ctx *ctx, const void *u0, const void *v0, int on_device);
+
+/*
+ * Point sources: dV/dt(x_s) += amp[s] * g(t) with the Ricker wavelet
+ * g(t) = (1 - 2 pi^2 f^2 (t - t_delay)^2) exp(-pi^2 f^2 (t - t_delay)^2), evaluated at the
+ * RK4 stage times t_n, t_n + dt/2, t_n + dt (t_n = n dt).  coords: host [ns][ndim]
+ * (x, y[, z]); each source must lie where no layer term reaches it within one step
+ * (the interior run of every axis, see pml_query_layout), else PML_EINVAL.  ns = 0
+ * removes all sources.  Not part of the paper (its runs are source-free).
+ */
+pml_status pml_set_sources(pml_ctx *ctx, int ns, const int64_t *coords, const double *amp,
+                           double f_peak, double t_delay);
+
+/*
+ * Receivers: after every pml_step step k (counted from this call), U at each receiver
+ * is written to trace_buf[k * nr + r] (device, context precision), for k < capacity.
+ * nr = 0 removes the receivers.
+ */
+pml_status pml_set_receivers(pml_ctx *ctx, int nr, const int64_t *coords, void *trace_buf,
+                             int64_t capacity);
+
+/* Advance n RK4 steps (asynchronous). */
+pml_status pml_step(pml_ctx *ctx, int64_t n);
+
+/* Copy field PML_FIELD_* of the current state into a dense T-grid (host or device). */
+pml_status pml_read_field(pml_ctx *ctx, int field, void *dst, int on_device);
+
+/*
+ * FP64 reductions over the physical window w..w+N-1 of every axis (synchronising):
+ *   out[0] = E, the energy eq:Energy (Sec. 1.1.5):
+ *            1/2 sum V^2 + 1/2 sum_i sum_a ((U(i+e_a) - U(i)) / h)^2
+ *   out[1] = max |U|, out[2] = sqrt(sum U^2),
+ *   out[3] = sqrt(sum (U - ref)^2), out[4] = max |U - ref|
+ * ref: NULL, or a device FP64 array of the window shape [N2][N1][N0].
+ */
+pml_status pml_norms(pml_ctx *ctx, const double *ref, double out[5]);
+
+/* Current step counter (number of RK4 steps since pml_set_initial). */
+pml_status pml_get_step(const pml_ctx *ctx, int64_t *step);
+
+/* Wait for all enqueued work and report any device-side error. */
+pml_status pml_sync(pml_ctx *ctx);
+
+/*
+ * Integer layout tables of axis `axis` (host arrays of length T[axis]):
+ *   phi_active[i] = sigma[i] != 0, psi_active[i] = sigma[i-1] != 0 (supports, Sec. 1.1.2)
+ *   interior[i]   = 1 on the run of vertices where sigma vanishes on edges i-2..i+1, the
+ *                   run containing the centre vertex: there one RK4 step of Eq. 3 equals
+ *                   one RK4 step of eq:DiscreteWaveEquation, and the library uses its
+ *                   interior (layer-free) kernel.
+ * Any pointer may be NULL.
+ */
+pml_status pml_query_layout(const pml_ctx *ctx, int axis, uint8_t *phi_active,
+                            uint8_t *psi_active, uint8_t *interior);
+
+/* Edge-centred damping of axis `axis` as used (host, length T[axis], FP64). */
+pml_status pml_query_sigma(const pml_ctx *ctx, int axis, double *sigma);
+
+/*
+ * Discrete adjoint of the RK4 scheme (the transpose of one step is P(dt A)^T =
+ * P(dt A^T), A^T written out from the entries of Eq. 3).  Requires PML_FLAG_ADJOINT.
+ *
+ * pml_adjoint_reset: adjoint state := 0, adjoint clock := current forward step count,
+ *   source-amplitude gradient accumulators := 0.
+ * pml_adjoint_step: for k = 0..n-1, with m = adjoint clock:
+ *     1. dJ/dU_m at the receivers += residual[k * nr + r] (device, context precision,
+ *        [n][nr]; NULL = no injection)
+ *     2. accumulate dJ/da_s of the step m-1 -> m
+ *     3. adjoint state := P(dt A)^T adjoint state;  adjoint clock := m - 1
+ *   For a misfit J = 1/2 sum_{m>=1} sum_r (U_m(x_r) - d_{m,r})^2 the residual row of
+ *   step m is U_m(x_r) - d_{m,r}.  Afterwards, if grad_u is not NULL the U part of the
+ *   adjoint state (dJ/dU at the adjoint clock) is copied to grad_u (device dense T-grid,
+ *   context precision), and if grad_amp is not NULL the accumulated dJ/da (host, FP64,
+ *   [ns]) is copied there (synchronising).
+ */
+pml_status pml_adjoint_reset(pml_ctx *ctx);
+pml_status pml_adjoint_step(pml_ctx *ctx, int64_t n, const void *residual, void *grad_u,
+                            double *grad_amp);
+/* Copy field PML_FIELD_* of the adjoint state into a dense T-grid (host or device). */
+pml_status pml_adjoint_read_field(pml_ctx *ctx, int field, void *dst, int on_device);
+
+/*
+ * Checkpoints: the complete forward state (U, V, Phi_a, Psi_a in the library's padded
+ * layout) plus the step counter.  pml_state_bytes gives the size; dst/src may be host or
+ * device memory.
+ */
+pml_status pml_state_bytes(const pml_ctx *ctx, size_t *bytes);
+pml_status pml_save_state(pml_ctx *ctx, void *dst, int on_device);
+pml_status pml_load_state(pml_ctx *ctx, const void *src, int on_device);
+
+/*
+ * Kernel timing.  With enable = 1 every kernel the context launches is bracketed by CUDA
+ * events recorded on the context's stream (kinds: 0 interior, 1 layer, 2 point kernels
+ * for sources / receivers).  pml_profile_read synchronises, returns the summed
+ * durations in milliseconds and the launch counts per kind, and clears them.
+ */
+pml_status pml_profile_enable(pml_ctx *ctx, int enable);
+pml_status pml_profile_read(pml_ctx *ctx, double ms[3], int64_t launches[3]);
+
+void pml_destroy(pml_ctx *ctx);
+const char *pml_last_error(const pml_ctx *ctx);
+const char *pml_status_string(pml_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PML_H_ */

@@ -1,0 +1,249 @@
+"""ctypes binding of the C ABI in ``include/pml.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Pointers are passed
+as plain integers (``tensor.data_ptr()`` for device memory, numpy ``ctypes.data`` for
+host memory).  There is no fallback: if ``libpml.so`` has not been built, loading
+fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpml.so")
+
+PML_OK = 0
+PML_EINVAL = 1
+PML_ENOMEM = 2
+PML_ECUDA = 3
+PML_ESTATE = 4
+PML_EUNSTABLE = 5
+PML_ENONFINITE = 6
+PML_ETIMEOUT = 7
+
+PML_SIGMA_CONSTANT = 0
+PML_SIGMA_POWER = 1
+PML_SIGMA_RANDOM = 2
+PML_SIGMA_USER = 3
+
+PML_FLAG_ADJOINT = 1
+
+PML_FIELD_U = 0
+PML_FIELD_V = 1
+
+
+def PML_FIELD_PHI(a):
+    return 2 + 2 * a
+
+
+def PML_FIELD_PSI(a):
+    return 3 + 2 * a
+
+
+# every symbol the header declares (checked by the CPU test suite)
+EXPORTED = (
+    "pml_workspace_bytes", "pml_create", "pml_set_initial", "pml_set_sources",
+    "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
+    "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
+    "pml_adjoint_read_field", "pml_state_bytes", "pml_save_state", "pml_load_state",
+    "pml_profile_enable", "pml_profile_read", "pml_destroy", "pml_last_error",
+    "pml_status_string",
+)
+
+
+class pml_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3)]
+
+
+class pml_sigma_profile(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma_max", ctypes.c_double), ("order", ctypes.c_double),
+                ("user", ctypes.c_void_p * 3)]
+
+
+class PMLError(RuntimeError):
+    def __init__(self, status, text):
+        super().__init__("pml status %d: %s" % (status, text))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libpml.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libpml.so is not built (%s); run `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"` first" % p)
+    lib = ctypes.CDLL(p)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    st = ctypes.c_int
+    sig = {
+        "pml_workspace_bytes": [ctypes.POINTER(pml_grid), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_size_t)],
+        "pml_create": [ctypes.POINTER(pml_grid), ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                       ctypes.POINTER(pml_sigma_profile), ctypes.c_int, P, P, ctypes.c_size_t,
+                       ctypes.c_int, ctypes.POINTER(P)],
+        "pml_set_initial": [P, P, P, ctypes.c_int],
+        "pml_set_sources": [P, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_double],
+        "pml_set_receivers": [P, ctypes.c_int, P, P, i64],
+        "pml_step": [P, i64],
+        "pml_read_field": [P, ctypes.c_int, P, ctypes.c_int],
+        "pml_norms": [P, P, P],
+        "pml_get_step": [P, ctypes.POINTER(i64)],
+        "pml_sync": [P],
+        "pml_query_layout": [P, ctypes.c_int, P, P, P],
+        "pml_query_sigma": [P, ctypes.c_int, P],
+        "pml_adjoint_reset": [P],
+        "pml_adjoint_step": [P, i64, P, P, P],
+        "pml_adjoint_read_field": [P, ctypes.c_int, P, ctypes.c_int],
+        "pml_state_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "pml_save_state": [P, P, ctypes.c_int],
+        "pml_load_state": [P, P, ctypes.c_int],
+        "pml_profile_enable": [P, ctypes.c_int],
+        "pml_profile_read": [P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = st
+    lib.pml_destroy.argtypes = [P]
+    lib.pml_destroy.restype = None
+    lib.pml_last_error.argtypes = [P]
+    lib.pml_last_error.restype = ctypes.c_char_p
+    lib.pml_status_string.argtypes = [ctypes.c_int]
+    lib.pml_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != PML_OK:
+        txt = load().pml_last_error(ctx)
+        raise PMLError(status, txt.decode() if txt else "")
+    return status
+
+
+# ---- one Python function per C entry point -------------------------------------------
+
+def pml_workspace_bytes(ndim, n, pml_width, precision, flags=0) -> int:
+    g = pml_grid(ndim, (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))))
+    out = ctypes.c_size_t(0)
+    _check(load().pml_workspace_bytes(ctypes.byref(g), int(pml_width), int(precision), int(flags),
+                                      ctypes.byref(out)))
+    return int(out.value)
+
+
+def pml_create(ndim, n, h, dt, pml_width, kind, sigma_max, order, user, precision, stream,
+               workspace, workspace_bytes, flags=0):
+    """user: sequence of host pointers (int) or None per axis."""
+    g = pml_grid(ndim, (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))))
+    u = [None, None, None]
+    if user is not None:
+        for a, p in enumerate(user):
+            u[a] = p
+    prof = pml_sigma_profile(int(kind), float(sigma_max), float(order), (ctypes.c_void_p * 3)(*u))
+    ctx = ctypes.c_void_p(0)
+    _check(load().pml_create(ctypes.byref(g), float(h), float(dt), int(pml_width), ctypes.byref(prof),
+                             int(precision), stream, workspace, int(workspace_bytes), int(flags),
+                             ctypes.byref(ctx)))
+    return ctx.value
+
+
+def pml_set_initial(ctx, u0, v0, on_device):
+    _check(load().pml_set_initial(ctx, u0, v0, int(on_device)), ctx)
+
+
+def pml_set_sources(ctx, ns, coords, amp, f_peak, t_delay):
+    _check(load().pml_set_sources(ctx, int(ns), coords, amp, float(f_peak), float(t_delay)), ctx)
+
+
+def pml_set_receivers(ctx, nr, coords, trace_buf, capacity):
+    _check(load().pml_set_receivers(ctx, int(nr), coords, trace_buf, int(capacity)), ctx)
+
+
+def pml_step(ctx, n):
+    _check(load().pml_step(ctx, int(n)), ctx)
+
+
+def pml_read_field(ctx, field, dst, on_device):
+    _check(load().pml_read_field(ctx, int(field), dst, int(on_device)), ctx)
+
+
+def pml_norms(ctx, ref, out):
+    _check(load().pml_norms(ctx, ref, out), ctx)
+
+
+def pml_get_step(ctx) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().pml_get_step(ctx, ctypes.byref(v)), ctx)
+    return int(v.value)
+
+
+def pml_sync(ctx):
+    _check(load().pml_sync(ctx), ctx)
+
+
+def pml_query_layout(ctx, axis, phi, psi, interior):
+    _check(load().pml_query_layout(ctx, int(axis), phi, psi, interior), ctx)
+
+
+def pml_query_sigma(ctx, axis, out):
+    _check(load().pml_query_sigma(ctx, int(axis), out), ctx)
+
+
+def pml_adjoint_reset(ctx):
+    _check(load().pml_adjoint_reset(ctx), ctx)
+
+
+def pml_adjoint_step(ctx, n, residual, grad_u, grad_amp):
+    _check(load().pml_adjoint_step(ctx, int(n), residual, grad_u, grad_amp), ctx)
+
+
+def pml_adjoint_read_field(ctx, field, dst, on_device):
+    _check(load().pml_adjoint_read_field(ctx, int(field), dst, int(on_device)), ctx)
+
+
+def pml_state_bytes(ctx) -> int:
+    v = ctypes.c_size_t(0)
+    _check(load().pml_state_bytes(ctx, ctypes.byref(v)), ctx)
+    return int(v.value)
+
+
+def pml_save_state(ctx, dst, on_device):
+    _check(load().pml_save_state(ctx, dst, int(on_device)), ctx)
+
+
+def pml_load_state(ctx, src, on_device):
+    _check(load().pml_load_state(ctx, src, int(on_device)), ctx)
+
+
+def pml_profile_enable(ctx, enable):
+    _check(load().pml_profile_enable(ctx, int(enable)), ctx)
+
+
+def pml_profile_read(ctx):
+    """Returns (ms[3], launches[3]) for kinds interior, layer, point kernels."""
+    import numpy as np
+    ms = np.zeros(3, dtype=np.float64)
+    n = np.zeros(3, dtype=np.int64)
+    _check(load().pml_profile_read(ctx, ms.ctypes.data, n.ctypes.data), ctx)
+    return ms, n
+
+
+def pml_destroy(ctx):
+    load().pml_destroy(ctx)
+
+
+def pml_last_error(ctx) -> str:
+    t = load().pml_last_error(ctx)
+    return t.decode() if t else ""
+
+
+def pml_status_string(status) -> str:
+    return load().pml_status_string(int(status)).decode()

@@ -1,0 +1,295 @@
+// Internal declarations shared by the runtime and the kernels of the discrete-PML
+// library (sm_103a).  Nothing here is part of the public ABI (include/pml.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pml {
+
+// Ghost ring width of every padded field array.  The layer kernels read a halo of 4
+// vertices (one per RK4 stage), the interior kernels a halo of 2; the ghost ring holds
+// periodic copies so that every tile load is a plain rectangular TMA box.
+constexpr int G = 4;
+
+// Padded storage of one field: logical vertex (x, y, z), x in [-G, T0+G) etc., lives at
+// origin + x + y * P + z * PS.
+struct Geom {
+    int ndim;
+    int64_t T[3];      // vertices per axis (T[2] = 1 in 2D)
+    int64_t P;         // row pitch in elements (multiple of 32)
+    int64_t R;         // rows per plane incl. ghosts: T[1] + 2G
+    int64_t PS;        // plane stride = P * R
+    int64_t planes;    // T[2] + 2G (3D) or 1 (2D)
+    int64_t elems;     // elements per field array
+    int64_t origin;    // element offset of logical (0, 0, 0)
+};
+
+// Inclusive output range of the layer-free ("interior") kernels per axis.
+struct Range {
+    int64_t lo, hi;    // lo > hi: empty
+};
+
+// Coefficients of one RK4 step written as the Taylor polynomial
+// P(dt A) = I + dt A + (dt A)^2/2 + (dt A)^3/6 + (dt A)^4/24 restricted to the layer-free
+// region, where A = [[0, I], [L, 0]] on (U, V) and L = D / h^2 (D the unscaled
+// 5-/7-point difference).  Expanding the powers of A:
+//   U' = U + a1 V + a2 DU + a3 DV + a4 D^2U + a5 D^2V
+//   V' = V + b1 U + b2 DU + b3 DV + b4 D^2U + b5 D^2V
+// Forward:  a = (dt, dt^2/2h^2, dt^3/6h^2, dt^4/24h^4, 0),  b = (0, dt/h^2, dt^2/2h^2, dt^3/6h^4, dt^4/24h^4)
+// Adjoint (A^T = [[0, L], [I, 0]]):
+//           a = (0, dt^2/2h^2, dt/h^2, dt^4/24h^4, dt^3/6h^4), b = (dt, dt^3/6h^2, dt^2/2h^2, 0, dt^4/24h^4)
+struct StepCoef {
+    double a1, a2, a3, a4, a5;
+    double b1, b2, b3, b4, b5;
+};
+
+// One output tile of a layer kernel (2D: z fields unused).
+struct LayerTile {
+    int32_t x0, y0, z0;        // tile origin (x0 multiple of 4)
+    int32_t xlo, xhi;          // inclusive output clamp (rectangle of the frame)
+    int32_t ylo, yhi;
+    int32_t zlo, zhi;
+    int32_t flags;             // bit a: aux fields of axis a are active in the footprint
+};
+
+struct DeviceError {
+    int code;                  // 0 = ok, 1 = mbarrier wait timed out
+    int where;
+};
+
+// ---------------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll suspends for a hardware-defined
+// interval), records the failure and returns false.  No wait in this library can spin
+// forever.
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DeviceError *err, int where)
+{
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) {
+        atomicCAS(&err->code, 0, 1);
+        err->where = where;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                            int32_t z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Four consecutive x values of one row owned by one lane.
+template <typename T> struct V4 {
+    T x, y, z, w;
+};
+
+template <typename T> __device__ __forceinline__ V4<T> lds4(const T *p);
+template <> __device__ __forceinline__ V4<float> lds4<float>(const float *p)
+{
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ V4<double> lds4<double>(const double *p)
+{
+    double2 a = reinterpret_cast<const double2 *>(p)[0];
+    double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return {a.x, a.y, b.x, b.y};
+}
+
+template <typename T> __device__ __forceinline__ void stg4(T *p, const V4<T> &v);
+template <> __device__ __forceinline__ void stg4<float>(float *p, const V4<float> &v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v.x, v.y, v.z, v.w);
+}
+template <> __device__ __forceinline__ void stg4<double>(double *p, const V4<double> &v)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v.x, v.y);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v.z, v.w);
+}
+
+template <typename T> __device__ __forceinline__ T get4(const V4<T> &v, int k)
+{
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// Store one value at logical (x, y, z) and at every periodic image that falls inside the
+// ghost ring, so that the next step's tile loads see a periodic field.
+template <typename T>
+__device__ __forceinline__ void store_wrapped(T *base, const Geom &g, int64_t x, int64_t y, int64_t z,
+                                              T v)
+{
+    int64_t xs[2] = {x, x}, ys[2] = {y, y}, zs[2] = {z, z};
+    int nx = 1, ny = 1, nz = 1;
+    if (x < G) xs[nx++] = x + g.T[0];
+    else if (x >= g.T[0] - G) xs[nx++] = x - g.T[0];
+    if (y < G) ys[ny++] = y + g.T[1];
+    else if (y >= g.T[1] - G) ys[ny++] = y - g.T[1];
+    if (g.ndim == 3) {
+        if (z < G) zs[nz++] = z + g.T[2];
+        else if (z >= g.T[2] - G) zs[nz++] = z - g.T[2];
+    }
+    for (int c = 0; c < nz; ++c)
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) base[g.origin + xs[a] + ys[b] * g.P + zs[c] * g.PS] = v;
+}
+
+__device__ __forceinline__ bool near_edge(const Geom &g, int64_t x, int64_t y, int64_t z)
+{
+    bool e = x < G || x >= g.T[0] - G || y < G || y >= g.T[1] - G;
+    if (g.ndim == 3) e = e || z < G || z >= g.T[2] - G;
+    return e;
+}
+
+#endif  // __CUDACC__
+
+// ---------------------------------------------------------------------------------
+// kernel launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------------
+
+// Interior (layer-free) step of a 2D field pair: reads (U, V) through the tensor maps
+// (box 128 x kRows2D rows), writes (Uo, Vo) on the output rectangle xr x yr.
+struct Interior2DArgs {
+    Geom g;
+    Range xr, yr;
+    StepCoef c;
+    DeviceError *err;
+};
+cudaError_t launch_interior2d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                              void *Uo, void *Vo, const Interior2DArgs &a, int grid,
+                              cudaStream_t st);
+int interior2d_box_rows(int prec);
+int interior2d_max_blocks_per_sm(int prec, bool adjoint);
+
+// Layer step of 2D tiles (Horner form of the RK4 polynomial with the full operator).
+struct Layer2DArgs {
+    Geom g;
+    double dt, h;
+    const void *sig[2];        // device sigma per axis (context precision), length T[a]
+    const LayerTile *tiles;
+    int ntiles;
+    DeviceError *err;
+};
+constexpr int kLayerTH = 16, kLayerTW = 32;  // 2D layer tile (output) size
+cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U,V,Px,Qx,Py,Qy*/,
+                           void *const *out /*[6]*/, const Layer2DArgs &a, cudaStream_t st);
+
+// 3D counterparts.
+struct Interior3DArgs {
+    Geom g;
+    Range xr, yr, zr;
+    StepCoef c;
+    DeviceError *err;
+};
+cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                              void *Uo, void *Vo, const Interior3DArgs &a, int grid,
+                              cudaStream_t st);
+int interior3d_box_rows(int prec);
+int interior3d_tile_y();
+int interior3d_max_blocks_per_sm(int prec, bool adjoint);
+
+struct Layer3DArgs {
+    Geom g;
+    double dt, h;
+    const void *sig[3];
+    const LayerTile *tiles;
+    int ntiles;
+    DeviceError *err;
+};
+constexpr int kLayer3TX = 16, kLayer3TY = 8, kLayer3TZ = 4;  // 3D layer tile (output) size
+cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,
+                           void *const *out /*[8]*/, const Layer3DArgs &a, cudaStream_t st);
+
+// Sources and receivers after a forward step; receiver injection and source-amplitude
+// gradients before an adjoint step.
+struct PointArgs {
+    Geom g;
+    int ns;
+    const int64_t *src_off;    // element offsets (origin-relative flat index) of sources
+    const int32_t *src_xyz;    // logical coordinates [ns][3]
+    const double *src_amp;
+    double f_peak, t_delay;
+    int nr;
+    const int64_t *rec_off;
+    double dt, h;
+};
+cudaError_t launch_post_step(int prec, void *U, void *V, const PointArgs &a, int64_t step,
+                             void *trace_row, cudaStream_t st);
+cudaError_t launch_adjoint_points(int prec, void *Ub, void *Vb, const PointArgs &a, int64_t m,
+                                  const void *residual_row, double *grad_amp, cudaStream_t st);
+
+// Ghost ring refresh, dense <-> padded copies and FP64 norms.
+cudaError_t launch_fill_ghosts(int prec, void *f, const Geom &g, cudaStream_t st);
+cudaError_t launch_norms(int prec, const void *U, const void *V, const Geom &g, const int64_t *wlo,
+                         const int64_t *whi, double h, const double *ref, double *partials,
+                         int nblocks, double *out, cudaStream_t st);
+constexpr int kNormBlocks = 592;   // fixed partition (4 x 148): deterministic sums
+constexpr int kNormVals = 5;
+
+}  // namespace pml

@@ -1,0 +1,957 @@
+// Host runtime of the discrete-PML library: the C ABI of include/pml.h.
+//
+// Responsibilities: validate arguments, build the damping profiles (edge-centred,
+// Sec. 1.1.2) and the integer layout tables, carve the device workspace, encode the
+// TMA tensor maps, and enqueue the step kernels on the caller's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pml.h"
+
+using namespace pml;
+
+namespace {
+
+constexpr int kMaxSources = 1024;
+constexpr int kMaxReceivers = 16384;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+thread_local std::string g_create_error;
+
+struct Plan {
+    int nd = 0, esz = 0, nf = 0;
+    int64_t T[3] = {1, 1, 1};
+    Geom g{};
+    size_t fields[2][8] = {};
+    size_t adj[2][8] = {};
+    size_t sig[3] = {};
+    size_t tiles = 0, tiles_adj = 0, max_tiles = 0;
+    size_t partials = 0, normout = 0, err = 0;
+    size_t src_off = 0, src_xyz = 0, src_amp = 0, grad = 0, rec_off = 0;
+    size_t total = 0;
+};
+
+Geom make_geom(int nd, const int64_t T[3])
+{
+    Geom g{};
+    g.ndim = nd;
+    for (int a = 0; a < 3; ++a) g.T[a] = a < nd ? T[a] : 1;
+    g.P = round_up(g.T[0] + 2 * G, 32);
+    g.R = g.T[1] + 2 * G;
+    g.PS = g.P * g.R;
+    g.planes = nd == 3 ? g.T[2] + 2 * G : 1;
+    g.elems = g.PS * g.planes;
+    g.origin = G + G * g.P + (nd == 3 ? G * g.PS : 0);
+    return g;
+}
+
+// Upper bound of the number of layer tiles of one frame decomposition.
+size_t tile_bound(int nd, const int64_t T[3])
+{
+    if (nd == 2)
+        return size_t(4) * size_t(T[0] / kLayerTW + 2) * size_t(T[1] / kLayerTH + 2);
+    return size_t(6) * size_t(T[0] / kLayer3TX + 2) * size_t(T[1] / kLayer3TY + 2) *
+           size_t(T[2] / kLayer3TZ + 2);
+}
+
+bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::string *why)
+{
+    if (!grid) { *why = "grid is NULL"; return false; }
+    if (grid->ndim != 2 && grid->ndim != 3) { *why = "ndim must be 2 or 3"; return false; }
+    if (w < 0) { *why = "pml_width must be >= 0"; return false; }
+    if (prec != 32 && prec != 64) { *why = "precision must be 32 or 64"; return false; }
+    p->nd = grid->ndim;
+    p->esz = prec == 32 ? 4 : 8;
+    p->nf = 2 + 2 * p->nd;
+    for (int a = 0; a < p->nd; ++a) {
+        if (grid->n[a] < 1) { *why = "every axis needs at least one interior vertex"; return false; }
+        p->T[a] = grid->n[a] + 2 * int64_t(w);
+        if (p->T[a] < 2 * G) { *why = "every axis needs n + 2w >= 8 vertices"; return false; }
+        if (p->T[a] > (int64_t(1) << 30)) { *why = "axis too long"; return false; }
+    }
+    p->g = make_geom(p->nd, p->T);
+    size_t off = 0;
+    const size_t fb = align_up(size_t(p->g.elems) * p->esz, kAlign);
+    for (int s = 0; s < 2; ++s)
+        for (int f = 0; f < p->nf; ++f) { p->fields[s][f] = off; off += fb; }
+    if (flags & PML_FLAG_ADJOINT)
+        for (int s = 0; s < 2; ++s)
+            for (int f = 0; f < p->nf; ++f) { p->adj[s][f] = off; off += fb; }
+    for (int a = 0; a < p->nd; ++a) { p->sig[a] = off; off += align_up(size_t(p->T[a]) * p->esz, kAlign); }
+    p->max_tiles = tile_bound(p->nd, p->T);
+    p->tiles = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+    p->tiles_adj = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+    p->partials = off; off += align_up(size_t(kNormBlocks) * kNormVals * sizeof(double), kAlign);
+    p->normout = off; off += kAlign;
+    p->err = off; off += kAlign;
+    p->src_off = off; off += align_up(kMaxSources * sizeof(int64_t), kAlign);
+    p->src_xyz = off; off += align_up(kMaxSources * 3 * sizeof(int32_t), kAlign);
+    p->src_amp = off; off += align_up(kMaxSources * sizeof(double), kAlign);
+    p->grad = off; off += align_up(kMaxSources * sizeof(double), kAlign);
+    p->rec_off = off; off += align_up(kMaxReceivers * sizeof(int64_t), kAlign);
+    p->total = off;
+    return true;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+struct pml_ctx {
+    Plan plan;
+    int nd = 0, prec = 0, esz = 0, nf = 0, flags = 0, w = 0;
+    int64_t N[3] = {1, 1, 1}, T[3] = {1, 1, 1};
+    double h = 1, dt = 0.5;
+    std::vector<double> sig[3];
+    std::vector<uint8_t> phi[3], psi[3], inner[3];
+    Range ir[3], ir_adj[3];
+    Geom g{};
+    cudaStream_t st = nullptr;
+    bool own_ws = false;
+    char *ws = nullptr;
+    void *fld[2][8] = {}, *adj[2][8] = {};
+    int cur = 0, acur = 0;
+    void *dsig[3] = {};
+    LayerTile *dtiles = nullptr, *dtiles_adj = nullptr;
+    int ntiles = 0, ntiles_adj = 0;
+    double *dpart = nullptr, *dnorm = nullptr, *dgrad = nullptr;
+    DeviceError *derr = nullptr;
+    int ns = 0, nr = 0;
+    int64_t *dsrc_off = nullptr, *drec_off = nullptr;
+    int32_t *dsrc_xyz = nullptr;
+    double *dsrc_amp = nullptr;
+    double f_peak = 0, t_delay = 0;
+    void *trace = nullptr;
+    int64_t trace_cap = 0, trace_k = 0;
+    int64_t step = 0, astep = 0;
+    bool adj_ready = false;
+    CUtensorMap tm_int[2][2], tm_lay[2][8], tm_int_adj[2][2], tm_lay_adj[2][8];
+    int grid_int = 0, grid_int_adj = 0, sm_count = 0;
+    // kernel timing (pml_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;   // pairs
+    std::vector<int> prof_kind;
+    size_t prof_n = 0;
+    std::string err;
+};
+
+namespace {
+
+pml_status fail(pml_ctx *c, pml_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+pml_status cuda_fail(pml_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, PML_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PML_CU(c, call, what)                                      \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, (what));  \
+    } while (0)
+
+// depth of edge e in the layer: 0 on the physical edges and on both interface edges
+int64_t edge_depth(int64_t e, int64_t N, int64_t w)
+{
+    const int64_t a = w, b = w + N - 1;
+    int64_t d = 0;
+    if (a - 1 - e > d) d = a - 1 - e;
+    if (e - b > d) d = e - b;
+    return d;
+}
+
+pml_status build_sigma(pml_ctx *c, const pml_sigma_profile *pr)
+{
+    if (!pr) return fail(c, PML_EINVAL, "profile is NULL");
+    if (!(pr->sigma_max >= 0.0) || !std::isfinite(pr->sigma_max))
+        return fail(c, PML_EINVAL, "sigma_max must be finite and >= 0");
+    for (int a = 0; a < c->nd; ++a) {
+        const int64_t T = c->T[a], N = c->N[a], w = c->w;
+        std::vector<double> &s = c->sig[a];
+        s.assign(size_t(T), 0.0);
+        if ((pr->kind == PML_SIGMA_RANDOM || pr->kind == PML_SIGMA_USER) && !pr->user[a])
+            return fail(c, PML_EINVAL, "profile kind %d needs user[%d]", pr->kind, a);
+        for (int64_t e = 0; e < T; ++e) {
+            const int64_t d = edge_depth(e, N, w);
+            double v = 0.0;
+            switch (pr->kind) {
+            case PML_SIGMA_CONSTANT: v = d > 0 ? pr->sigma_max : 0.0; break;
+            case PML_SIGMA_POWER:
+                if (!(pr->order > 0.0)) return fail(c, PML_EINVAL, "power profile needs order > 0");
+                v = d > 0 ? pr->sigma_max * std::pow(double(d) / double(w), pr->order) : 0.0;
+                break;
+            case PML_SIGMA_RANDOM: {
+                const double u = pr->user[a][e];
+                if (!(u >= 0.0 && u <= 1.0)) return fail(c, PML_EINVAL, "random draws must lie in [0,1]");
+                v = d > 0 ? pr->sigma_max * u : 0.0;
+                break;
+            }
+            case PML_SIGMA_USER:
+                v = pr->user[a][e];
+                if (!std::isfinite(v) || v < 0.0) return fail(c, PML_EINVAL, "user sigma must be finite and >= 0");
+                if (d == 0 && v != 0.0)
+                    return fail(c, PML_EINVAL, "user sigma must vanish on the physical edges (axis %d, edge %lld)", a,
+                                (long long)e);
+                break;
+            default: return fail(c, PML_EINVAL, "unknown profile kind %d", pr->kind);
+            }
+            s[size_t(e)] = v;
+        }
+    }
+    return PML_OK;
+}
+
+// Supports of Phi / Psi and the layer-free run around the centre vertex.  `reach` is the
+// set of edge offsets that must carry zero damping: {-2..1} for the forward step and
+// {-3..2} for the transposed step.
+Range layer_free_run(const std::vector<double> &s, int64_t centre, int lo_off, int hi_off)
+{
+    const int64_t T = int64_t(s.size());
+    auto ok = [&](int64_t i) {
+        for (int k = lo_off; k <= hi_off; ++k)
+            if (s[size_t(((i + k) % T + T) % T)] != 0.0) return false;
+        return true;
+    };
+    bool all = true;
+    for (int64_t e = 0; e < T; ++e)
+        if (s[size_t(e)] != 0.0) { all = false; break; }
+    if (all) return {0, T - 1};
+    if (!ok(centre)) return {1, 0};
+    int64_t lo = centre, hi = centre;
+    while (lo - 1 >= 0 && ok(lo - 1)) --lo;
+    while (hi + 1 <= T - 1 && ok(hi + 1)) ++hi;
+    return {lo, hi};
+}
+
+void build_layout(pml_ctx *c)
+{
+    for (int a = 0; a < c->nd; ++a) {
+        const int64_t T = c->T[a];
+        const std::vector<double> &s = c->sig[a];
+        c->phi[a].assign(size_t(T), 0);
+        c->psi[a].assign(size_t(T), 0);
+        c->inner[a].assign(size_t(T), 0);
+        for (int64_t i = 0; i < T; ++i) {
+            c->phi[a][size_t(i)] = s[size_t(i)] != 0.0;
+            c->psi[a][size_t(i)] = s[size_t((i - 1 + T) % T)] != 0.0;
+        }
+        const int64_t centre = c->w + c->N[a] / 2;
+        c->ir[a] = layer_free_run(s, centre, -2, 1);
+        c->ir_adj[a] = layer_free_run(s, centre, -3, 2);
+        for (int64_t i = c->ir[a].lo; i <= c->ir[a].hi; ++i) c->inner[a][size_t(i)] = 1;
+    }
+    for (int a = c->nd; a < 3; ++a) c->ir[a] = c->ir_adj[a] = {0, 0};
+}
+
+bool axis_active(const pml_ctx *c, int a, int64_t lo, int64_t hi)
+{
+    const int64_t T = c->T[a];
+    for (int64_t i = lo; i < hi; ++i) {
+        const size_t k = size_t(((i % T) + T) % T);
+        if (c->phi[a][k] || c->psi[a][k]) return true;
+    }
+    return false;
+}
+
+struct Rect {
+    int64_t lo[3], hi[3];
+};
+
+// Frame = box minus the layer-free box ir[0] x ir[1] (x ir[2]), as disjoint rectangles.
+std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
+{
+    std::vector<Rect> out;
+    Rect full;
+    for (int a = 0; a < 3; ++a) { full.lo[a] = 0; full.hi[a] = a < c->nd ? c->T[a] - 1 : 0; }
+    bool empty = false;
+    for (int a = 0; a < c->nd; ++a) empty = empty || ir[a].lo > ir[a].hi;
+    if (empty) { out.push_back(full); return out; }
+    // peel axis by axis: slabs of axis a outside ir[a], restricted to ir of the earlier axes
+    Rect rest = full;
+    for (int a = c->nd - 1; a >= 0; --a) {
+        if (ir[a].lo > 0) {
+            Rect r = rest; r.lo[a] = 0; r.hi[a] = ir[a].lo - 1; out.push_back(r);
+        }
+        if (ir[a].hi < c->T[a] - 1) {
+            Rect r = rest; r.lo[a] = ir[a].hi + 1; r.hi[a] = c->T[a] - 1; out.push_back(r);
+        }
+        rest.lo[a] = ir[a].lo;
+        rest.hi[a] = ir[a].hi;
+    }
+    return out;
+}
+
+std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir)
+{
+    std::vector<LayerTile> t;
+    const int TX = c->nd == 2 ? kLayerTW : kLayer3TX;
+    const int TY = c->nd == 2 ? kLayerTH : kLayer3TY;
+    const int TZ = c->nd == 2 ? 1 : kLayer3TZ;
+    for (const Rect &r : frame_rects(c, ir)) {
+        for (int64_t z0 = r.lo[2]; z0 <= r.hi[2]; z0 += TZ)
+            for (int64_t y0 = r.lo[1]; y0 <= r.hi[1]; y0 += TY)
+                for (int64_t x0 = r.lo[0] & ~int64_t(3); x0 <= r.hi[0]; x0 += TX) {
+                    LayerTile L{};
+                    L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = int32_t(z0);
+                    L.xlo = int32_t(r.lo[0]); L.xhi = int32_t(r.hi[0]);
+                    L.ylo = int32_t(r.lo[1]); L.yhi = int32_t(r.hi[1]);
+                    L.zlo = int32_t(r.lo[2]); L.zhi = int32_t(r.hi[2]);
+                    int fl = 0;
+                    if (axis_active(c, 0, x0 - 4, x0 + TX + 4)) fl |= 1;
+                    if (axis_active(c, 1, y0 - 4, y0 + TY + 4)) fl |= 2;
+                    if (c->nd == 3 && axis_active(c, 2, z0 - 4, z0 + TZ + 4)) fl |= 4;
+                    L.flags = fl;
+                    t.push_back(L);
+                }
+    }
+    return t;
+}
+
+pml_status encode_map(pml_ctx *c, CUtensorMap *m, void *base, const uint32_t *box)
+{
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(c, PML_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const Geom &g = c->g;
+    const cuuint32_t rank = c->nd == 2 ? 2 : 3;
+    cuuint64_t dims[3] = {cuuint64_t(g.P), cuuint64_t(g.R), cuuint64_t(g.planes)};
+    cuuint64_t strides[2] = {cuuint64_t(g.P) * c->esz, cuuint64_t(g.PS) * c->esz};
+    cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_encode(m, c->esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank,
+                          base, dims, strides, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, PML_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    return PML_OK;
+}
+
+pml_status check_device_error(pml_ctx *c)
+{
+    DeviceError h{};
+    PML_CU(c, cudaMemcpyAsync(&h, c->derr, sizeof h, cudaMemcpyDeviceToHost, c->st), "read error flag");
+    PML_CU(c, cudaStreamSynchronize(c->st), "stream synchronize");
+    if (h.code != 0) return fail(c, PML_ETIMEOUT, "a bounded device wait gave up (site %d)", h.where);
+    return PML_OK;
+}
+
+cudaMemcpyKind kind_of(bool to_dev, bool from_dev)
+{
+    if (to_dev && from_dev) return cudaMemcpyDeviceToDevice;
+    if (to_dev) return cudaMemcpyHostToDevice;
+    if (from_dev) return cudaMemcpyDeviceToHost;
+    return cudaMemcpyHostToHost;
+}
+
+// dense T-grid <-> padded field (interior of the ghost ring)
+pml_status copy_dense(pml_ctx *c, void *padded, const void *dense, bool dense_on_dev, bool to_padded)
+{
+    const Geom &g = c->g;
+    cudaMemcpy3DParms p{};
+    char *pbase = static_cast<char *>(padded) + size_t(g.origin) * c->esz;
+    cudaPitchedPtr pp = make_cudaPitchedPtr(pbase, size_t(g.P) * c->esz, size_t(g.T[0]), size_t(g.R));
+    cudaPitchedPtr dp = make_cudaPitchedPtr(const_cast<void *>(dense), size_t(g.T[0]) * c->esz, size_t(g.T[0]),
+                                            size_t(g.T[1]));
+    p.extent = make_cudaExtent(size_t(g.T[0]) * c->esz, size_t(g.T[1]), size_t(g.T[2]));
+    if (to_padded) { p.srcPtr = dp; p.dstPtr = pp; p.kind = kind_of(true, dense_on_dev); }
+    else { p.srcPtr = pp; p.dstPtr = dp; p.kind = kind_of(dense_on_dev, true); }
+    PML_CU(c, cudaMemcpy3DAsync(&p, c->st), "cudaMemcpy3DAsync");
+    return PML_OK;
+}
+
+void step_coef(const pml_ctx *c, bool adjoint, StepCoef *k)
+{
+    const double dt = c->dt, h2 = c->h * c->h, h4 = h2 * h2;
+    const double d1 = dt, d2 = dt * dt / 2.0, d3 = dt * dt * dt / 6.0, d4 = dt * dt * dt * dt / 24.0;
+    if (!adjoint) {
+        *k = {d1, d2 / h2, d3 / h2, d4 / h4, 0.0, 0.0, d1 / h2, d2 / h2, d3 / h4, d4 / h4};
+    } else {
+        *k = {0.0, d2 / h2, d1 / h2, d4 / h4, d3 / h4, d1, d3 / h2, d2 / h2, 0.0, d4 / h4};
+    }
+}
+
+PointArgs point_args(const pml_ctx *c)
+{
+    PointArgs a{};
+    a.g = c->g;
+    a.ns = c->ns;
+    a.src_off = c->dsrc_off;
+    a.src_xyz = c->dsrc_xyz;
+    a.src_amp = c->dsrc_amp;
+    a.f_peak = c->f_peak;
+    a.t_delay = c->t_delay;
+    a.nr = c->nr;
+    a.rec_off = c->drec_off;
+    a.dt = c->dt;
+    a.h = c->h;
+    return a;
+}
+
+// Event pair around one kernel launch when profiling is on; returns the pair index.
+long prof_begin(pml_ctx *c, int kind)
+{
+    if (!c->prof_on) return -1;
+    if (c->prof_n == c->prof_kind.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return -1;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+        c->prof_ev.push_back(a);
+        c->prof_ev.push_back(b);
+        c->prof_kind.push_back(kind);
+    }
+    const size_t i = c->prof_n++;
+    c->prof_kind[i] = kind;
+    cudaEventRecord(c->prof_ev[2 * i], c->st);
+    return long(i);
+}
+
+void prof_end(pml_ctx *c, long i)
+{
+    if (i >= 0) cudaEventRecord(c->prof_ev[2 * size_t(i) + 1], c->st);
+}
+
+// One step (forward or transposed) from buffers `in` to buffers `out`.
+pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
+{
+    const int q = 1 - p;
+    void **out = adjoint ? c->adj[q] : c->fld[q];
+    const Range *ir = adjoint ? c->ir_adj : c->ir;
+    StepCoef k;
+    step_coef(c, adjoint, &k);
+    const CUtensorMap *ti = adjoint ? c->tm_int_adj[p] : c->tm_int[p];
+    const CUtensorMap *tl = adjoint ? c->tm_lay_adj[p] : c->tm_lay[p];
+    cudaError_t e;
+    if (c->nd == 2) {
+        Interior2DArgs a{};
+        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.c = k; a.err = c->derr;
+        long pi = prof_begin(c, 0);
+        e = launch_interior2d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
+                              adjoint ? c->grid_int_adj : c->grid_int, c->st);
+        prof_end(c, pi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "interior 2D kernel");
+        Layer2DArgs l{};
+        l.g = c->g; l.dt = c->dt; l.h = c->h;
+        l.sig[0] = c->dsig[0]; l.sig[1] = c->dsig[1];
+        l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
+        l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
+        l.err = c->derr;
+        pi = prof_begin(c, 1);
+        e = launch_layer2d(c->prec, adjoint, tl, out, l, c->st);
+        prof_end(c, pi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel");
+    } else {
+        Interior3DArgs a{};
+        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
+        long pi = prof_begin(c, 0);
+        e = launch_interior3d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
+                              adjoint ? c->grid_int_adj : c->grid_int, c->st);
+        prof_end(c, pi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "interior 3D kernel");
+        Layer3DArgs l{};
+        l.g = c->g; l.dt = c->dt; l.h = c->h;
+        for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
+        l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
+        l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
+        l.err = c->derr;
+        pi = prof_begin(c, 1);
+        e = launch_layer3d(c->prec, adjoint, tl, out, l, c->st);
+        prof_end(c, pi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "layer 3D kernel");
+    }
+    return PML_OK;
+}
+
+bool range_empty(const Range &r) { return r.lo > r.hi; }
+
+}  // namespace
+
+extern "C" {
+
+const char *pml_status_string(pml_status s)
+{
+    switch (s) {
+    case PML_OK: return "ok";
+    case PML_EINVAL: return "invalid argument";
+    case PML_ENOMEM: return "out of memory";
+    case PML_ECUDA: return "CUDA error";
+    case PML_ESTATE: return "invalid state";
+    case PML_EUNSTABLE: return "time step beyond the RK4 stability limit";
+    case PML_ENONFINITE: return "non-finite value";
+    case PML_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *pml_last_error(const pml_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+pml_status pml_workspace_bytes(const pml_grid *grid, int pml_width, int precision, int flags, size_t *bytes)
+{
+    Plan p;
+    std::string why;
+    if (!bytes) return fail(nullptr, PML_EINVAL, "bytes is NULL");
+    if (!make_plan(grid, pml_width, precision, flags, &p, &why)) return fail(nullptr, PML_EINVAL, "%s", why.c_str());
+    *bytes = p.total;
+    return PML_OK;
+}
+
+pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, const pml_sigma_profile *profile,
+                      int precision, void *cuda_stream, void *workspace, size_t workspace_bytes, int flags,
+                      pml_ctx **out)
+{
+    if (!out) return fail(nullptr, PML_EINVAL, "out is NULL");
+    *out = nullptr;
+    Plan plan;
+    std::string why;
+    if (!make_plan(grid, pml_width, precision, flags, &plan, &why)) return fail(nullptr, PML_EINVAL, "%s", why.c_str());
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(nullptr, PML_EINVAL, "h must be finite and > 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PML_EINVAL, "dt must be finite and > 0");
+    // RK4 is stable on the imaginary axis up to |z| = 2 sqrt(2); the discrete Laplacian's
+    // largest frequency is 2 sqrt(d) / h, hence dt <= sqrt(2/d) h.
+    if (dt > std::sqrt(2.0 / grid->ndim) * h * (1.0 + 1e-12))
+        return fail(nullptr, PML_EUNSTABLE, "dt = %g exceeds sqrt(2/%d) h = %g", dt, grid->ndim,
+                    std::sqrt(2.0 / grid->ndim) * h);
+    if (workspace && workspace_bytes < plan.total)
+        return fail(nullptr, PML_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, plan.total);
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+        return fail(nullptr, PML_EINVAL, "workspace must be 256-byte aligned");
+
+    pml_ctx *c = new pml_ctx();
+    c->plan = plan;
+    c->nd = plan.nd; c->prec = precision; c->esz = plan.esz; c->nf = plan.nf; c->flags = flags;
+    c->w = pml_width; c->h = h; c->dt = dt; c->g = plan.g;
+    for (int a = 0; a < 3; ++a) { c->N[a] = a < c->nd ? grid->n[a] : 1; c->T[a] = plan.T[a]; }
+    c->st = static_cast<cudaStream_t>(cuda_stream);
+
+    auto bail = [&](pml_status s) {
+        g_create_error = c->err;
+        if (c->own_ws && c->ws) cudaFree(c->ws);
+        delete c;
+        return s;
+    };
+    pml_status s = build_sigma(c, profile);
+    if (s != PML_OK) return bail(s);
+    build_layout(c);
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        fail(c, PML_ECUDA, "no CUDA device");
+        return bail(PML_ECUDA);
+    }
+    if (workspace) {
+        c->ws = static_cast<char *>(workspace);
+    } else {
+        cudaError_t e = cudaMalloc(&c->ws, plan.total);
+        if (e != cudaSuccess) {
+            c->ws = nullptr;
+            fail(c, PML_ENOMEM, "cudaMalloc(%zu): %s", plan.total, cudaGetErrorString(e));
+            return bail(PML_ENOMEM);
+        }
+        c->own_ws = true;
+    }
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < c->nf; ++f) {
+            c->fld[p][f] = c->ws + plan.fields[p][f];
+            if (flags & PML_FLAG_ADJOINT) c->adj[p][f] = c->ws + plan.adj[p][f];
+        }
+    for (int a = 0; a < c->nd; ++a) c->dsig[a] = c->ws + plan.sig[a];
+    c->dtiles = reinterpret_cast<LayerTile *>(c->ws + plan.tiles);
+    c->dtiles_adj = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_adj);
+    c->dpart = reinterpret_cast<double *>(c->ws + plan.partials);
+    c->dnorm = reinterpret_cast<double *>(c->ws + plan.normout);
+    c->derr = reinterpret_cast<DeviceError *>(c->ws + plan.err);
+    c->dsrc_off = reinterpret_cast<int64_t *>(c->ws + plan.src_off);
+    c->dsrc_xyz = reinterpret_cast<int32_t *>(c->ws + plan.src_xyz);
+    c->dsrc_amp = reinterpret_cast<double *>(c->ws + plan.src_amp);
+    c->dgrad = reinterpret_cast<double *>(c->ws + plan.grad);
+    c->drec_off = reinterpret_cast<int64_t *>(c->ws + plan.rec_off);
+
+    // state = 0 everywhere (both ping-pong halves, adjoint too)
+    {
+        cudaError_t e = cudaMemsetAsync(c->ws, 0, plan.sig[0], c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(DeviceError), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->dgrad, 0, kMaxSources * sizeof(double), c->st);
+        if (e != cudaSuccess) { cuda_fail(c, e, "clear workspace"); return bail(PML_ECUDA); }
+    }
+    // damping in the state precision
+    for (int a = 0; a < c->nd; ++a) {
+        std::vector<char> buf(size_t(c->T[a]) * c->esz);
+        for (int64_t i = 0; i < c->T[a]; ++i) {
+            if (c->esz == 4) reinterpret_cast<float *>(buf.data())[i] = float(c->sig[a][size_t(i)]);
+            else reinterpret_cast<double *>(buf.data())[i] = c->sig[a][size_t(i)];
+        }
+        cudaError_t e = cudaMemcpy(c->dsig[a], buf.data(), buf.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cuda_fail(c, e, "upload sigma"); return bail(PML_ECUDA); }
+    }
+    // layer tiles
+    {
+        std::vector<LayerTile> tf = build_tiles(c, c->ir), ta = build_tiles(c, c->ir_adj);
+        if (tf.size() > plan.max_tiles || ta.size() > plan.max_tiles) {
+            fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
+            return bail(PML_ENOMEM);
+        }
+        c->ntiles = int(tf.size());
+        c->ntiles_adj = int(ta.size());
+        cudaError_t e = cudaSuccess;
+        if (!tf.empty()) e = cudaMemcpy(c->dtiles, tf.data(), tf.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !ta.empty() && (flags & PML_FLAG_ADJOINT))
+            e = cudaMemcpy(c->dtiles_adj, ta.data(), ta.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cuda_fail(c, e, "upload tiles"); return bail(PML_ECUDA); }
+    }
+    // tensor maps
+    {
+        uint32_t box_int[3], box_lay[3];
+        if (c->nd == 2) {
+            box_int[0] = 128; box_int[1] = uint32_t(interior2d_box_rows(precision)); box_int[2] = 1;
+            box_lay[0] = kLayerTW + 8; box_lay[1] = kLayerTH + 8; box_lay[2] = 1;
+        } else {
+            box_int[0] = 128; box_int[1] = uint32_t(interior3d_tile_y() + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
+            box_lay[0] = kLayer3TX + 8; box_lay[1] = kLayer3TY + 8; box_lay[2] = kLayer3TZ + 8;
+        }
+        for (int p = 0; p < 2; ++p) {
+            for (int f = 0; f < 2; ++f) {
+                if ((s = encode_map(c, &c->tm_int[p][f], c->fld[p][f], box_int)) != PML_OK) return bail(s);
+                if ((flags & PML_FLAG_ADJOINT) &&
+                    (s = encode_map(c, &c->tm_int_adj[p][f], c->adj[p][f], box_int)) != PML_OK)
+                    return bail(s);
+            }
+            for (int f = 0; f < c->nf; ++f) {
+                if ((s = encode_map(c, &c->tm_lay[p][f], c->fld[p][f], box_lay)) != PML_OK) return bail(s);
+                if ((flags & PML_FLAG_ADJOINT) &&
+                    (s = encode_map(c, &c->tm_lay_adj[p][f], c->adj[p][f], box_lay)) != PML_OK)
+                    return bail(s);
+            }
+            for (int f = c->nf; f < 8; ++f) { c->tm_lay[p][f] = c->tm_lay[p][0]; c->tm_lay_adj[p][f] = c->tm_lay_adj[p][0]; }
+        }
+    }
+    {
+        int bps = c->nd == 2 ? interior2d_max_blocks_per_sm(precision, false) : interior3d_max_blocks_per_sm(precision, false);
+        int bpa = (flags & PML_FLAG_ADJOINT)
+                      ? (c->nd == 2 ? interior2d_max_blocks_per_sm(precision, true) : interior3d_max_blocks_per_sm(precision, true))
+                      : 0;
+        if (bps <= 0) { fail(c, PML_ECUDA, "interior kernel cannot be resident (shared memory / registers)"); return bail(PML_ECUDA); }
+        c->grid_int = bps * c->sm_count;
+        c->grid_int_adj = bpa * c->sm_count;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) { cuda_fail(c, e, "create"); return bail(PML_ECUDA); }
+    *out = c;
+    return PML_OK;
+}
+
+pml_status pml_profile_enable(pml_ctx *c, int enable)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    c->prof_on = enable != 0;
+    return PML_OK;
+}
+
+pml_status pml_profile_read(pml_ctx *c, double ms[3], int64_t launches[3])
+{
+    if (!c || !ms || !launches) return fail(c, PML_EINVAL, "NULL argument");
+    PML_CU(c, cudaStreamSynchronize(c->st), "stream synchronize");
+    for (int k = 0; k < 3; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (size_t i = 0; i < c->prof_n; ++i) {
+        float t = 0.f;
+        PML_CU(c, cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]), "event time");
+        ms[c->prof_kind[i]] += double(t);
+        launches[c->prof_kind[i]] += 1;
+    }
+    c->prof_n = 0;
+    return PML_OK;
+}
+
+void pml_destroy(pml_ctx *c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+}
+
+pml_status pml_set_initial(pml_ctx *c, const void *u0, const void *v0, int on_device)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    const size_t fb = align_up(size_t(c->g.elems) * c->esz, kAlign);
+    PML_CU(c, cudaMemsetAsync(c->ws, 0, fb * size_t(2 * c->nf), c->st), "clear state");
+    c->cur = 0;
+    if (u0) {
+        pml_status s = copy_dense(c, c->fld[0][0], u0, on_device != 0, true);
+        if (s != PML_OK) return s;
+    }
+    if (v0) {
+        pml_status s = copy_dense(c, c->fld[0][1], v0, on_device != 0, true);
+        if (s != PML_OK) return s;
+    }
+    PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][0], c->g, c->st), "ghost fill");
+    PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][1], c->g, c->st), "ghost fill");
+    c->step = 0;
+    c->trace_k = 0;
+    return PML_OK;
+}
+
+pml_status pml_set_sources(pml_ctx *c, int ns, const int64_t *coords, const double *amp, double f_peak,
+                           double t_delay)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (ns < 0 || ns > kMaxSources) return fail(c, PML_EINVAL, "0 <= ns <= %d", kMaxSources);
+    if (ns > 0 && (!coords || !amp)) return fail(c, PML_EINVAL, "coords/amp are NULL");
+    if (!std::isfinite(f_peak) || !std::isfinite(t_delay)) return fail(c, PML_EINVAL, "non-finite wavelet parameters");
+    std::vector<int64_t> off(static_cast<size_t>(ns));
+    std::vector<int32_t> xyz(size_t(3 * ns), 0);
+    for (int s = 0; s < ns; ++s) {
+        if (!std::isfinite(amp[s])) return fail(c, PML_ENONFINITE, "source amplitude %d is not finite", s);
+        int64_t o = 0;
+        const int64_t st[3] = {1, c->g.P, c->g.PS};
+        for (int a = 0; a < c->nd; ++a) {
+            const int64_t x = coords[s * c->nd + a];
+            if (x < c->ir[a].lo || x > c->ir[a].hi)
+                return fail(c, PML_EINVAL, "source %d: coordinate %lld of axis %d is outside the layer-free run [%lld, %lld]",
+                            s, (long long)x, a, (long long)c->ir[a].lo, (long long)c->ir[a].hi);
+            xyz[size_t(3 * s + a)] = int32_t(x);
+            o += x * st[a];
+        }
+        off[size_t(s)] = o;
+    }
+    if (ns > 0) {
+        PML_CU(c, cudaMemcpy(c->dsrc_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "sources");
+        PML_CU(c, cudaMemcpy(c->dsrc_xyz, xyz.data(), xyz.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "sources");
+        PML_CU(c, cudaMemcpy(c->dsrc_amp, amp, size_t(ns) * sizeof(double), cudaMemcpyHostToDevice), "sources");
+    }
+    c->ns = ns;
+    c->f_peak = f_peak;
+    c->t_delay = t_delay;
+    return PML_OK;
+}
+
+pml_status pml_set_receivers(pml_ctx *c, int nr, const int64_t *coords, void *trace_buf, int64_t capacity)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (nr < 0 || nr > kMaxReceivers) return fail(c, PML_EINVAL, "0 <= nr <= %d", kMaxReceivers);
+    if (nr > 0 && (!coords || !trace_buf || capacity < 0)) return fail(c, PML_EINVAL, "receiver arguments");
+    std::vector<int64_t> off(static_cast<size_t>(nr));
+    const int64_t st[3] = {1, c->g.P, c->g.PS};
+    for (int r = 0; r < nr; ++r) {
+        int64_t o = 0;
+        for (int a = 0; a < c->nd; ++a) {
+            const int64_t x = coords[r * c->nd + a];
+            if (x < 0 || x >= c->T[a]) return fail(c, PML_EINVAL, "receiver %d outside the box", r);
+            o += x * st[a];
+        }
+        off[size_t(r)] = o;
+    }
+    if (nr > 0)
+        PML_CU(c, cudaMemcpy(c->drec_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "receivers");
+    c->nr = nr;
+    c->trace = trace_buf;
+    c->trace_cap = capacity;
+    c->trace_k = 0;
+    return PML_OK;
+}
+
+pml_status pml_step(pml_ctx *c, int64_t n)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(c, PML_EINVAL, "n must be >= 0");
+    const PointArgs pa = point_args(c);
+    for (int64_t k = 0; k < n; ++k) {
+        const int p = c->cur, q = 1 - p;
+        pml_status s = enqueue_step(c, false, p);
+        if (s != PML_OK) return s;
+        void *row = nullptr;
+        if (c->nr > 0 && c->trace_k < c->trace_cap)
+            row = static_cast<char *>(c->trace) + size_t(c->trace_k) * size_t(c->nr) * c->esz;
+        if (c->ns > 0 || row) {
+            long pi = prof_begin(c, 2);
+            cudaError_t e = launch_post_step(c->prec, c->fld[q][0], c->fld[q][1], pa, c->step, row, c->st);
+            prof_end(c, pi);
+            if (e != cudaSuccess) return cuda_fail(c, e, "post-step kernel");
+        }
+        if (row) c->trace_k++;
+        c->cur = q;
+        c->step++;
+    }
+    return PML_OK;
+}
+
+pml_status pml_read_field(pml_ctx *c, int field, void *dst, int on_device)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (field < 0 || field >= c->nf || !dst) return fail(c, PML_EINVAL, "bad field %d or NULL dst", field);
+    pml_status s = copy_dense(c, c->fld[c->cur][field], dst, on_device != 0, false);
+    if (s != PML_OK) return s;
+    if (!on_device) return check_device_error(c);
+    return PML_OK;
+}
+
+pml_status pml_norms(pml_ctx *c, const double *ref, double out[5])
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, PML_EINVAL, "out is NULL");
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < c->nd; ++a) { lo[a] = c->w; hi[a] = c->w + c->N[a] - 1; }
+    PML_CU(c, launch_norms(c->prec, c->fld[c->cur][0], c->fld[c->cur][1], c->g, lo, hi, c->h, ref, c->dpart,
+                           kNormBlocks, c->dnorm, c->st), "norms kernel");
+    PML_CU(c, cudaMemcpyAsync(out, c->dnorm, kNormVals * sizeof(double), cudaMemcpyDeviceToHost, c->st), "norms copy");
+    return check_device_error(c);
+}
+
+pml_status pml_get_step(const pml_ctx *c, int64_t *step)
+{
+    if (!c || !step) return fail(nullptr, PML_EINVAL, "NULL argument");
+    *step = c->step;
+    return PML_OK;
+}
+
+pml_status pml_sync(pml_ctx *c)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    return check_device_error(c);
+}
+
+pml_status pml_query_layout(const pml_ctx *c, int axis, uint8_t *phi_active, uint8_t *psi_active, uint8_t *interior)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (axis < 0 || axis >= c->nd) return fail(const_cast<pml_ctx *>(c), PML_EINVAL, "bad axis");
+    const size_t T = size_t(c->T[axis]);
+    if (phi_active) std::memcpy(phi_active, c->phi[axis].data(), T);
+    if (psi_active) std::memcpy(psi_active, c->psi[axis].data(), T);
+    if (interior) std::memcpy(interior, c->inner[axis].data(), T);
+    return PML_OK;
+}
+
+pml_status pml_query_sigma(const pml_ctx *c, int axis, double *sigma)
+{
+    if (!c || !sigma) return fail(nullptr, PML_EINVAL, "NULL argument");
+    if (axis < 0 || axis >= c->nd) return fail(const_cast<pml_ctx *>(c), PML_EINVAL, "bad axis");
+    std::memcpy(sigma, c->sig[axis].data(), c->sig[axis].size() * sizeof(double));
+    return PML_OK;
+}
+
+pml_status pml_adjoint_reset(pml_ctx *c)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (!(c->flags & PML_FLAG_ADJOINT)) return fail(c, PML_ESTATE, "context was created without PML_FLAG_ADJOINT");
+    const size_t fb = align_up(size_t(c->g.elems) * c->esz, kAlign);
+    PML_CU(c, cudaMemsetAsync(c->adj[0][0], 0, fb * size_t(2 * c->nf), c->st), "clear adjoint");
+    PML_CU(c, cudaMemsetAsync(c->dgrad, 0, kMaxSources * sizeof(double), c->st), "clear gradient");
+    c->acur = 0;
+    c->astep = c->step;
+    c->adj_ready = true;
+    return PML_OK;
+}
+
+pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *grad_u, double *grad_amp)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (!c->adj_ready) return fail(c, PML_ESTATE, "call pml_adjoint_reset first");
+    if (n < 0) return fail(c, PML_EINVAL, "n must be >= 0");
+    const PointArgs pa = point_args(c);
+    for (int64_t k = 0; k < n; ++k) {
+        const int p = c->acur;
+        const int64_t m = c->astep;
+        const void *row = (residual && c->nr > 0)
+                              ? static_cast<const char *>(residual) + size_t(k) * size_t(c->nr) * c->esz
+                              : nullptr;
+        if (row || c->ns > 0)
+            PML_CU(c, launch_adjoint_points(c->prec, c->adj[p][0], c->adj[p][1], pa, m, row,
+                                            c->ns > 0 ? c->dgrad : nullptr, c->st), "adjoint point kernel");
+        pml_status s = enqueue_step(c, true, p);
+        if (s != PML_OK) return s;
+        c->acur = 1 - p;
+        c->astep = m - 1;
+    }
+    if (grad_u) {
+        pml_status s = copy_dense(c, c->adj[c->acur][0], grad_u, true, false);
+        if (s != PML_OK) return s;
+    }
+    if (grad_amp && c->ns > 0) {
+        PML_CU(c, cudaMemcpyAsync(grad_amp, c->dgrad, size_t(c->ns) * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+               "gradient copy");
+        return check_device_error(c);
+    }
+    return PML_OK;
+}
+
+pml_status pml_adjoint_read_field(pml_ctx *c, int field, void *dst, int on_device)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (!c->adj_ready) return fail(c, PML_ESTATE, "call pml_adjoint_reset first");
+    if (field < 0 || field >= c->nf || !dst) return fail(c, PML_EINVAL, "bad field %d or NULL dst", field);
+    pml_status s = copy_dense(c, c->adj[c->acur][field], dst, on_device != 0, false);
+    if (s != PML_OK) return s;
+    if (!on_device) return check_device_error(c);
+    return PML_OK;
+}
+
+pml_status pml_state_bytes(const pml_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return fail(nullptr, PML_EINVAL, "NULL argument");
+    *bytes = 64 + size_t(c->nf) * size_t(c->g.elems) * c->esz;
+    return PML_OK;
+}
+
+pml_status pml_save_state(pml_ctx *c, void *dst, int on_device)
+{
+    if (!c || !dst) return fail(c, PML_EINVAL, "NULL argument");
+    int64_t hdr[8] = {0x504d4c53, c->step, c->nf, c->g.elems, c->esz, 0, 0, 0};
+    char *d = static_cast<char *>(dst);
+    const cudaMemcpyKind kh = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    PML_CU(c, cudaMemcpyAsync(d, hdr, sizeof hdr, kh, c->st), "save header");
+    const size_t fb = size_t(c->g.elems) * c->esz;
+    for (int f = 0; f < c->nf; ++f)
+        PML_CU(c, cudaMemcpyAsync(d + 64 + f * fb, c->fld[c->cur][f], fb,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st),
+               "save field");
+    return check_device_error(c);
+}
+
+pml_status pml_load_state(pml_ctx *c, const void *src, int on_device)
+{
+    if (!c || !src) return fail(c, PML_EINVAL, "NULL argument");
+    int64_t hdr[8];
+    PML_CU(c, cudaMemcpyAsync(hdr, src, sizeof hdr, on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->st),
+           "load header");
+    PML_CU(c, cudaStreamSynchronize(c->st), "load header");
+    if (hdr[0] != 0x504d4c53 || hdr[2] != c->nf || hdr[3] != c->g.elems || hdr[4] != c->esz)
+        return fail(c, PML_EINVAL, "checkpoint does not match this context");
+    const char *sp = static_cast<const char *>(src);
+    const size_t fb = size_t(c->g.elems) * c->esz;
+    for (int f = 0; f < c->nf; ++f)
+        PML_CU(c, cudaMemcpyAsync(c->fld[0][f], sp + 64 + f * fb, fb,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st),
+               "load field");
+    c->cur = 0;
+    c->step = hdr[1];
+    return check_device_error(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+"""The C-ABI library loads on a machine without a GPU and exports every symbol that
+include/pml.h declares (no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pml.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pml_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_01390_gb300 import build as b
+    return ctypes.CDLL(b.build())
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("pml_create", "pml_set_initial", "pml_step", "pml_read_field", "pml_adjoint_step",
+                 "pml_norms", "pml_set_sources", "pml_set_receivers", "pml_save_state",
+                 "pml_load_state", "pml_destroy", "pml_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1804_01390_gb300 import _lib
+    assert sorted(_lib.EXPORTED) == _declared()
+
+
+def test_host_only_calls_without_gpu(lib):
+    """pml_workspace_bytes and pml_status_string need no device."""
+    from paper_1804_01390_gb300 import _lib
+    _lib.load()
+    b32 = _lib.pml_workspace_bytes(2, (128, 128), 16, 32)
+    b64 = _lib.pml_workspace_bytes(2, (128, 128), 16, 64)
+    assert b64 > b32 > 0
+    with pytest.raises(_lib.PMLError) as e:
+        _lib.pml_workspace_bytes(4, (1, 1), 1, 32)
+    assert e.value.status == _lib.PML_EINVAL
+    with pytest.raises(_lib.PMLError):
+        _lib.pml_workspace_bytes(2, (2, 2), 1, 32)       # n + 2w < 8
+    assert _lib.pml_status_string(_lib.PML_EUNSTABLE).startswith("time step")
