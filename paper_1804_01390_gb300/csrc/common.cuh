@@ -258,11 +258,17 @@ struct Layer3DArgs {
     Geom g;
     double dt, h;
     const void *sig[3];
-    const LayerTile *tiles;
+    const LayerTile *tiles;    // sorted by flags (set of axes with active aux fields)
     int ntiles;
+    int class_off[9];          // tiles of flags m are [class_off[m], class_off[m+1])
     DeviceError *err;
 };
-constexpr int kLayer3TX = 16, kLayer3TY = 8, kLayer3TZ = 4;  // 3D layer tile (output) size
+// 3D layer column tiles (x, y output extent; halo 4 on each side) and z segment length
+constexpr int kLayer3TXf = 28, kLayer3TYf = 8;   // FP32: 36 x 16 region columns
+constexpr int kLayer3TXd = 12, kLayer3TYd = 4;   // FP64: 20 x 12 region columns
+constexpr int kLayer3LZ = 64;
+int layer3d_tile_x(int prec);
+int layer3d_tile_y(int prec);
 cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,
                            void *const *out /*[8]*/, const Layer3DArgs &a, cudaStream_t st);
 

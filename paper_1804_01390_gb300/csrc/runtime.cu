@@ -59,12 +59,12 @@ Geom make_geom(int nd, const int64_t T[3])
 }
 
 // Upper bound of the number of layer tiles of one frame decomposition.
-size_t tile_bound(int nd, const int64_t T[3])
+size_t tile_bound(int nd, int prec, const int64_t T[3])
 {
     if (nd == 2)
         return size_t(4) * size_t(T[0] / kLayerTW + 2) * size_t(T[1] / kLayerTH + 2);
-    return size_t(6) * size_t(T[0] / kLayer3TX + 2) * size_t(T[1] / kLayer3TY + 2) *
-           size_t(T[2] / kLayer3TZ + 2);
+    const int TX = prec == 32 ? kLayer3TXf : kLayer3TXd, TY = prec == 32 ? kLayer3TYf : kLayer3TYd;
+    return size_t(5) * size_t(T[0] / TX + 2) * size_t(T[1] / TY + 2) * size_t(T[2] / kLayer3LZ + 2);
 }
 
 bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::string *why)
@@ -91,7 +91,7 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
         for (int s = 0; s < 2; ++s)
             for (int f = 0; f < p->nf; ++f) { p->adj[s][f] = off; off += fb; }
     for (int a = 0; a < p->nd; ++a) { p->sig[a] = off; off += align_up(size_t(p->T[a]) * p->esz, kAlign); }
-    p->max_tiles = tile_bound(p->nd, p->T);
+    p->max_tiles = tile_bound(p->nd, prec, p->T);
     p->tiles = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
     p->tiles_adj = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
     p->partials = off; off += align_up(size_t(kNormBlocks) * kNormVals * sizeof(double), kAlign);
@@ -127,6 +127,7 @@ struct pml_ctx {
     void *dsig[3] = {};
     LayerTile *dtiles = nullptr, *dtiles_adj = nullptr;
     int ntiles = 0, ntiles_adj = 0;
+    int class_off[9] = {}, class_off_adj[9] = {};
     double *dpart = nullptr, *dnorm = nullptr, *dgrad = nullptr;
     DeviceError *derr = nullptr;
     int ns = 0, nr = 0;
@@ -289,14 +290,18 @@ std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
     bool empty = false;
     for (int a = 0; a < c->nd; ++a) empty = empty || ir[a].lo > ir[a].hi;
     if (empty) { out.push_back(full); return out; }
-    // peel axis by axis: slabs of axis a outside ir[a], restricted to ir of the earlier axes
+    // peel axis by axis: slabs of axis a outside ir[a], restricted to ir of the earlier axes.
+    // In 3D the two z slabs form one band across the periodic seam (the z-streaming layer
+    // kernel loads plane by plane and wraps z itself), so it is one rectangle with an
+    // unwrapped z range ir.hi+1 .. T + ir.lo - 1.
     Rect rest = full;
     for (int a = c->nd - 1; a >= 0; --a) {
-        if (ir[a].lo > 0) {
-            Rect r = rest; r.lo[a] = 0; r.hi[a] = ir[a].lo - 1; out.push_back(r);
-        }
-        if (ir[a].hi < c->T[a] - 1) {
-            Rect r = rest; r.lo[a] = ir[a].hi + 1; r.hi[a] = c->T[a] - 1; out.push_back(r);
+        const bool lo_gap = ir[a].lo > 0, hi_gap = ir[a].hi < c->T[a] - 1;
+        if (a == 2 && (lo_gap || hi_gap)) {
+            Rect r = rest; r.lo[a] = ir[a].hi + 1; r.hi[a] = c->T[a] + ir[a].lo - 1; out.push_back(r);
+        } else {
+            if (lo_gap) { Rect r = rest; r.lo[a] = 0; r.hi[a] = ir[a].lo - 1; out.push_back(r); }
+            if (hi_gap) { Rect r = rest; r.lo[a] = ir[a].hi + 1; r.hi[a] = c->T[a] - 1; out.push_back(r); }
         }
         rest.lo[a] = ir[a].lo;
         rest.hi[a] = ir[a].hi;
@@ -304,12 +309,16 @@ std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
     return out;
 }
 
-std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir)
+// Layer tiles of the frame.  2D: kLayerTW x kLayerTH output tiles.  3D: (x, y) column
+// tiles streamed over z segments of at most kLayer3LZ planes (zlo..zhi, unwrapped), sorted
+// by flags so that each class runs with its own field count.
+std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_off[9])
 {
     std::vector<LayerTile> t;
-    const int TX = c->nd == 2 ? kLayerTW : kLayer3TX;
-    const int TY = c->nd == 2 ? kLayerTH : kLayer3TY;
-    const int TZ = c->nd == 2 ? 1 : kLayer3TZ;
+    const bool d3 = c->nd == 3;
+    const int TX = d3 ? layer3d_tile_x(c->prec) : kLayerTW;
+    const int TY = d3 ? layer3d_tile_y(c->prec) : kLayerTH;
+    const int TZ = d3 ? kLayer3LZ : 1;
     for (const Rect &r : frame_rects(c, ir)) {
         for (int64_t z0 = r.lo[2]; z0 <= r.hi[2]; z0 += TZ)
             for (int64_t y0 = r.lo[1]; y0 <= r.hi[1]; y0 += TY)
@@ -318,15 +327,20 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir)
                     L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = int32_t(z0);
                     L.xlo = int32_t(r.lo[0]); L.xhi = int32_t(r.hi[0]);
                     L.ylo = int32_t(r.lo[1]); L.yhi = int32_t(r.hi[1]);
-                    L.zlo = int32_t(r.lo[2]); L.zhi = int32_t(r.hi[2]);
+                    L.zlo = int32_t(z0); L.zhi = int32_t(std::min<int64_t>(z0 + TZ - 1, r.hi[2]));
+                    if (!d3) { L.zlo = 0; L.zhi = 0; }
                     int fl = 0;
                     if (axis_active(c, 0, x0 - 4, x0 + TX + 4)) fl |= 1;
                     if (axis_active(c, 1, y0 - 4, y0 + TY + 4)) fl |= 2;
-                    if (c->nd == 3 && axis_active(c, 2, z0 - 4, z0 + TZ + 4)) fl |= 4;
+                    if (d3 && axis_active(c, 2, L.zlo - 4, L.zhi + 5)) fl |= 4;
                     L.flags = fl;
                     t.push_back(L);
                 }
     }
+    std::stable_sort(t.begin(), t.end(), [](const LayerTile &a, const LayerTile &b) { return a.flags < b.flags; });
+    for (int m = 0; m <= 8; ++m) class_off[m] = 0;
+    for (const LayerTile &L : t) class_off[L.flags + 1]++;
+    for (int m = 0; m < 8; ++m) class_off[m + 1] += class_off[m];
     return t;
 }
 
@@ -479,6 +493,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
         l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
+        for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
         l.err = c->derr;
         pi = prof_begin(c, 1);
         e = launch_layer3d(c->prec, adjoint, tl, out, l, c->st);
@@ -487,8 +502,6 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
     }
     return PML_OK;
 }
-
-bool range_empty(const Range &r) { return r.lo > r.hi; }
 
 }  // namespace
 
@@ -611,7 +624,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     }
     // layer tiles
     {
-        std::vector<LayerTile> tf = build_tiles(c, c->ir), ta = build_tiles(c, c->ir_adj);
+        std::vector<LayerTile> tf = build_tiles(c, c->ir, c->class_off),
+                               ta = build_tiles(c, c->ir_adj, c->class_off_adj);
         if (tf.size() > plan.max_tiles || ta.size() > plan.max_tiles) {
             fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
             return bail(PML_ENOMEM);
@@ -632,7 +646,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             box_lay[0] = kLayerTW + 8; box_lay[1] = kLayerTH + 8; box_lay[2] = 1;
         } else {
             box_int[0] = 128; box_int[1] = uint32_t(interior3d_tile_y() + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
-            box_lay[0] = kLayer3TX + 8; box_lay[1] = kLayer3TY + 8; box_lay[2] = kLayer3TZ + 8;
+            box_lay[0] = uint32_t(layer3d_tile_x(precision) + 8); box_lay[1] = uint32_t(layer3d_tile_y(precision) + 8);
+            box_lay[2] = 1;
         }
         for (int p = 0; p < 2; ++p) {
             for (int f = 0; f < 2; ++f) {

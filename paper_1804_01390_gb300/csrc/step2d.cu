@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kLThreads)
         sy[k] = sgy[i];
     }
     __syncthreads();
-    if (!mbar_wait(&bar, 0, a.err, 2)) return;
+    if (!__syncthreads_and(mbar_wait(&bar, 0, a.err, 2))) return;
 
     const T ih = T(1.0 / a.h), ih2 = T(1.0 / (a.h * a.h)), i2h = T(0.5 / a.h);
     const T cl[4] = {T(a.dt / 4.0), T(a.dt / 3.0), T(a.dt / 2.0), T(a.dt)};

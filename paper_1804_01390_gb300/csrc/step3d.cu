@@ -1,21 +1,596 @@
-// 3D kernels of one RK4 step of the discrete PML system.
+// 3D kernels of one RK4 step of the discrete PML system (eq:DiscretePML, Sec. 1.1.2) on
+// sm_103a.  Same evaluation of the RK4 polynomial as the 2D kernels (closed form in the
+// layer-free region, Horner form with the full operator in the layer frame), with the
+// 7-point difference and streaming along z.
+//
+//  * k_interior3d: a CTA owns a 120-column x strip by kBY3 output rows and streams z.
+//    One warp per region row (kBY3 + 4 rows: halo 2 in y); TMA brings one z-plane box of
+//    U and V per stage; each lane keeps three planes of U, V, DU, DV in registers (z
+//    neighbours), y neighbours come from the shared-memory plane, x neighbours from
+//    shuffles.  DU/DV planes go through a 3-slot shared ring for the second difference.
+//
+//  * k_layer3d: a CTA owns an (x, y) column tile of the frame and streams z; one thread
+//    per region column (halo 4 in x and y).  The four Horner levels run pipelined in z:
+//    when input plane p arrives, level 4 produces plane p-1, level 3 plane p-2, level 2
+//    plane p-3 and level 1 (the output) plane p-4.  Own-column z neighbours live in
+//    register rings, x/y neighbours in one shared plane per level; one block barrier per
+//    plane.  Templated on the set of axes whose aux fields are active in the tile, so
+//    face tiles carry 4 fields, edge tiles 6 and corner tiles 8.
 #include "common.cuh"
 
 namespace pml {
 
-int interior3d_box_rows(int) { return 1; }
-int interior3d_tile_y() { return 16; }
-int interior3d_max_blocks_per_sm(int, bool) { return 0; }
+constexpr int kBY3 = 8;        // interior output rows per CTA
+constexpr int kStrip3 = 120;   // interior output columns per CTA (lanes 1..30)
+constexpr int kS3 = 4;         // interior TMA plane stages
 
-cudaError_t launch_interior3d(int, bool, const CUtensorMap *, const CUtensorMap *, void *, void *,
-                              const Interior3DArgs &, int, cudaStream_t)
+int interior3d_box_rows(int) { return 1; }
+int interior3d_tile_y() { return kBY3; }
+
+template <typename T>
+__device__ __forceinline__ V4<T> diff7(const V4<T> &c, const V4<T> &ym, const V4<T> &yp, const V4<T> &zm,
+                                       const V4<T> &zp)
 {
-    return cudaErrorNotSupported;
+    const T l = __shfl_up_sync(0xffffffffu, c.w, 1);
+    const T r = __shfl_down_sync(0xffffffffu, c.x, 1);
+    V4<T> o;
+    o.x = (((l + c.y) + (ym.x + yp.x)) + (zm.x + zp.x)) - T(6) * c.x;
+    o.y = (((c.x + c.z) + (ym.y + yp.y)) + (zm.y + zp.y)) - T(6) * c.y;
+    o.z = (((c.y + c.w) + (ym.z + yp.z)) + (zm.z + zp.z)) - T(6) * c.z;
+    o.w = (((c.z + r) + (ym.w + yp.w)) + (zm.w + zp.w)) - T(6) * c.w;
+    return o;
 }
 
-cudaError_t launch_layer3d(int, bool, const CUtensorMap *, void *const *, const Layer3DArgs &, cudaStream_t)
+template <typename T> struct I3 {
+    static constexpr int NW = kBY3 + 4;
+    static constexpr int ROW = 128;
+    static constexpr uint32_t FIELD = NW * ROW * sizeof(T);
+    static constexpr uint32_t STAGE = 2 * FIELD;
+    static constexpr uint32_t DPLANE = 2 * (kBY3 + 2) * ROW * sizeof(T);
+    static constexpr size_t SMEM = size_t(kS3) * STAGE + 3 * DPLANE + 128;
+};
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
+    k_interior3d(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
+                 T *__restrict__ Uo, T *__restrict__ Vo, const Interior3DArgs a)
 {
-    return cudaErrorNotSupported;
+    using C = I3<T>;
+    constexpr int ROW = C::ROW, NW = C::NW, S = kS3, DR = kBY3 + 2;
+    __shared__ __align__(8) uint64_t bars[S];
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *dbuf = reinterpret_cast<T *>(smem + S * C::STAGE);   // [3][2][DR][ROW]
+
+    const int tid = threadIdx.x, k = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmV);
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const Geom &g = a.g;
+    const int64_t xs0 = a.xr.lo & ~int64_t(3);
+    const int64_t nstrips = (a.xr.hi - xs0) / kStrip3 + 1;
+    const int64_t nty = (a.yr.hi - a.yr.lo) / kBY3 + 1;
+    const int64_t nz = a.zr.hi - a.zr.lo + 1;
+    const int64_t total = nstrips * nty * nz;
+    int64_t cur = total * blockIdx.x / gridDim.x;
+    const int64_t end = total * (blockIdx.x + 1) / gridDim.x;
+
+    const T a1 = T(a.c.a1), a2 = T(a.c.a2), a3 = T(a.c.a3), a4 = T(a.c.a4), a5 = T(a.c.a5);
+    const T b1 = T(a.c.b1), b2 = T(a.c.b2), b3 = T(a.c.b3), b4 = T(a.c.b4), b5 = T(a.c.b5);
+    uint32_t use = 0;
+
+    while (cur < end) {
+        const int64_t col = cur / nz, zi = cur - col * nz;
+        const int64_t cnt = (nz - zi) < (end - cur) ? (nz - zi) : (end - cur);
+        const int64_t s = col / nty, t = col - s * nty;
+        const int64_t xs = xs0 + kStrip3 * s, y0 = a.yr.lo + kBY3 * t, z0 = a.zr.lo + zi;
+        const int n_in = int(cnt) + 4;
+        const int32_t tx = int32_t(xs - 4 + G), ty = int32_t(y0 - 2 + G), tz = int32_t(z0 - 2 + G);
+
+        if (tid == 0) {
+            fence_proxy_async();
+            const int npro = n_in < S ? n_in : S;
+            for (int p = 0; p < npro; ++p) {
+                const int st = (use + p) % S;
+                unsigned char *dst = smem + st * C::STAGE;
+                mbar_arrive_expect_tx(&bars[st], C::STAGE);
+                tma_load_3d(dst, &tmU, tx, ty, tz + p, &bars[st]);
+                tma_load_3d(dst + C::FIELD, &tmV, tx, ty, tz + p, &bars[st]);
+            }
+        }
+
+        const int64_t x0 = xs - 4 + 4 * lane;
+        const int64_t y = y0 - 2 + k;
+        const bool out_lane = lane >= 1 && lane <= 30;
+        const bool full_vec = out_lane && x0 >= a.xr.lo && x0 + 3 <= a.xr.hi && x0 >= G && x0 + 3 < g.T[0] - G;
+        const bool d_row = k >= 1 && k <= kBY3 + 2;
+        const bool o_row = k >= 2 && k <= kBY3 + 1 && y <= a.yr.hi;
+        V4<T> u[3], v[3], du[3], dv[3];
+        bool ok = true;
+
+        for (int p0 = 0; p0 < n_in && ok; p0 += 3) {
+#pragma unroll
+            for (int PH = 0; PH < 3; ++PH) {
+                const int p = p0 + PH;
+                if (p < n_in && ok) {
+                    const uint32_t uu = use + p;
+                    const int st = uu % S;
+                    if (!mbar_wait(&bars[st], (uu / S) & 1u, a.err, 3)) {
+                        ok = false;
+                    } else {
+                        const T *sU = reinterpret_cast<const T *>(smem + st * C::STAGE);
+                        const T *sV = sU + NW * ROW;
+                        u[PH] = lds4(sU + k * ROW + 4 * lane);
+                        v[PH] = lds4(sV + k * ROW + 4 * lane);
+                        const int J1 = (PH + 2) % 3, J2 = (PH + 1) % 3;   // planes p-1, p-2
+                        if (p >= 2 && d_row) {
+                            const int sp = (use + p - 1) % S;
+                            const T *pU = reinterpret_cast<const T *>(smem + sp * C::STAGE);
+                            const T *pV = pU + NW * ROW;
+                            du[J1] = diff7(u[J1], lds4(pU + (k - 1) * ROW + 4 * lane), lds4(pU + (k + 1) * ROW + 4 * lane),
+                                           u[J2], u[PH]);
+                            dv[J1] = diff7(v[J1], lds4(pV + (k - 1) * ROW + 4 * lane), lds4(pV + (k + 1) * ROW + 4 * lane),
+                                           v[J2], v[PH]);
+                            T *db = dbuf + size_t((p - 1) % 3) * 2 * DR * ROW;
+                            stg4(db + (k - 1) * ROW + 4 * lane, du[J1]);
+                            stg4(db + DR * ROW + (k - 1) * ROW + 4 * lane, dv[J1]);
+                        }
+                    }
+                }
+                ok = __syncthreads_and(ok);
+                if (p < n_in && ok) {
+                    if (tid == 0 && p >= 1 && p - 1 + S < n_in) {
+                        fence_proxy_async();
+                        const int st2 = (use + p - 1) % S;
+                        unsigned char *dst = smem + st2 * C::STAGE;
+                        mbar_arrive_expect_tx(&bars[st2], C::STAGE);
+                        tma_load_3d(dst, &tmU, tx, ty, tz + p - 1 + S, &bars[st2]);
+                        tma_load_3d(dst + C::FIELD, &tmV, tx, ty, tz + p - 1 + S, &bars[st2]);
+                    }
+                    if (p >= 4 && o_row) {
+                        const int J1 = (PH + 2) % 3, J2 = (PH + 1) % 3;
+                        const T *db = dbuf + size_t((p - 2) % 3) * 2 * DR * ROW;
+                        const V4<T> d2u = diff7(du[J2], lds4(db + (k - 2) * ROW + 4 * lane), lds4(db + k * ROW + 4 * lane),
+                                                du[PH], du[J1]);
+                        const V4<T> d2v = diff7(dv[J2], lds4(db + DR * ROW + (k - 2) * ROW + 4 * lane),
+                                                lds4(db + DR * ROW + k * ROW + 4 * lane), dv[PH], dv[J1]);
+                        const V4<T> &uc = u[J2], &vc = v[J2], &duc = du[J2], &dvc = dv[J2];
+                        V4<T> uo, vo;
+#define PML_OUT(q)                                                                            \
+    if (!ADJ) {                                                                               \
+        uo.q = uc.q + (a1 * vc.q + (a2 * duc.q + (a3 * dvc.q + a4 * d2u.q)));                \
+        vo.q = vc.q + (b2 * duc.q + (b3 * dvc.q + (b4 * d2u.q + b5 * d2v.q)));               \
+    } else {                                                                                  \
+        uo.q = uc.q + (a2 * duc.q + (a3 * dvc.q + (a4 * d2u.q + a5 * d2v.q)));               \
+        vo.q = vc.q + (b1 * uc.q + (b2 * duc.q + (b3 * dvc.q + b5 * d2v.q)));                \
+    }
+                        PML_OUT(x) PML_OUT(y) PML_OUT(z) PML_OUT(w)
+#undef PML_OUT
+                        const int64_t z = z0 + p - 4;
+                        if (full_vec && y >= G && y < g.T[1] - G && z >= G && z < g.T[2] - G) {
+                            const int64_t off = g.origin + z * g.PS + y * g.P + x0;
+                            stg4(Uo + off, uo);
+                            stg4(Vo + off, vo);
+                        } else if (out_lane) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int64_t x = x0 + q;
+                                if (x >= a.xr.lo && x <= a.xr.hi) {
+                                    store_wrapped(Uo, g, x, y, z, get4(uo, q));
+                                    store_wrapped(Vo, g, x, y, z, get4(vo, q));
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!ok) return;
+        use += n_in;
+        cur += cnt;
+    }
+}
+
+template <typename T, bool ADJ> static cudaError_t prep_interior3d()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_interior3d<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(I3<T>::SMEM));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <typename T, bool ADJ> static int occ_interior3d()
+{
+    if (prep_interior3d<T, ADJ>() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior3d<T, ADJ>, 32 * (kBY3 + 4), I3<T>::SMEM) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+int interior3d_max_blocks_per_sm(int prec, bool adjoint)
+{
+    if (prec == 32) return adjoint ? occ_interior3d<float, true>() : occ_interior3d<float, false>();
+    return adjoint ? occ_interior3d<double, true>() : occ_interior3d<double, false>();
+}
+
+cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                              void *Uo, void *Vo, const Interior3DArgs &a, int grid, cudaStream_t st)
+{
+    if (a.xr.lo > a.xr.hi || a.yr.lo > a.yr.hi || a.zr.lo > a.zr.hi || grid <= 0) return cudaSuccess;
+    cudaError_t e;
+    const int threads = 32 * (kBY3 + 4);
+#define PML_LAUNCH(TT, AA)                                                                              \
+    if ((e = prep_interior3d<TT, AA>()) != cudaSuccess) return e;                                       \
+    k_interior3d<TT, AA><<<grid, threads, I3<TT>::SMEM, st>>>(*tmU, *tmV, (TT *)Uo, (TT *)Vo, a);
+    if (prec == 32) {
+        if (adjoint) { PML_LAUNCH(float, true) } else { PML_LAUNCH(float, false) }
+    } else {
+        if (adjoint) { PML_LAUNCH(double, true) } else { PML_LAUNCH(double, false) }
+    }
+#undef PML_LAUNCH
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// layer frame, z-streaming Horner pipeline
+// ------------------------------------------------------------------------------------
+
+template <typename T> struct L3 {
+    // region (x, y) = tile + halo 4 on each side; one thread per region column
+    static constexpr int RX = sizeof(T) == 4 ? kLayer3TXf + 8 : kLayer3TXd + 8;
+    static constexpr int RY = sizeof(T) == 4 ? kLayer3TYf + 8 : kLayer3TYd + 8;
+    static constexpr int PL = RX * RY;
+    static constexpr int S = 6;   // resident planes p-4..p plus one in flight
+};
+
+template <int MASK> struct Fields {
+    static constexpr int NAX = ((MASK >> 0) & 1) + ((MASK >> 1) & 1) + ((MASK >> 2) & 1);
+    static constexpr int NF = 2 + 2 * NAX;
+    // global field id of local field f (0 U, 1 V, then Phi/Psi of the active axes)
+    static __device__ __forceinline__ constexpr int gid(int f)
+    {
+        if (f < 2) return f;
+        int k = (f - 2) >> 1, ax = 0;
+        for (int a = 0; a < 3; ++a)
+            if ((MASK >> a) & 1) {
+                if (k == 0) { ax = a; break; }
+                --k;
+            }
+        return 2 + 2 * ax + ((f - 2) & 1);
+    }
+    static __device__ __forceinline__ constexpr int axis(int k)   // k-th active axis
+    {
+        for (int a = 0; a < 3; ++a)
+            if ((MASK >> a) & 1) {
+                if (k == 0) return a;
+                --k;
+            }
+        return 0;
+    }
+};
+
+template <typename T> struct Sig3 {
+    T si[3], sm[3];   // sigma_a[i_a], sigma_a[i_a - 1]
+};
+
+// A z (or A^T z) at one vertex; N(f, d) returns local field f at direction d:
+// 0 centre, 1 x-, 2 x+, 3 y-, 4 y+, 5 z-, 6 z+.
+template <typename T, bool ADJ, int MASK, typename Get>
+__device__ __forceinline__ void apply_A3(const Get &N, const Sig3<T> &s, T ih, T ih2, T i2h, T *o)
+{
+    using F = Fields<MASK>;
+    const T half = T(0.5);
+    if (!ADJ) {
+        const T U0 = N(0, 0);
+        const T lap = (((N(0, 2) + N(0, 1)) - T(2) * U0) + ((N(0, 4) + N(0, 3)) - T(2) * U0)) +
+                      ((N(0, 6) + N(0, 5)) - T(2) * U0);
+        T aV = lap * ih2;
+        o[0] = N(1, 0);
+#pragma unroll
+        for (int k = 0; k < F::NAX; ++k) {
+            const int ax = F::axis(k), fp = 2 + 2 * k, fq = 3 + 2 * k, dm = 1 + 2 * ax, dp = 2 + 2 * ax;
+            const T si = s.si[ax], sm = s.sm[ax];
+            aV += (si * N(fq, dp) - sm * N(fp, dm)) * ih;
+            const T dU = (N(0, dp) - N(0, dm)) * i2h;
+            o[fp] = si != T(0) ? -half * (sm * N(fp, dm) + si * N(fp, 0)) - dU : T(0);
+            o[fq] = sm != T(0) ? -half * (sm * N(fq, 0) + si * N(fq, dp)) - dU : T(0);
+        }
+        o[1] = aV;
+    } else {
+        const T V0 = N(1, 0);
+        const T lap = (((N(1, 2) + N(1, 1)) - T(2) * V0) + ((N(1, 4) + N(1, 3)) - T(2) * V0)) +
+                      ((N(1, 6) + N(1, 5)) - T(2) * V0);
+        T aU = lap * ih2;
+        o[1] = N(0, 0);
+#pragma unroll
+        for (int k = 0; k < F::NAX; ++k) {
+            const int ax = F::axis(k), fp = 2 + 2 * k, fq = 3 + 2 * k, dm = 1 + 2 * ax, dp = 2 + 2 * ax;
+            const T si = s.si[ax], sm = s.sm[ax];
+            aU += ((N(fp, dp) - N(fp, dm)) + (N(fq, dp) - N(fq, dm))) * i2h;
+            o[fp] = si != T(0) ? -si * N(1, dp) * ih - half * si * (N(fp, dp) + N(fp, 0)) : T(0);
+            o[fq] = sm != T(0) ? sm * N(1, dm) * ih - half * sm * (N(fq, 0) + N(fq, dm)) : T(0);
+        }
+        o[0] = aU;
+    }
+}
+
+struct Maps8 {
+    CUtensorMap m[8];
+};
+struct Out8 {
+    void *p[8];
+};
+
+template <typename T, int MASK>
+__device__ __forceinline__ void issue_plane3(T *stage_base, const Maps8 &maps, const LayerTile &tile, int64_t zin,
+                                             const Geom &g, uint64_t *bar)
+{
+    using F = Fields<MASK>;
+    constexpr int PL = L3<T>::PL;
+    int64_t z = zin % g.T[2];
+    if (z < 0) z += g.T[2];
+    mbar_arrive_expect_tx(bar, uint32_t(F::NF * PL * sizeof(T)));
+#pragma unroll
+    for (int f = 0; f < F::NF; ++f)
+        tma_load_3d(stage_base + f * PL, &maps.m[F::gid(f)], tile.x0 - 4 + G, tile.y0 - 4 + G, int32_t(z + G), bar);
+}
+
+template <typename T, bool ADJ, int MASK>
+__global__ void __launch_bounds__(L3<T>::PL, 1)
+    k_layer3d(const __grid_constant__ Maps8 maps, const Out8 out, const Layer3DArgs a, int tile_base)
+{
+    using F = Fields<MASK>;
+    constexpr int NF = F::NF, RX = L3<T>::RX, RY = L3<T>::RY, PL = L3<T>::PL, S = L3<T>::S;
+    extern __shared__ unsigned char smem_dyn[];
+    T *stage = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *Zb = stage + S * NF * PL;   // [3 levels][2 slots][NF][PL]
+    __shared__ T sx[RX + 1], sy[RY + 1];
+    __shared__ __align__(8) uint64_t bars[S];
+
+    const LayerTile tile = a.tiles[tile_base + blockIdx.x];
+    const Geom &g = a.g;
+    const int tid = threadIdx.x, cx = tid % RX, cy = tid / RX;
+    const int nout = tile.zhi - tile.zlo + 1;
+    const int nin = nout + 8;
+    const int64_t zin0 = int64_t(tile.zlo) - 4;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        const int npro = nin < S ? nin : S;
+        for (int p = 0; p < npro; ++p) issue_plane3<T, MASK>(stage + p * NF * PL, maps, tile, zin0 + p, g, &bars[p]);
+    }
+    const T *sgx = static_cast<const T *>(a.sig[0]);
+    const T *sgy = static_cast<const T *>(a.sig[1]);
+    const T *sgz = static_cast<const T *>(a.sig[2]);
+    for (int k = tid; k <= RX; k += PL) {
+        int64_t i = (int64_t(tile.x0) - 5 + k) % g.T[0];
+        if (i < 0) i += g.T[0];
+        sx[k] = sgx[i];
+    }
+    for (int k = tid; k <= RY; k += PL) {
+        int64_t i = (int64_t(tile.y0) - 5 + k) % g.T[1];
+        if (i < 0) i += g.T[1];
+        sy[k] = sgy[i];
+    }
+    __syncthreads();
+
+    const T ih = T(1.0 / a.h), ih2 = T(1.0 / (a.h * a.h)), i2h = T(0.5 / a.h);
+    const T c4 = T(a.dt / 4.0), c3 = T(a.dt / 3.0), c2 = T(a.dt / 2.0), c1 = T(a.dt);
+    T z4r[3][NF], z3r[3][NF], z2r[3][NF];
+    Sig3<T> sg;
+    sg.si[0] = sx[cx + 1];
+    sg.sm[0] = sx[cx];
+    sg.si[1] = sy[cy + 1];
+    sg.sm[1] = sy[cy];
+    auto zsig = [&](int64_t zl, Sig3<T> &s) {
+        int64_t z = zl % g.T[2];
+        if (z < 0) z += g.T[2];
+        s.si[2] = sgz[z];
+        s.sm[2] = sgz[z == 0 ? g.T[2] - 1 : z - 1];
+    };
+    const bool v4 = cx >= 1 && cx <= RX - 2 && cy >= 1 && cy <= RY - 2;
+    const bool v3 = cx >= 2 && cx <= RX - 3 && cy >= 2 && cy <= RY - 3;
+    const bool v2 = cx >= 3 && cx <= RX - 4 && cy >= 3 && cy <= RY - 4;
+    const bool v1 = cx >= 4 && cx <= RX - 5 && cy >= 4 && cy <= RY - 5;
+    const int64_t gx = int64_t(tile.x0) - 4 + cx, gy = int64_t(tile.y0) - 4 + cy;
+    const bool in_rect = v1 && gx >= tile.xlo && gx <= tile.xhi && gy >= tile.ylo && gy <= tile.yhi;
+
+    bool ok = true;
+    for (int p0 = 0; p0 < nin && ok; p0 += 3) {
+#pragma unroll
+        for (int PH = 0; PH < 3; ++PH) {
+            const int p = p0 + PH;
+            if (p < nin) {
+                if (!mbar_wait(&bars[p % S], (p / S) & 1, a.err, 4)) ok = false;
+                if (ok) {
+                    // level 4 at plane q = p-1 from the input planes in the stage ring
+                    if (p >= 2 && v4) {
+                        const int q = p - 1;
+                        const T *Pc = stage + (q % S) * NF * PL, *Pm = stage + ((q - 1) % S) * NF * PL,
+                                *Pp = stage + (p % S) * NF * PL;
+                        auto N = [&](int f, int d) -> T {
+                            const int o = f * PL + tid;
+                            switch (d) {
+                            case 0: return Pc[o];
+                            case 1: return Pc[o - 1];
+                            case 2: return Pc[o + 1];
+                            case 3: return Pc[o - RX];
+                            case 4: return Pc[o + RX];
+                            case 5: return Pm[o];
+                            default: return Pp[o];
+                            }
+                        };
+                        zsig(zin0 + q, sg);
+                        T r[NF];
+                        apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+                        T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PL;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const T val = Pc[f * PL + tid] + c4 * r[f];
+                            z4r[(PH + 2) % 3][f] = val;
+                            zb[f * PL + tid] = val;
+                        }
+                    }
+                    // level 3 at plane q = p-2 (z neighbours: own ring; x/y: level-4 plane)
+                    if (p >= 4 && v3) {
+                        const int q = p - 2;
+                        const T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PL;
+                        auto N = [&](int f, int d) -> T {
+                            switch (d) {
+                            case 0: return z4r[(PH + 1) % 3][f];
+                            case 1: return zb[f * PL + tid - 1];
+                            case 2: return zb[f * PL + tid + 1];
+                            case 3: return zb[f * PL + tid - RX];
+                            case 4: return zb[f * PL + tid + RX];
+                            case 5: return z4r[PH][f];
+                            default: return z4r[(PH + 2) % 3][f];
+                            }
+                        };
+                        zsig(zin0 + q, sg);
+                        T r[NF];
+                        apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+                        const T *Y = stage + (q % S) * NF * PL;
+                        T *zo = Zb + ((1 * 2 + (q & 1)) * NF) * PL;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const T val = Y[f * PL + tid] + c3 * r[f];
+                            z3r[(PH + 1) % 3][f] = val;
+                            zo[f * PL + tid] = val;
+                        }
+                    }
+                    // level 2 at plane q = p-3
+                    if (p >= 6 && v2) {
+                        const int q = p - 3;
+                        const T *zb = Zb + ((1 * 2 + (q & 1)) * NF) * PL;
+                        auto N = [&](int f, int d) -> T {
+                            switch (d) {
+                            case 0: return z3r[PH][f];
+                            case 1: return zb[f * PL + tid - 1];
+                            case 2: return zb[f * PL + tid + 1];
+                            case 3: return zb[f * PL + tid - RX];
+                            case 4: return zb[f * PL + tid + RX];
+                            case 5: return z3r[(PH + 2) % 3][f];
+                            default: return z3r[(PH + 1) % 3][f];
+                            }
+                        };
+                        zsig(zin0 + q, sg);
+                        T r[NF];
+                        apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+                        const T *Y = stage + (q % S) * NF * PL;
+                        T *zo = Zb + ((2 * 2 + (q & 1)) * NF) * PL;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const T val = Y[f * PL + tid] + c2 * r[f];
+                            z2r[PH][f] = val;
+                            zo[f * PL + tid] = val;
+                        }
+                    }
+                    // level 1 (output) at plane q = p-4
+                    if (p >= 8 && in_rect) {
+                        const int q = p - 4;
+                        const T *zb = Zb + ((2 * 2 + (q & 1)) * NF) * PL;
+                        auto N = [&](int f, int d) -> T {
+                            switch (d) {
+                            case 0: return z2r[(PH + 2) % 3][f];
+                            case 1: return zb[f * PL + tid - 1];
+                            case 2: return zb[f * PL + tid + 1];
+                            case 3: return zb[f * PL + tid - RX];
+                            case 4: return zb[f * PL + tid + RX];
+                            case 5: return z2r[(PH + 1) % 3][f];
+                            default: return z2r[PH][f];
+                            }
+                        };
+                        const int64_t zl = zin0 + q;
+                        zsig(zl, sg);
+                        T r[NF];
+                        apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+                        const T *Y = stage + (q % S) * NF * PL;
+                        int64_t z = zl % g.T[2];
+                        if (z < 0) z += g.T[2];
+                        const bool edge = near_edge(g, gx, gy, z);
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const T val = Y[f * PL + tid] + c1 * r[f];
+                            T *dst = static_cast<T *>(out.p[F::gid(f)]);
+                            if (edge) store_wrapped(dst, g, gx, gy, z, val);
+                            else dst[g.origin + gx + gy * g.P + z * g.PS] = val;
+                        }
+                    }
+                }
+            }
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            if (p < nin && tid == 0 && p >= 4 && p - 4 + S < nin) {
+                fence_proxy_async();
+                const int st = (p - 4) % S;
+                issue_plane3<T, MASK>(stage + st * NF * PL, maps, tile, zin0 + p - 4 + S, g, &bars[st]);
+            }
+        }
+    }
+}
+
+template <typename T, int MASK> static size_t layer3d_smem()
+{
+    return (size_t(L3<T>::S) + 6) * Fields<MASK>::NF * L3<T>::PL * sizeof(T) + 128;
+}
+
+template <typename T, bool ADJ, int MASK>
+static cudaError_t launch_l3(const Maps8 &m, const Out8 &o, const Layer3DArgs &a, cudaStream_t st)
+{
+    const int n = a.class_off[MASK + 1] - a.class_off[MASK];
+    if (n <= 0) return cudaSuccess;
+    static bool done = false;
+    const size_t sm = layer3d_smem<T, MASK>();
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_layer3d<T, ADJ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    k_layer3d<T, ADJ, MASK><<<n, L3<T>::PL, sm, st>>>(m, o, a, a.class_off[MASK]);
+    return cudaGetLastError();
+}
+
+template <typename T, bool ADJ>
+static cudaError_t launch_l3_all(const Maps8 &m, const Out8 &o, const Layer3DArgs &a, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = launch_l3<T, ADJ, 0>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 1>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 2>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 3>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 4>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 5>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 6>(m, o, a, st)) != cudaSuccess) return e;
+    return launch_l3<T, ADJ, 7>(m, o, a, st);
+}
+
+int layer3d_tile_x(int prec) { return prec == 32 ? kLayer3TXf : kLayer3TXd; }
+int layer3d_tile_y(int prec) { return prec == 32 ? kLayer3TYf : kLayer3TYd; }
+
+cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp, const Layer3DArgs &a,
+                           cudaStream_t st)
+{
+    if (a.ntiles <= 0) return cudaSuccess;
+    Maps8 m;
+    Out8 o;
+    for (int f = 0; f < 8; ++f) {
+        m.m[f] = tm[f];
+        o.p[f] = outp[f];
+    }
+    if (prec == 32) return adjoint ? launch_l3_all<float, true>(m, o, a, st) : launch_l3_all<float, false>(m, o, a, st);
+    return adjoint ? launch_l3_all<double, true>(m, o, a, st) : launch_l3_all<double, false>(m, o, a, st);
 }
 
 }  // namespace pml

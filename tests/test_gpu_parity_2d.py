@@ -102,8 +102,13 @@ def test_cfg1_full_fp64_and_fp32():
         for f in range(6):
             assert rel_l2(got200[f], want200[f]) <= TOL[prec], (prec, f, rel_l2(got200[f], want200[f]))
         if prec == 64:
+            # by step 1000 the pulse has left the box: the remaining field is ~1e-10 of the
+            # initial one, so the error is measured against the initial field's norm
+            n0 = np.linalg.norm(u0)
             for f in range(6):
-                assert rel_l2(got[f], want[f]) <= TOL[64], (f, rel_l2(got[f], want[f]))
+                diff = np.linalg.norm(got[f].reshape(-1) - want[f].reshape(-1))
+                assert diff <= TOL[64] * n0, (f, diff / n0)
+                assert rel_l2(got[f], want[f]) <= 1e-10, (f, rel_l2(got[f], want[f]))
         else:
             # after 1000 steps the field has left the box (max |U| ~ 1e-4 of the start);
             # the absolute error stays at FP32 rounding of the initial amplitude
