@@ -127,9 +127,9 @@ def max_over_ranks(x, ws, device=None):
 # measurements
 # ------------------------------------------------------------------------------------
 
-def _workload():
+def _workload(n=None):
     from paper_1804_01390_gb300 import workloads as wk
-    return wk.cfg2()
+    return wk.cfg2() if n is None else wk.cfg2(N=n)
 
 
 def timed_steps(solver, steps, warmup, ws, profile=False):
@@ -166,7 +166,7 @@ def run_ours(args, ws, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    wl = _workload()
+    wl = _workload(args.n)
     pts = wl.points
     u0 = wk.initial_field(wl, dtype=np.float32)
     K, W = args.steps, args.warmup
@@ -271,8 +271,9 @@ def run_ours(args, ws, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "2D 8192^2 interior + 32-cell quadratic PML (T = 8256^2), 16 seeded "
-                                   "Gaussian pulses, RK4 dt = 0.5h", "grid": list(wl.T), "pml_width": wl.w,
+            "config": {"workload": "2D %d^2 interior + 32-cell quadratic PML (T = %d^2), 16 seeded "
+                                   "Gaussian pulses, RK4 dt = 0.5h" % (wl.N[0], wl.T[0]), "grid": list(wl.T),
+                       "pml_width": wl.w,
                        "l2": "inputs larger than L2 (U and V are 272 MB each; 1.09 GB state read + written "
                              "per step)", "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -355,6 +356,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--n", type=int, default=None,
+                    help="physical domain side (default 8192); smaller values are for profiling runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -232,11 +232,14 @@ struct Layer2DArgs {
     Geom g;
     double dt, h;
     const void *sig[2];        // device sigma per axis (context precision), length T[a]
-    const LayerTile *tiles;
+    const LayerTile *tiles;    // sorted by flags (set of axes with active aux fields)
     int ntiles;
+    int class_off[9];          // tiles of flags m are [class_off[m], class_off[m+1])
     DeviceError *err;
 };
-constexpr int kLayerTH = 16, kLayerTW = 32;  // 2D layer tile (output) size
+// 2D layer work items: 24 output columns (one warp, halo 4 lanes per side) by at most
+// kLayer2LY output rows of one frame rectangle
+constexpr int kLayerTW = 24, kLayer2LY = 256;
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U,V,Px,Qx,Py,Qy*/,
                            void *const *out /*[6]*/, const Layer2DArgs &a, cudaStream_t st);
 

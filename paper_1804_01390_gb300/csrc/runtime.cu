@@ -62,7 +62,7 @@ Geom make_geom(int nd, const int64_t T[3])
 size_t tile_bound(int nd, int prec, const int64_t T[3])
 {
     if (nd == 2)
-        return size_t(4) * size_t(T[0] / kLayerTW + 2) * size_t(T[1] / kLayerTH + 2);
+        return size_t(4) * size_t(T[0] / kLayerTW + 2) * size_t(T[1] / kLayer2LY + 2);
     const int TX = prec == 32 ? kLayer3TXf : kLayer3TXd, TY = prec == 32 ? kLayer3TYf : kLayer3TYd;
     return size_t(5) * size_t(T[0] / TX + 2) * size_t(T[1] / TY + 2) * size_t(T[2] / kLayer3LZ + 2);
 }
@@ -317,7 +317,7 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
     std::vector<LayerTile> t;
     const bool d3 = c->nd == 3;
     const int TX = d3 ? layer3d_tile_x(c->prec) : kLayerTW;
-    const int TY = d3 ? layer3d_tile_y(c->prec) : kLayerTH;
+    const int TY = d3 ? layer3d_tile_y(c->prec) : kLayer2LY;
     const int TZ = d3 ? kLayer3LZ : 1;
     for (const Rect &r : frame_rects(c, ir)) {
         for (int64_t z0 = r.lo[2]; z0 <= r.hi[2]; z0 += TZ)
@@ -328,10 +328,13 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
                     L.xlo = int32_t(r.lo[0]); L.xhi = int32_t(r.hi[0]);
                     L.ylo = int32_t(r.lo[1]); L.yhi = int32_t(r.hi[1]);
                     L.zlo = int32_t(z0); L.zhi = int32_t(std::min<int64_t>(z0 + TZ - 1, r.hi[2]));
-                    if (!d3) { L.zlo = 0; L.zhi = 0; }
+                    if (!d3) {   // 2D: a run of at most kLayer2LY rows streamed by one warp
+                        L.zlo = 0; L.zhi = 0;
+                        L.ylo = int32_t(y0); L.yhi = int32_t(std::min<int64_t>(y0 + TY - 1, r.hi[1]));
+                    }
                     int fl = 0;
                     if (axis_active(c, 0, x0 - 4, x0 + TX + 4)) fl |= 1;
-                    if (axis_active(c, 1, y0 - 4, y0 + TY + 4)) fl |= 2;
+                    if (axis_active(c, 1, L.ylo - 4, (d3 ? y0 + TY : L.yhi + 1) + 4)) fl |= 2;
                     if (d3 && axis_active(c, 2, L.zlo - 4, L.zhi + 5)) fl |= 4;
                     L.flags = fl;
                     t.push_back(L);
@@ -475,6 +478,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         l.sig[0] = c->dsig[0]; l.sig[1] = c->dsig[1];
         l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
+        for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
         l.err = c->derr;
         pi = prof_begin(c, 1);
         e = launch_layer2d(c->prec, adjoint, tl, out, l, c->st);
@@ -643,7 +647,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         uint32_t box_int[3], box_lay[3];
         if (c->nd == 2) {
             box_int[0] = 128; box_int[1] = uint32_t(interior2d_box_rows(precision)); box_int[2] = 1;
-            box_lay[0] = kLayerTW + 8; box_lay[1] = kLayerTH + 8; box_lay[2] = 1;
+            box_lay[0] = 32; box_lay[1] = 6; box_lay[2] = 1;   // one warp's 32 columns x 6 rows
         } else {
             box_int[0] = 128; box_int[1] = uint32_t(interior3d_tile_y() + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
             box_lay[0] = uint32_t(layer3d_tile_x(precision) + 8); box_lay[1] = uint32_t(layer3d_tile_y(precision) + 8);

@@ -248,213 +248,309 @@ cudaError_t launch_interior2d(int prec, bool adjoint, const CUtensorMap *tmU, co
 }
 
 // ------------------------------------------------------------------------------------
-// Layer frame: Horner form with the full operator of Eq. 3 (or its transpose).
+// Layer frame: Horner form with the full operator of Eq. 3 (or its transpose), streamed
+// down the rows by independent warps.
+//
+// A warp owns 32 consecutive columns (lane = column; lanes 4..27 are its kL2W outputs,
+// lanes 0..3 and 28..31 the halo of the four applications of A) and a run of rows of one
+// frame rectangle.  When input row p arrives, level 4 (z4 = y + dt/4 A y) produces row
+// p-1, level 3 row p-2, level 2 row p-3 and level 1 (y' = y + dt A z2) the output row
+// p-4.  Row neighbours of each level come from three-row register rings, column
+// neighbours from shuffles, the base y of every level from the warp's TMA ring; no block
+// barrier is needed.  Templated on the axes whose aux fields are active in the strip.
 // ------------------------------------------------------------------------------------
 
-constexpr int kLR = kLayerTH + 8;   // region rows (halo 4 = one per application of A)
-constexpr int kLC = kLayerTW + 8;   // region columns
-constexpr int kLN = kLR * kLC;
-constexpr int kLThreads = 256;
-constexpr int kLPts = (kLN + kLThreads - 1) / kLThreads;
+constexpr int kL2CH = 6;     // rows per TMA box (multiple of 3: the register ring period)
+constexpr int kL2S = 4;      // TMA stages per warp
 
+template <int MASK> struct Fields2 {
+    static constexpr int NAX = ((MASK >> 0) & 1) + ((MASK >> 1) & 1);
+    static constexpr int NF = 2 + 2 * NAX;
+    static __device__ __forceinline__ constexpr int axis(int k)
+    {
+        return (MASK & 1) ? k : 1;   // k-th active axis
+    }
+    static __device__ __forceinline__ constexpr int gid(int f)
+    {
+        return f < 2 ? f : 2 + 2 * axis((f - 2) >> 1) + ((f - 2) & 1);
+    }
+};
+
+template <typename T> struct Sig2 {
+    T si[2], sm[2];   // sigma_a[i_a], sigma_a[i_a - 1]
+};
+
+// A z (or A^T z) at one vertex; N(f, d): d = 0 centre, 1 x-, 2 x+, 3 y-, 4 y+.
+template <typename T, bool ADJ, int MASK, typename Get>
+__device__ __forceinline__ void apply_A2(const Get &N, const Sig2<T> &s, T ih, T ih2, T i2h, T *o)
+{
+    using F = Fields2<MASK>;
+    const T half = T(0.5);
+    if (!ADJ) {
+        const T U0 = N(0, 0);
+        const T lap = ((N(0, 2) + N(0, 1)) - T(2) * U0) + ((N(0, 4) + N(0, 3)) - T(2) * U0);
+        T aV = lap * ih2;
+        o[0] = N(1, 0);
+#pragma unroll
+        for (int k = 0; k < F::NAX; ++k) {
+            const int ax = F::axis(k), fp = 2 + 2 * k, fq = 3 + 2 * k, dm = 1 + 2 * ax, dp = 2 + 2 * ax;
+            const T si = s.si[ax], sm = s.sm[ax];
+            aV += (si * N(fq, dp) - sm * N(fp, dm)) * ih;
+            const T dU = (N(0, dp) - N(0, dm)) * i2h;
+            o[fp] = si != T(0) ? -half * (sm * N(fp, dm) + si * N(fp, 0)) - dU : T(0);
+            o[fq] = sm != T(0) ? -half * (sm * N(fq, 0) + si * N(fq, dp)) - dU : T(0);
+        }
+        o[1] = aV;
+    } else {
+        const T V0 = N(1, 0);
+        const T lap = ((N(1, 2) + N(1, 1)) - T(2) * V0) + ((N(1, 4) + N(1, 3)) - T(2) * V0);
+        T aU = lap * ih2;
+        o[1] = N(0, 0);
+#pragma unroll
+        for (int k = 0; k < F::NAX; ++k) {
+            const int ax = F::axis(k), fp = 2 + 2 * k, fq = 3 + 2 * k, dm = 1 + 2 * ax, dp = 2 + 2 * ax;
+            const T si = s.si[ax], sm = s.sm[ax];
+            aU += ((N(fp, dp) - N(fp, dm)) + (N(fq, dp) - N(fq, dm))) * i2h;
+            o[fp] = si != T(0) ? -si * N(1, dp) * ih - half * si * (N(fp, dp) + N(fp, 0)) : T(0);
+            o[fq] = sm != T(0) ? sm * N(1, dm) * ih - half * sm * (N(fq, 0) + N(fq, dm)) : T(0);
+        }
+        o[0] = aU;
+    }
+}
+
+struct Maps6 {
+    CUtensorMap m[6];
+};
 struct Out6 {
     void *p[6];
 };
 
-// Field order in shared memory and in the tensor maps: U, V, Phi_x, Psi_x, Phi_y, Psi_y.
-template <typename T, bool ADJ>
-__device__ __forceinline__ void apply_A2(const T *__restrict__ Z, const T *sx, const T *sy, int r,
-                                         int c, bool ax, bool ay, T ih, T ih2, T i2h, T o[6])
+template <typename T, int MASK>
+__device__ __forceinline__ void issue_chunk2(T *dst, const Maps6 &maps, int32_t x, int32_t y, uint64_t *bar)
 {
-#define F(f, rr, cc) Z[(f) * kLN + (rr) * kLC + (cc)]
-    const T half = T(0.5);
-    if (!ADJ) {
-        const T zU = F(0, r, c);
-        const T lap = ((F(0, r, c + 1) + F(0, r, c - 1)) - T(2) * zU) +
-                      ((F(0, r + 1, c) + F(0, r - 1, c)) - T(2) * zU);
-        T aV = lap * ih2;
-        o[0] = F(1, r, c);
-        if (ax) {
-            const T si = sx[c + 1], sm = sx[c];
-            aV += (si * F(3, r, c + 1) - sm * F(2, r, c - 1)) * ih;
-            const T dU = (F(0, r, c + 1) - F(0, r, c - 1)) * i2h;
-            o[2] = si != T(0) ? -half * (sm * F(2, r, c - 1) + si * F(2, r, c)) - dU : T(0);
-            o[3] = sm != T(0) ? -half * (sm * F(3, r, c) + si * F(3, r, c + 1)) - dU : T(0);
-        }
-        if (ay) {
-            const T si = sy[r + 1], sm = sy[r];
-            aV += (si * F(5, r + 1, c) - sm * F(4, r - 1, c)) * ih;
-            const T dU = (F(0, r + 1, c) - F(0, r - 1, c)) * i2h;
-            o[4] = si != T(0) ? -half * (sm * F(4, r - 1, c) + si * F(4, r, c)) - dU : T(0);
-            o[5] = sm != T(0) ? -half * (sm * F(5, r, c) + si * F(5, r + 1, c)) - dU : T(0);
-        }
-        o[1] = aV;
-    } else {
-        // transpose of the operator above (entries collected column by column)
-        const T zV = F(1, r, c);
-        const T lap = ((F(1, r, c + 1) + F(1, r, c - 1)) - T(2) * zV) +
-                      ((F(1, r + 1, c) + F(1, r - 1, c)) - T(2) * zV);
-        T aU = lap * ih2;
-        o[1] = F(0, r, c);
-        if (ax) {
-            const T si = sx[c + 1], sm = sx[c];
-            aU += ((F(2, r, c + 1) - F(2, r, c - 1)) + (F(3, r, c + 1) - F(3, r, c - 1))) * i2h;
-            o[2] = si != T(0) ? -si * F(1, r, c + 1) * ih - half * si * (F(2, r, c + 1) + F(2, r, c)) : T(0);
-            o[3] = sm != T(0) ? sm * F(1, r, c - 1) * ih - half * sm * (F(3, r, c) + F(3, r, c - 1)) : T(0);
-        }
-        if (ay) {
-            const T si = sy[r + 1], sm = sy[r];
-            aU += ((F(4, r + 1, c) - F(4, r - 1, c)) + (F(5, r + 1, c) - F(5, r - 1, c))) * i2h;
-            o[4] = si != T(0) ? -si * F(1, r + 1, c) * ih - half * si * (F(4, r + 1, c) + F(4, r, c)) : T(0);
-            o[5] = sm != T(0) ? sm * F(1, r - 1, c) * ih - half * sm * (F(5, r, c) + F(5, r - 1, c)) : T(0);
-        }
-        o[0] = aU;
-    }
-#undef F
+    using F = Fields2<MASK>;
+    constexpr int FE = kL2CH * 32;
+    mbar_arrive_expect_tx(bar, uint32_t(F::NF * FE * sizeof(T)));
+#pragma unroll
+    for (int f = 0; f < F::NF; ++f) tma_load_2d(dst + f * FE, &maps.m[F::gid(f)], x, y, bar);
 }
 
-template <typename T, bool ADJ>
-__global__ void __launch_bounds__(kLThreads)
-    k_layer2d(const __grid_constant__ CUtensorMap t0, const __grid_constant__ CUtensorMap t1,
-              const __grid_constant__ CUtensorMap t2, const __grid_constant__ CUtensorMap t3,
-              const __grid_constant__ CUtensorMap t4, const __grid_constant__ CUtensorMap t5, const Out6 out,
-              const Layer2DArgs a)
+template <typename T, bool ADJ, int MASK>
+__global__ void __launch_bounds__(128)
+    k_layer2d(const __grid_constant__ Maps6 maps, const Out6 out, const Layer2DArgs a, int base, int count)
 {
+    using F = Fields2<MASK>;
+    constexpr int NF = F::NF, CH = kL2CH, S = kL2S, FE = CH * 32, SE = NF * FE;
+    __shared__ __align__(8) uint64_t bars[4][S];
     extern __shared__ unsigned char smem_dyn[];
-    T *Y = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
-    T *Z = Y + 6 * kLN;
-    __shared__ T sx[kLC + 1], sy[kLR + 1];
-    __shared__ __align__(8) uint64_t bar;
-
-    const LayerTile tile = a.tiles[blockIdx.x];
-    const bool ax = tile.flags & 1, ay = tile.flags & 2;
+    T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * 4 + warp;
+    if (item >= count) return;   // whole warp; the kernel has no block barrier
+    T *ring = smem + warp * S * SE;
+    const LayerTile tile = a.tiles[base + item];
     const Geom &g = a.g;
-    const int tid = threadIdx.x;
-
-    if (tid == 0) {
-        mbar_init(&bar, 1);
+    const int nout = tile.yhi - tile.ylo + 1, nin = nout + 8;
+    const int nch = (nin + CH - 1) / CH;
+    const int32_t tx = tile.x0 - 4 + G, ty = tile.ylo - 4 + G;
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
         fence_mbar_init();
-        constexpr uint32_t FB = kLN * sizeof(T);
-        const uint32_t bytes = FB * (2 + (ax ? 2 : 0) + (ay ? 2 : 0));
-        mbar_arrive_expect_tx(&bar, bytes);
-        const int32_t x = tile.x0 - 4 + G, y = tile.y0 - 4 + G;
-        tma_load_2d(Y + 0 * kLN, &t0, x, y, &bar);
-        tma_load_2d(Y + 1 * kLN, &t1, x, y, &bar);
-        if (ax) {
-            tma_load_2d(Y + 2 * kLN, &t2, x, y, &bar);
-            tma_load_2d(Y + 3 * kLN, &t3, x, y, &bar);
-        }
-        if (ay) {
-            tma_load_2d(Y + 4 * kLN, &t4, x, y, &bar);
-            tma_load_2d(Y + 5 * kLN, &t5, x, y, &bar);
-        }
+        const int npro = nch < S ? nch : S;
+        for (int c = 0; c < npro; ++c) issue_chunk2<T, MASK>(ring + c * SE, maps, tx, ty + c * CH, &bars[warp][c]);
     }
-    // damping of the edges to the left of / below each region vertex and of the vertex
+    __syncwarp();
+
     const T *sgx = static_cast<const T *>(a.sig[0]);
     const T *sgy = static_cast<const T *>(a.sig[1]);
-    for (int k = tid; k <= kLC; k += kLThreads) {
-        int64_t i = (int64_t(tile.x0) - 5 + k) % g.T[0];
-        if (i < 0) i += g.T[0];
-        sx[k] = sgx[i];
+    const int64_t gx = int64_t(tile.x0) - 4 + lane;
+    Sig2<T> sg;
+    {
+        const int64_t xi = ((gx % g.T[0]) + g.T[0]) % g.T[0];
+        sg.si[0] = sgx[xi];
+        sg.sm[0] = sgx[xi == 0 ? g.T[0] - 1 : xi - 1];
     }
-    for (int k = tid; k <= kLR; k += kLThreads) {
-        int64_t i = (int64_t(tile.y0) - 5 + k) % g.T[1];
-        if (i < 0) i += g.T[1];
-        sy[k] = sgy[i];
-    }
-    __syncthreads();
-    if (!__syncthreads_and(mbar_wait(&bar, 0, a.err, 2))) return;
-
+    auto ysig = [&](int q) {
+        int64_t yi = (int64_t(tile.ylo) - 4 + q) % g.T[1];
+        if (yi < 0) yi += g.T[1];
+        sg.si[1] = sgy[yi];
+        sg.sm[1] = sgy[yi == 0 ? g.T[1] - 1 : yi - 1];
+    };
+    const bool out_lane = lane >= 4 && lane <= 27 && gx >= tile.xlo && gx <= tile.xhi;
     const T ih = T(1.0 / a.h), ih2 = T(1.0 / (a.h * a.h)), i2h = T(0.5 / a.h);
-    const T cl[4] = {T(a.dt / 4.0), T(a.dt / 3.0), T(a.dt / 2.0), T(a.dt)};
-    const int nfl = 2;
-#pragma unroll 1
-    for (int L = 0; L < 4; ++L) {
-        const int rad = 3 - L;
-        const int rlo = 4 - rad, clo = 4 - rad;
-        const int nr = kLayerTH + 2 * rad, nc = kLayerTW + 2 * rad, np = nr * nc;
-        const T *src = L == 0 ? Y : Z;
-        T res[kLPts][6];
-#pragma unroll
-        for (int k = 0; k < kLPts; ++k) {
-            const int p = tid + k * kLThreads;
-            if (p < np) {
-                const int r = rlo + p / nc, c = clo + p % nc;
-                apply_A2<T, ADJ>(src, sx, sy, r, c, ax, ay, ih, ih2, i2h, res[k]);
-            }
+    const T c4 = T(a.dt / 4.0), c3 = T(a.dt / 3.0), c2 = T(a.dt / 2.0), c1 = T(a.dt);
+    T z4[3][NF], z3[3][NF], z2[3][NF];
+
+    for (int c = 0; c < nch; ++c) {
+        if (!mbar_wait(&bars[warp][c % S], (c / S) & 1, a.err, 2)) {
+            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2) mbar_wait(&bars[warp][c2 % S], (c2 / S) & 1, nullptr, 0);
+            return;
         }
-        __syncthreads();
-        if (L < 3) {
-            const T cL = cl[L];
+        const T *cur = ring + (c % S) * SE + lane;
+        const T *prv = ring + ((c + S - 1) % S) * SE + lane;
 #pragma unroll
-            for (int k = 0; k < kLPts; ++k) {
-                const int p = tid + k * kLThreads;
-                if (p < np) {
-                    const int o = (rlo + p / nc) * kLC + clo + p % nc;
-                    for (int f = 0; f < nfl; ++f) Z[f * kLN + o] = Y[f * kLN + o] + cL * res[k][f];
-                    if (ax)
-                        for (int f = 2; f < 4; ++f) Z[f * kLN + o] = Y[f * kLN + o] + cL * res[k][f];
-                    if (ay)
-                        for (int f = 4; f < 6; ++f) Z[f * kLN + o] = Y[f * kLN + o] + cL * res[k][f];
+        for (int j = 0; j < CH; ++j) {
+            const int p = c * CH + j;
+            if (p < nin) {
+                const int PH = j % 3;
+                // own-column value of input row p - k, field f (rows of this or the previous chunk)
+                auto Y = [&](int k, int f) -> T {
+                    const int r = j - k;
+                    return r >= 0 ? cur[f * FE + r * 32] : prv[f * FE + (r + CH) * 32];
+                };
+                if (p >= 2) {   // level 4 at row p-1
+                    T cen[NF], xm[NF], xp[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        cen[f] = Y(1, f);
+                        xm[f] = __shfl_up_sync(0xffffffffu, cen[f], 1);
+                        xp[f] = __shfl_down_sync(0xffffffffu, cen[f], 1);
+                    }
+                    auto N = [&](int f, int d) -> T {
+                        switch (d) {
+                        case 0: return cen[f];
+                        case 1: return xm[f];
+                        case 2: return xp[f];
+                        case 3: return Y(2, f);
+                        default: return Y(0, f);
+                        }
+                    };
+                    ysig(p - 1);
+                    T r[NF];
+                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) z4[(PH + 2) % 3][f] = cen[f] + c4 * r[f];
                 }
-            }
-            __syncthreads();
-        } else {
-            const T cL = cl[3];
+                if (p >= 4) {   // level 3 at row p-2
+                    T xm[NF], xp[NF];
 #pragma unroll
-            for (int k = 0; k < kLPts; ++k) {
-                const int p = tid + k * kLThreads;
-                if (p < np) {
-                    const int rr = rlo + p / nc, cc = clo + p % nc;
-                    const int64_t x = int64_t(tile.x0) + cc - 4, y = int64_t(tile.y0) + rr - 4;
-                    if (x >= tile.xlo && x <= tile.xhi && y >= tile.ylo && y <= tile.yhi) {
-                        const int o = rr * kLC + cc;
-                        const bool edge = near_edge(g, x, y, 0);
-                        for (int f = 0; f < 6; ++f) {
-                            if ((f == 2 || f == 3) && !ax) continue;
-                            if ((f == 4 || f == 5) && !ay) continue;
-                            const T val = Y[f * kLN + o] + cL * res[k][f];
-                            T *dst = static_cast<T *>(out.p[f]);
-                            if (edge) store_wrapped(dst, g, x, y, 0, val);
-                            else dst[g.origin + x + y * g.P] = val;
+                    for (int f = 0; f < NF; ++f) {
+                        xm[f] = __shfl_up_sync(0xffffffffu, z4[(PH + 1) % 3][f], 1);
+                        xp[f] = __shfl_down_sync(0xffffffffu, z4[(PH + 1) % 3][f], 1);
+                    }
+                    auto N = [&](int f, int d) -> T {
+                        switch (d) {
+                        case 0: return z4[(PH + 1) % 3][f];
+                        case 1: return xm[f];
+                        case 2: return xp[f];
+                        case 3: return z4[PH][f];
+                        default: return z4[(PH + 2) % 3][f];
+                        }
+                    };
+                    ysig(p - 2);
+                    T r[NF];
+                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) z3[(PH + 1) % 3][f] = Y(2, f) + c3 * r[f];
+                }
+                if (p >= 6) {   // level 2 at row p-3
+                    T xm[NF], xp[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        xm[f] = __shfl_up_sync(0xffffffffu, z3[PH][f], 1);
+                        xp[f] = __shfl_down_sync(0xffffffffu, z3[PH][f], 1);
+                    }
+                    auto N = [&](int f, int d) -> T {
+                        switch (d) {
+                        case 0: return z3[PH][f];
+                        case 1: return xm[f];
+                        case 2: return xp[f];
+                        case 3: return z3[(PH + 2) % 3][f];
+                        default: return z3[(PH + 1) % 3][f];
+                        }
+                    };
+                    ysig(p - 3);
+                    T r[NF];
+                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) z2[PH][f] = Y(3, f) + c2 * r[f];
+                }
+                if (p >= 8) {   // level 1: output row p-4
+                    T xm[NF], xp[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        xm[f] = __shfl_up_sync(0xffffffffu, z2[(PH + 2) % 3][f], 1);
+                        xp[f] = __shfl_down_sync(0xffffffffu, z2[(PH + 2) % 3][f], 1);
+                    }
+                    auto N = [&](int f, int d) -> T {
+                        switch (d) {
+                        case 0: return z2[(PH + 2) % 3][f];
+                        case 1: return xm[f];
+                        case 2: return xp[f];
+                        case 3: return z2[(PH + 1) % 3][f];
+                        default: return z2[PH][f];
+                        }
+                    };
+                    ysig(p - 4);
+                    T r[NF];
+                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+                    if (out_lane) {
+                        const int64_t y = int64_t(tile.ylo) + p - 8;
+                        const bool edge = near_edge(g, gx, y, 0);
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const T val = Y(4, f) + c1 * r[f];
+                            T *dst = static_cast<T *>(out.p[F::gid(f)]);
+                            if (edge) store_wrapped(dst, g, gx, y, 0, val);
+                            else dst[g.origin + gx + y * g.P] = val;
                         }
                     }
                 }
             }
         }
+        __syncwarp();
+        // chunk c-1 is no longer needed (rows >= c*CH - 4 remain in use): refill it
+        if (lane == 0 && c >= 1 && c - 1 + S < nch) {
+            fence_proxy_async();
+            const int st = (c - 1) % S;
+            issue_chunk2<T, MASK>(ring + st * SE, maps, tx, ty + (c - 1 + S) * CH, &bars[warp][st]);
+        }
     }
 }
 
-template <typename T> static size_t layer2d_smem() { return size_t(12) * kLN * sizeof(T) + 128; }
-
-template <typename T, bool ADJ> static cudaError_t prep_layer2d()
+template <typename T, int MASK> static size_t layer2d_smem()
 {
+    return size_t(4) * kL2S * Fields2<MASK>::NF * kL2CH * 32 * sizeof(T) + 128;
+}
+
+template <typename T, bool ADJ, int MASK>
+static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, cudaStream_t st)
+{
+    const int n = a.class_off[MASK + 1] - a.class_off[MASK];
+    if (n <= 0) return cudaSuccess;
     static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_layer2d<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(layer2d_smem<T>()));
-    if (e == cudaSuccess) done = true;
-    return e;
+    const size_t sm = layer2d_smem<T, MASK>();
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_layer2d<T, ADJ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    k_layer2d<T, ADJ, MASK><<<(n + 3) / 4, 128, sm, st>>>(m, o, a, a.class_off[MASK], n);
+    return cudaGetLastError();
+}
+
+template <typename T, bool ADJ>
+static cudaError_t launch_l2_all(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = launch_l2<T, ADJ, 0>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l2<T, ADJ, 1>(m, o, a, st)) != cudaSuccess) return e;
+    if ((e = launch_l2<T, ADJ, 2>(m, o, a, st)) != cudaSuccess) return e;
+    return launch_l2<T, ADJ, 3>(m, o, a, st);
 }
 
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp,
                            const Layer2DArgs &a, cudaStream_t st)
 {
     if (a.ntiles <= 0) return cudaSuccess;
+    Maps6 m;
     Out6 o;
-    for (int f = 0; f < 6; ++f) o.p[f] = outp[f];
-    cudaError_t e;
-#define PML_LAUNCH(TT, AA)                                                                           \
-    if ((e = prep_layer2d<TT, AA>()) != cudaSuccess) return e;                                       \
-    k_layer2d<TT, AA><<<a.ntiles, kLThreads, layer2d_smem<TT>(), st>>>(tm[0], tm[1], tm[2], tm[3], \
-                                                                        tm[4], tm[5], o, a);
-    if (prec == 32) {
-        if (adjoint) { PML_LAUNCH(float, true) } else { PML_LAUNCH(float, false) }
-    } else {
-        if (adjoint) { PML_LAUNCH(double, true) } else { PML_LAUNCH(double, false) }
+    for (int f = 0; f < 6; ++f) {
+        m.m[f] = tm[f];
+        o.p[f] = outp[f];
     }
-#undef PML_LAUNCH
-    return cudaGetLastError();
+    if (prec == 32) return adjoint ? launch_l2_all<float, true>(m, o, a, st) : launch_l2_all<float, false>(m, o, a, st);
+    return adjoint ? launch_l2_all<double, true>(m, o, a, st) : launch_l2_all<double, false>(m, o, a, st);
 }
 
 }  // namespace pml
