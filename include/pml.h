@@ -226,6 +226,21 @@ pml_status pml_load_state(pml_ctx *ctx, const void *src, int on_device);
 pml_status pml_profile_enable(pml_ctx *ctx, int enable);
 pml_status pml_profile_read(pml_ctx *ctx, double ms[3], int64_t launches[3]);
 
+/*
+ * Kernel variants and autotuning.  The layer-free (interior) kernel of a 2D context
+ * exists in several shapes (columns per lane, rows per TMA box, pipeline depth,
+ * resident CTAs per SM); 3D contexts have one.  pml_get_variant reports the current
+ * one and how many exist; pml_set_variant selects one (synchronising).
+ * pml_autotune times every variant for `steps` steps on the current state (sources and
+ * receivers are suspended while it runs; the state advances by
+ * (steps + 2) * count steps, so tune before pml_set_initial), keeps the fastest, writes
+ * its index to *chosen and, if times_ms is not NULL, each variant's milliseconds per step
+ * to times_ms[0..count-1].
+ */
+pml_status pml_get_variant(const pml_ctx *ctx, int *variant, int *count);
+pml_status pml_set_variant(pml_ctx *ctx, int variant);
+pml_status pml_autotune(pml_ctx *ctx, int steps, double *times_ms, int *chosen);
+
 void pml_destroy(pml_ctx *ctx);
 const char *pml_last_error(const pml_ctx *ctx);
 const char *pml_status_string(pml_status s);

@@ -47,6 +47,7 @@ EXPORTED = (
     "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
     "pml_adjoint_read_field", "pml_state_bytes", "pml_save_state", "pml_load_state",
+    "pml_get_variant", "pml_set_variant", "pml_autotune",
     "pml_profile_enable", "pml_profile_read", "pml_destroy", "pml_last_error",
     "pml_status_string",
 )
@@ -106,6 +107,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_save_state": [P, P, ctypes.c_int],
         "pml_load_state": [P, P, ctypes.c_int],
         "pml_profile_enable": [P, ctypes.c_int],
+        "pml_get_variant": [P, P, P],
+        "pml_set_variant": [P, ctypes.c_int],
+        "pml_autotune": [P, ctypes.c_int, P, P],
         "pml_profile_read": [P, P, P],
     }
     for name, args in sig.items():
@@ -221,6 +225,28 @@ def pml_save_state(ctx, dst, on_device):
 
 def pml_load_state(ctx, src, on_device):
     _check(load().pml_load_state(ctx, src, int(on_device)), ctx)
+
+
+def pml_get_variant(ctx):
+    """Returns (current variant, number of variants)."""
+    v = ctypes.c_int(0)
+    n = ctypes.c_int(0)
+    _check(load().pml_get_variant(ctx, ctypes.byref(v), ctypes.byref(n)), ctx)
+    return int(v.value), int(n.value)
+
+
+def pml_set_variant(ctx, variant):
+    _check(load().pml_set_variant(ctx, int(variant)), ctx)
+
+
+def pml_autotune(ctx, steps):
+    """Returns (chosen variant, per-variant ms per step)."""
+    import numpy as np
+    _, n = pml_get_variant(ctx)
+    times = np.zeros(n, dtype=np.float64)
+    ch = ctypes.c_int(0)
+    _check(load().pml_autotune(ctx, int(steps), times.ctypes.data, ctypes.byref(ch)), ctx)
+    return int(ch.value), times
 
 
 def pml_profile_enable(ctx, enable):

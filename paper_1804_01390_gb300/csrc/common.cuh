@@ -40,10 +40,32 @@ struct Range {
 // Forward:  a = (dt, dt^2/2h^2, dt^3/6h^2, dt^4/24h^4, 0),  b = (0, dt/h^2, dt^2/2h^2, dt^3/6h^4, dt^4/24h^4)
 // Adjoint (A^T = [[0, L], [I, 0]]):
 //           a = (0, dt^2/2h^2, dt/h^2, dt^4/24h^4, dt^3/6h^4), b = (dt, dt^3/6h^2, dt^2/2h^2, 0, dt^4/24h^4)
-struct StepCoef {
-    double a1, a2, a3, a4, a5;
-    double b1, b2, b3, b4, b5;
+template <typename T> struct StepCoefT {
+    T a1, a2, a3, a4, a5;
+    T b1, b2, b3, b4, b5;
 };
+// Both precisions are carried so that a kernel never converts a coefficient on the device
+// (a double -> float conversion runs on the FP64 pipe, which is narrow on this part).
+struct StepCoef {
+    StepCoefT<double> d;
+    StepCoefT<float> f;
+};
+template <typename T> __host__ __device__ __forceinline__ const StepCoefT<T> &coef_of(const StepCoef &c);
+template <> __host__ __device__ __forceinline__ const StepCoefT<double> &coef_of<double>(const StepCoef &c) { return c.d; }
+template <> __host__ __device__ __forceinline__ const StepCoefT<float> &coef_of<float>(const StepCoef &c) { return c.f; }
+
+// Constants of the layer kernels (1/h, 1/h^2, 1/(2h) and the Horner coefficients
+// dt/4, dt/3, dt/2, dt), in both precisions.
+template <typename T> struct LayerConstT {
+    T ih, ih2, i2h, c4, c3, c2, c1;
+};
+struct LayerConst {
+    LayerConstT<double> d;
+    LayerConstT<float> f;
+};
+template <typename T> __host__ __device__ __forceinline__ const LayerConstT<T> &lconst_of(const LayerConst &c);
+template <> __host__ __device__ __forceinline__ const LayerConstT<double> &lconst_of<double>(const LayerConst &c) { return c.d; }
+template <> __host__ __device__ __forceinline__ const LayerConstT<float> &lconst_of<float>(const LayerConst &c) { return c.f; }
 
 // One output tile of a layer kernel (2D: z fields unused).
 struct LayerTile {
@@ -213,33 +235,41 @@ __device__ __forceinline__ bool near_edge(const Geom &g, int64_t x, int64_t y, i
 // kernel launchers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------------
 
-// Interior (layer-free) step of a 2D field pair: reads (U, V) through the tensor maps
-// (box 128 x kRows2D rows), writes (Uo, Vo) on the output rectangle xr x yr.
+// Interior (layer-free) step of a 2D field pair: reads (U, V) through the tensor maps,
+// writes (Uo, Vo) on the output rectangle xr x yr.  Persistent kernel fed by a work
+// queue: this launch counts on queue[parity] and clears queue[1 - parity].
 struct Interior2DArgs {
     Geom g;
     Range xr, yr;
     StepCoef c;
     DeviceError *err;
+    int *queue;
+    int parity;
 };
-cudaError_t launch_interior2d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
-                              void *Uo, void *Vo, const Interior2DArgs &a, int grid,
-                              cudaStream_t st);
-int interior2d_box_rows(int prec);
-int interior2d_max_blocks_per_sm(int prec, bool adjoint);
+// Variant v of the 2D interior kernel (see kI2Vars32 / kI2Vars64 in step2d.cu): its TMA
+// box is interior2d_box_cols(prec, v) x interior2d_box_rows(prec, v).
+int interior2d_variants(int prec);
+int interior2d_box_cols(int prec, int v);
+int interior2d_box_rows(int prec, int v);
+int interior2d_max_blocks_per_sm(int prec, bool adjoint, int v);
+// overlap_previous: the launch may start while the previous kernel of the stream (the
+// layer kernel of the same step, whose outputs it does not read) is still running
+cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                              void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
+                              bool overlap_previous);
 
-// Layer step of 2D tiles (Horner form of the RK4 polynomial with the full operator).
+// Layer step of 2D strips (Horner form of the RK4 polynomial with the full operator).
 struct Layer2DArgs {
     Geom g;
-    double dt, h;
+    LayerConst k;
     const void *sig[2];        // device sigma per axis (context precision), length T[a]
-    const LayerTile *tiles;    // sorted by flags (set of axes with active aux fields)
+    const LayerTile *tiles;
     int ntiles;
-    int class_off[9];          // tiles of flags m are [class_off[m], class_off[m+1])
     DeviceError *err;
 };
 // 2D layer work items: 24 output columns (one warp, halo 4 lanes per side) by at most
 // kLayer2LY output rows of one frame rectangle
-constexpr int kLayerTW = 24, kLayer2LY = 256;
+constexpr int kLayerTW = 24, kLayer2LY = 16;
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U,V,Px,Qx,Py,Qy*/,
                            void *const *out /*[6]*/, const Layer2DArgs &a, cudaStream_t st);
 
@@ -259,7 +289,7 @@ int interior3d_max_blocks_per_sm(int prec, bool adjoint);
 
 struct Layer3DArgs {
     Geom g;
-    double dt, h;
+    LayerConst k;
     const void *sig[3];
     const LayerTile *tiles;    // sorted by flags (set of axes with active aux fields)
     int ntiles;

@@ -39,7 +39,7 @@ struct Plan {
     size_t adj[2][8] = {};
     size_t sig[3] = {};
     size_t tiles = 0, tiles_adj = 0, max_tiles = 0;
-    size_t partials = 0, normout = 0, err = 0;
+    size_t partials = 0, normout = 0, err = 0, queue = 0;
     size_t src_off = 0, src_xyz = 0, src_amp = 0, grad = 0, rec_off = 0;
     size_t total = 0;
 };
@@ -97,6 +97,7 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
     p->partials = off; off += align_up(size_t(kNormBlocks) * kNormVals * sizeof(double), kAlign);
     p->normout = off; off += kAlign;
     p->err = off; off += kAlign;
+    p->queue = off; off += kAlign;
     p->src_off = off; off += align_up(kMaxSources * sizeof(int64_t), kAlign);
     p->src_xyz = off; off += align_up(kMaxSources * 3 * sizeof(int32_t), kAlign);
     p->src_amp = off; off += align_up(kMaxSources * sizeof(double), kAlign);
@@ -130,6 +131,8 @@ struct pml_ctx {
     int class_off[9] = {}, class_off_adj[9] = {};
     double *dpart = nullptr, *dnorm = nullptr, *dgrad = nullptr;
     DeviceError *derr = nullptr;
+    int *dqueue = nullptr;              // work counters of the persistent 2D step (fwd 0/1, adj 2/3)
+    int64_t launches_fwd = 0, launches_adj = 0;
     int ns = 0, nr = 0;
     int64_t *dsrc_off = nullptr, *drec_off = nullptr;
     int32_t *dsrc_xyz = nullptr;
@@ -141,6 +144,7 @@ struct pml_ctx {
     bool adj_ready = false;
     CUtensorMap tm_int[2][2], tm_lay[2][8], tm_int_adj[2][2], tm_lay_adj[2][8];
     int grid_int = 0, grid_int_adj = 0, sm_count = 0;
+    int ivar = 0;                       // interior kernel variant (2D)
     // kernel timing (pml_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs
@@ -266,6 +270,8 @@ void build_layout(pml_ctx *c)
     }
     for (int a = c->nd; a < 3; ++a) c->ir[a] = c->ir_adj[a] = {0, 0};
 }
+
+bool range_empty(const Range &r) { return r.lo > r.hi; }
 
 bool axis_active(const pml_ctx *c, int a, int64_t lo, int64_t hi)
 {
@@ -408,10 +414,21 @@ void step_coef(const pml_ctx *c, bool adjoint, StepCoef *k)
     const double dt = c->dt, h2 = c->h * c->h, h4 = h2 * h2;
     const double d1 = dt, d2 = dt * dt / 2.0, d3 = dt * dt * dt / 6.0, d4 = dt * dt * dt * dt / 24.0;
     if (!adjoint) {
-        *k = {d1, d2 / h2, d3 / h2, d4 / h4, 0.0, 0.0, d1 / h2, d2 / h2, d3 / h4, d4 / h4};
+        k->d = {d1, d2 / h2, d3 / h2, d4 / h4, 0.0, 0.0, d1 / h2, d2 / h2, d3 / h4, d4 / h4};
     } else {
-        *k = {0.0, d2 / h2, d1 / h2, d4 / h4, d3 / h4, d1, d3 / h2, d2 / h2, 0.0, d4 / h4};
+        k->d = {0.0, d2 / h2, d1 / h2, d4 / h4, d3 / h4, d1, d3 / h2, d2 / h2, 0.0, d4 / h4};
     }
+    const StepCoefT<double> &e = k->d;
+    k->f = {float(e.a1), float(e.a2), float(e.a3), float(e.a4), float(e.a5),
+            float(e.b1), float(e.b2), float(e.b3), float(e.b4), float(e.b5)};
+}
+
+LayerConst layer_const(const pml_ctx *c)
+{
+    LayerConst k;
+    k.d = {1.0 / c->h, 1.0 / (c->h * c->h), 0.5 / c->h, c->dt / 4.0, c->dt / 3.0, c->dt / 2.0, c->dt};
+    k.f = {float(k.d.ih), float(k.d.ih2), float(k.d.i2h), float(k.d.c4), float(k.d.c3), float(k.d.c2), float(k.d.c1)};
+    return k;
 }
 
 PointArgs point_args(const pml_ctx *c)
@@ -466,24 +483,28 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
     const CUtensorMap *tl = adjoint ? c->tm_lay_adj[p] : c->tm_lay[p];
     cudaError_t e;
     if (c->nd == 2) {
-        Interior2DArgs a{};
-        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.c = k; a.err = c->derr;
-        long pi = prof_begin(c, 0);
-        e = launch_interior2d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
-                              adjoint ? c->grid_int_adj : c->grid_int, c->st);
-        prof_end(c, pi);
-        if (e != cudaSuccess) return cuda_fail(c, e, "interior 2D kernel");
         Layer2DArgs l{};
-        l.g = c->g; l.dt = c->dt; l.h = c->h;
+        l.g = c->g; l.k = layer_const(c);
         l.sig[0] = c->dsig[0]; l.sig[1] = c->dsig[1];
         l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
-        for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
         l.err = c->derr;
-        pi = prof_begin(c, 1);
+        long pi = prof_begin(c, 1);
         e = launch_layer2d(c->prec, adjoint, tl, out, l, c->st);
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel");
+        Interior2DArgs a{};
+        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.c = k; a.err = c->derr;
+        int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
+        a.queue = c->dqueue + (adjoint ? 2 : 0);
+        a.parity = int(nl & 1);
+        // overlap with the layer kernel only when no event sits between the two launches
+        pi = prof_begin(c, 0);
+        e = launch_interior2d(c->prec, adjoint, c->ivar, &ti[0], &ti[1], out[0], out[1], a,
+                              adjoint ? c->grid_int_adj : c->grid_int, c->st, l.ntiles > 0 && !c->prof_on);
+        prof_end(c, pi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "interior 2D kernel");
+        if (!range_empty(ir[0]) && !range_empty(ir[1])) ++nl;
     } else {
         Interior3DArgs a{};
         a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
@@ -493,7 +514,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "interior 3D kernel");
         Layer3DArgs l{};
-        l.g = c->g; l.dt = c->dt; l.h = c->h;
+        l.g = c->g; l.k = layer_const(c);
         for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
         l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
@@ -504,6 +525,35 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "layer 3D kernel");
     }
+    return PML_OK;
+}
+
+// Grid sizes of the interior kernels for the current variant: all resident CTAs.
+pml_status interior_grids(pml_ctx *c)
+{
+    const bool adj = (c->flags & PML_FLAG_ADJOINT) != 0;
+    int bps = c->nd == 2 ? interior2d_max_blocks_per_sm(c->prec, false, c->ivar) : interior3d_max_blocks_per_sm(c->prec, false);
+    int bpa = adj ? (c->nd == 2 ? interior2d_max_blocks_per_sm(c->prec, true, c->ivar) : interior3d_max_blocks_per_sm(c->prec, true))
+                  : 0;
+    if (bps <= 0 || (adj && bpa <= 0))
+        return fail(c, PML_ECUDA, "interior kernel cannot be resident (shared memory / registers)");
+    c->grid_int = bps * c->sm_count;
+    c->grid_int_adj = bpa * c->sm_count;
+    return PML_OK;
+}
+
+// Tensor maps of the 2D interior kernel for the current variant's box.
+pml_status encode_interior_maps(pml_ctx *c)
+{
+    if (c->nd != 2) return PML_OK;
+    uint32_t box[3] = {uint32_t(interior2d_box_cols(c->prec, c->ivar)), uint32_t(interior2d_box_rows(c->prec, c->ivar)), 1};
+    pml_status s;
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 2; ++f) {
+            if ((s = encode_map(c, &c->tm_int[p][f], c->fld[p][f], box)) != PML_OK) return s;
+            if ((c->flags & PML_FLAG_ADJOINT) && (s = encode_map(c, &c->tm_int_adj[p][f], c->adj[p][f], box)) != PML_OK)
+                return s;
+        }
     return PML_OK;
 }
 
@@ -603,6 +653,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     c->dpart = reinterpret_cast<double *>(c->ws + plan.partials);
     c->dnorm = reinterpret_cast<double *>(c->ws + plan.normout);
     c->derr = reinterpret_cast<DeviceError *>(c->ws + plan.err);
+    c->dqueue = reinterpret_cast<int *>(c->ws + plan.queue);
     c->dsrc_off = reinterpret_cast<int64_t *>(c->ws + plan.src_off);
     c->dsrc_xyz = reinterpret_cast<int32_t *>(c->ws + plan.src_xyz);
     c->dsrc_amp = reinterpret_cast<double *>(c->ws + plan.src_amp);
@@ -613,6 +664,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     {
         cudaError_t e = cudaMemsetAsync(c->ws, 0, plan.sig[0], c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(DeviceError), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->dqueue, 0, 4 * sizeof(int), c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->dgrad, 0, kMaxSources * sizeof(double), c->st);
         if (e != cudaSuccess) { cuda_fail(c, e, "clear workspace"); return bail(PML_ECUDA); }
     }
@@ -646,8 +698,9 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     {
         uint32_t box_int[3], box_lay[3];
         if (c->nd == 2) {
-            box_int[0] = 128; box_int[1] = uint32_t(interior2d_box_rows(precision)); box_int[2] = 1;
-            box_lay[0] = 32; box_lay[1] = 6; box_lay[2] = 1;   // one warp's 32 columns x 6 rows
+            box_int[0] = uint32_t(interior2d_box_cols(precision, c->ivar));
+            box_int[1] = uint32_t(interior2d_box_rows(precision, c->ivar)); box_int[2] = 1;
+            box_lay[0] = 32; box_lay[1] = 3; box_lay[2] = 1;   // one warp's 32 columns x 3 rows
         } else {
             box_int[0] = 128; box_int[1] = uint32_t(interior3d_tile_y() + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
             box_lay[0] = uint32_t(layer3d_tile_x(precision) + 8); box_lay[1] = uint32_t(layer3d_tile_y(precision) + 8);
@@ -669,19 +722,73 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             for (int f = c->nf; f < 8; ++f) { c->tm_lay[p][f] = c->tm_lay[p][0]; c->tm_lay_adj[p][f] = c->tm_lay_adj[p][0]; }
         }
     }
-    {
-        int bps = c->nd == 2 ? interior2d_max_blocks_per_sm(precision, false) : interior3d_max_blocks_per_sm(precision, false);
-        int bpa = (flags & PML_FLAG_ADJOINT)
-                      ? (c->nd == 2 ? interior2d_max_blocks_per_sm(precision, true) : interior3d_max_blocks_per_sm(precision, true))
-                      : 0;
-        if (bps <= 0) { fail(c, PML_ECUDA, "interior kernel cannot be resident (shared memory / registers)"); return bail(PML_ECUDA); }
-        c->grid_int = bps * c->sm_count;
-        c->grid_int_adj = bpa * c->sm_count;
-    }
+    if ((s = interior_grids(c)) != PML_OK) return bail(s);
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) { cuda_fail(c, e, "create"); return bail(PML_ECUDA); }
     *out = c;
     return PML_OK;
+}
+
+pml_status pml_set_variant(pml_ctx *c, int variant)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    const int n = c->nd == 2 ? interior2d_variants(c->prec) : 1;
+    if (variant < 0 || variant >= n) return fail(c, PML_EINVAL, "variant %d not in [0, %d)", variant, n);
+    PML_CU(c, cudaStreamSynchronize(c->st), "stream synchronize");
+    const int old = c->ivar;
+    c->ivar = variant;
+    pml_status s = encode_interior_maps(c);
+    if (s == PML_OK) s = interior_grids(c);
+    if (s != PML_OK) {
+        c->ivar = old;
+        encode_interior_maps(c);
+        interior_grids(c);
+    }
+    return s;
+}
+
+pml_status pml_get_variant(const pml_ctx *c, int *variant, int *count)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (variant) *variant = c->ivar;
+    if (count) *count = c->nd == 2 ? interior2d_variants(c->prec) : 1;
+    return PML_OK;
+}
+
+pml_status pml_autotune(pml_ctx *c, int steps, double *times_ms, int *chosen)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (steps < 1) return fail(c, PML_EINVAL, "steps must be >= 1");
+    const int n = c->nd == 2 ? interior2d_variants(c->prec) : 1;
+    cudaEvent_t e0, e1;
+    PML_CU(c, cudaEventCreate(&e0), "event");
+    PML_CU(c, cudaEventCreate(&e1), "event");
+    int best = c->ivar;
+    double best_ms = 1e300;
+    pml_status st = PML_OK;
+    const int ns = c->ns, nr = c->nr;
+    c->ns = 0;   // time the step alone: no sources, no receiver rows consumed
+    c->nr = 0;
+    for (int v = 0; v < n && st == PML_OK; ++v) {
+        if ((st = pml_set_variant(c, v)) != PML_OK) break;
+        if ((st = pml_step(c, 2)) != PML_OK) break;      // warm-up
+        cudaEventRecord(e0, c->st);
+        if ((st = pml_step(c, steps)) != PML_OK) break;
+        cudaEventRecord(e1, c->st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(c, PML_ECUDA, "autotune sync"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = double(ms) / steps;
+        if (times_ms) times_ms[v] = per;
+        if (per < best_ms) { best_ms = per; best = v; }
+    }
+    c->ns = ns;
+    c->nr = nr;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PML_OK) return st;
+    if (chosen) *chosen = best;
+    return pml_set_variant(c, best);
 }
 
 pml_status pml_profile_enable(pml_ctx *c, int enable)

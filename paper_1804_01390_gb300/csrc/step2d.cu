@@ -22,229 +22,225 @@
 
 namespace pml {
 
-constexpr int kRows2D = 6;   // rows per TMA box; multiple of 3 (register ring period)
-constexpr int kStrip = 120;  // output columns per warp strip (lanes 1..30)
+// Interior kernel variants.
+//  kind 0 (row-parallel): a CTA of BY warps streams one strip of 120 output columns in
+//     blocks of BY rows, one warp per row; U/V rows come through an S-chunk TMA ring,
+//     first differences through a shared row ring; block barriers twice per block.
+//  kind 1 (warp-streaming): each warp streams its own strip down the rows with register
+//     row rings; NC columns per lane (30 NC outputs per strip), CH rows per TMA box,
+//     S stages per warp.
+// minb: resident CTAs per SM the launch bounds ask for.
+struct I2Var {
+    int kind, nc, ch, s, minb;   // kind 0: ch = BY (rows per block / warps per CTA)
+};
+constexpr I2Var kI2Vars32[] = {{1, 4, 6, 3, 3}, {0, 4, 8, 8, 2}, {0, 4, 4, 8, 4}, {1, 4, 6, 2, 4}, {1, 8, 3, 3, 2}};
+constexpr I2Var kI2Vars64[] = {{0, 4, 4, 8, 3}, {0, 4, 8, 4, 1}, {1, 4, 6, 2, 2}, {1, 4, 3, 3, 2}};
+constexpr int kNI2Vars32 = sizeof(kI2Vars32) / sizeof(I2Var);
+constexpr int kNI2Vars64 = sizeof(kI2Vars64) / sizeof(I2Var);
+constexpr int kI2Rows = 64;     // rows per work item, warp-streaming kind
+constexpr int kI2RowsR = 128;   // rows per work item, row-parallel kind
 
-template <typename T> struct Stages2D {
-    static constexpr int S = sizeof(T) == 4 ? 3 : 2;
+int interior2d_variants(int prec) { return prec == 32 ? kNI2Vars32 : kNI2Vars64; }
+int interior2d_box_cols(int prec, int v) { return 32 * (prec == 32 ? kI2Vars32[v].nc : kI2Vars64[v].nc); }
+int interior2d_threads(int prec, int v)
+{
+    const I2Var &q = prec == 32 ? kI2Vars32[v] : kI2Vars64[v];
+    return q.kind == 0 ? 32 * q.ch : 128;
+}
+int interior2d_box_rows(int prec, int v) { return prec == 32 ? kI2Vars32[v].ch : kI2Vars64[v].ch; }
+
+
+
+
+// Pairs of adjacent columns.  FP32 uses the packed FP32x2 instructions of this
+// architecture (one instruction rounds each lane of the pair exactly like the scalar
+// one); FP64 uses two scalar operations.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    using P = float2;
+    static __device__ __forceinline__ P mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ P add(P a, P b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ P mul(P a, P b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ P fma(P a, P b, P c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct Pair<double> {
+    using P = double2;
+    static __device__ __forceinline__ P mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ P add(P a, P b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ P mul(P a, P b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ P fma(P a, P b, P c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
 };
 
-int interior2d_box_rows(int) { return kRows2D; }
-
-// Unscaled 5-point difference of one lane's 4 columns: c is the centre row, up/dn the
-// rows above/below; x neighbours across lanes by shuffles.
-template <typename T>
-__device__ __forceinline__ V4<T> diff5(const V4<T> &c, const V4<T> &up, const V4<T> &dn)
+// Unscaled 5-point difference of one lane's NC columns held as NC/2 pairs; l / r are the
+// values left of column 0 and right of column NC-1 (neighbouring lanes), up / dn the rows
+// above and below.  o = ((x-1 + x+1) + (up + dn)) - 4 x.
+template <typename T, int NH>
+__device__ __forceinline__ void diff5p(const typename Pair<T>::P (&c)[NH], T l, T r, const typename Pair<T>::P (&up)[NH],
+                                       const typename Pair<T>::P (&dn)[NH], typename Pair<T>::P (&o)[NH])
 {
-    const T l = __shfl_up_sync(0xffffffffu, c.w, 1);
-    const T r = __shfl_down_sync(0xffffffffu, c.x, 1);
-    V4<T> o;
-    o.x = ((l + c.y) + (up.x + dn.x)) - T(4) * c.x;
-    o.y = ((c.x + c.z) + (up.y + dn.y)) - T(4) * c.y;
-    o.z = ((c.y + c.w) + (up.z + dn.z)) - T(4) * c.z;
-    o.w = ((c.z + r) + (up.w + dn.w)) - T(4) * c.w;
-    return o;
+    using M = Pair<T>;
+    const typename M::P m4 = M::mk(T(-4), T(-4));
+#pragma unroll
+    for (int k = 0; k < NH; ++k) {
+        const typename M::P left = M::mk(k == 0 ? l : c[k - 1].y, c[k].x);
+        const typename M::P right = M::mk(c[k].y, k == NH - 1 ? r : c[k + 1].x);
+        o[k] = M::fma(m4, c[k], M::add(M::add(left, right), M::add(up[k], dn[k])));
+    }
 }
 
-template <typename T, bool ADJ>
-__global__ void __launch_bounds__(128)
-    k_interior2d(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
-                 T *__restrict__ Uo, T *__restrict__ Vo, const Interior2DArgs a)
+// One interior work item: output rows y0 .. y0+cnt-1 of the strip starting at column xs,
+// streamed by one warp through its TMA ring (`wbase`, S stages).  The warp's barriers are
+// initialised once per kernel; `use` counts the ring stages this warp has consumed so far
+// and gives each stage's slot and phase parity.
+template <typename T, bool ADJ, int NC, int CH, int S>
+__device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUtensorMap *tmV, T *__restrict__ Uo,
+                                               T *__restrict__ Vo, const Interior2DArgs &a, int64_t xs, int64_t y0,
+                                               int cnt, unsigned char *wbase, uint64_t *bars, int lane,
+                                               uint32_t &use)
 {
-    constexpr int CH = kRows2D;
-    constexpr int S = Stages2D<T>::S;
-    constexpr int ROW = 128;
+    using M = Pair<T>;
+    using PT = typename M::P;
+    constexpr int NH = NC / 2;
+    constexpr int ROW = 32 * NC;
     constexpr uint32_t FIELD_BYTES = CH * ROW * sizeof(T);
     constexpr uint32_t STAGE_BYTES = 2 * FIELD_BYTES;
-    __shared__ __align__(8) uint64_t bars[4][S];
-    extern __shared__ unsigned char smem_dyn[];
-    unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const Geom &g = a.g;
+    const StepCoefT<T> &kc = coef_of<T>(a.c);
+    const PT A1 = M::mk(kc.a1, kc.a1), A2 = M::mk(kc.a2, kc.a2), A3 = M::mk(kc.a3, kc.a3), A4 = M::mk(kc.a4, kc.a4),
+             A5 = M::mk(kc.a5, kc.a5);
+    const PT B1 = M::mk(kc.b1, kc.b1), B2 = M::mk(kc.b2, kc.b2), B3 = M::mk(kc.b3, kc.b3), B4 = M::mk(kc.b4, kc.b4),
+             B5 = M::mk(kc.b5, kc.b5);
+    const int n_in = cnt + 4;
+    const int nch = (n_in + CH - 1) / CH;
+    const int32_t tx = int32_t(xs - NC + G);
+    const int32_t ty = int32_t(y0 - 2 + G);
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wbase = smem + warp * S * STAGE_BYTES;
     if (lane == 0) {
-        prefetch_tmap(&tmU);
-        prefetch_tmap(&tmV);
-        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
-        fence_mbar_init();
+        fence_proxy_async();   // earlier generic reads of the ring before async writes
+        const int npro = nch < S ? nch : S;
+        for (int c = 0; c < npro; ++c) {
+            const int slot = (use + c) % S;
+            unsigned char *dst = wbase + slot * STAGE_BYTES;
+            mbar_arrive_expect_tx(&bars[slot], STAGE_BYTES);
+            tma_load_2d(dst, tmU, tx, ty + c * CH, &bars[slot]);
+            tma_load_2d(dst + FIELD_BYTES, tmV, tx, ty + c * CH, &bars[slot]);
+        }
     }
     __syncwarp();
 
-    const Geom &g = a.g;
-    const int64_t xs0 = a.xr.lo & ~int64_t(3);
-    const int64_t nstrips = (a.xr.hi - xs0) / kStrip + 1;
-    const int64_t nrows = a.yr.hi - a.yr.lo + 1;
-    const int64_t total = nstrips * nrows;
-    const int64_t nw = int64_t(gridDim.x) * 4, gw = int64_t(blockIdx.x) * 4 + warp;
-    int64_t cur = total * gw / nw;
-    const int64_t end = total * (gw + 1) / nw;
+    const int64_t x0 = xs - NC + NC * lane;
+    const bool out_lane = lane >= 1 && lane <= 30;
+    // every output row of this segment can use vector stores (the common case)
+    const bool seg_vec = out_lane && x0 >= a.xr.lo && x0 + NC - 1 <= a.xr.hi && x0 >= G &&
+                         x0 + NC - 1 < g.T[0] - G && y0 >= G && y0 + cnt <= g.T[1] - G;
+    T *const pU = Uo + g.origin + (y0 - 4) * g.P + x0;   // output row of input row q: pU + q P
+    T *const pV = Vo + g.origin + (y0 - 4) * g.P + x0;
+    PT u[3][NH], v[3][NH], du[3][NH], dv[3][NH];
+    T ul[3], ur[3], vl[3], vr[3], dul[3], dur[3], dvl[3], dvr[3];
 
-    const T a1 = T(a.c.a1), a2 = T(a.c.a2), a3 = T(a.c.a3), a4 = T(a.c.a4), a5 = T(a.c.a5);
-    const T b1 = T(a.c.b1), b2 = T(a.c.b2), b3 = T(a.c.b3), b4 = T(a.c.b4), b5 = T(a.c.b5);
-    uint32_t use = 0;
-
-    while (cur < end) {
-        const int64_t s = cur / nrows, r0 = cur - s * nrows;
-        const int64_t cnt = (nrows - r0) < (end - cur) ? (nrows - r0) : (end - cur);
-        const int64_t y0 = a.yr.lo + r0;
-        const int64_t xs = xs0 + kStrip * s;
-        const int n_in = int(cnt) + 4;
-        const int nch = (n_in + CH - 1) / CH;
-        const int32_t tx = int32_t(xs - 4 + G);
-        const int32_t ty = int32_t(y0 - 2 + G);
-
-        if (lane == 0) {
-            fence_proxy_async();   // earlier generic reads of the ring before async writes
-            const int npro = nch < S ? nch : S;
-            for (int c = 0; c < npro; ++c) {
-                const int slot = (use + c) % S;
-                unsigned char *dst = wbase + slot * STAGE_BYTES;
-                mbar_arrive_expect_tx(&bars[warp][slot], STAGE_BYTES);
-                tma_load_2d(dst, &tmU, tx, ty + c * CH, &bars[warp][slot]);
-                tma_load_2d(dst + FIELD_BYTES, &tmV, tx, ty + c * CH, &bars[warp][slot]);
-            }
+    // one input row q at ring position j (compile-time after unrolling)
+    auto row = [&](const T *sU, const T *sV, int j, int q, bool d1, bool d2) {
+        const int J0 = j % 3, J1 = (j + 2) % 3, J2 = (j + 1) % 3;   // rows q, q-1, q-2
+#pragma unroll
+        for (int k = 0; k < NH; k += 2) {
+            const V4<T> tu = lds4(sU + 2 * k), tv = lds4(sV + 2 * k);
+            u[J0][k] = M::mk(tu.x, tu.y);
+            u[J0][k + 1] = M::mk(tu.z, tu.w);
+            v[J0][k] = M::mk(tv.x, tv.y);
+            v[J0][k + 1] = M::mk(tv.z, tv.w);
         }
-
-        const int64_t x0 = xs - 4 + 4 * lane;
-        const bool out_lane = lane >= 1 && lane <= 30;
-        const bool full_vec = out_lane && x0 >= a.xr.lo && x0 + 3 <= a.xr.hi && x0 >= G &&
-                              x0 + 3 < g.T[0] - G;
-        V4<T> u[3], v[3], du[3], dv[3];
-
-        for (int c = 0; c < nch; ++c) {
-            const uint32_t uu = use + c;
-            const int slot = uu % S;
-            if (!mbar_wait(&bars[warp][slot], (uu / S) & 1u, a.err, 1)) {
-                // give the copies still in flight a bounded chance to land, then stop
-                for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2)
-                    mbar_wait(&bars[warp][(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0);
-                return;
+        // edges of row q for its difference at the next row
+        ul[J0] = __shfl_up_sync(0xffffffffu, u[J0][NH - 1].y, 1);
+        ur[J0] = __shfl_down_sync(0xffffffffu, u[J0][0].x, 1);
+        vl[J0] = __shfl_up_sync(0xffffffffu, v[J0][NH - 1].y, 1);
+        vr[J0] = __shfl_down_sync(0xffffffffu, v[J0][0].x, 1);
+        if (d1) {
+            diff5p<T, NH>(u[J1], ul[J1], ur[J1], u[J2], u[J0], du[J1]);
+            diff5p<T, NH>(v[J1], vl[J1], vr[J1], v[J2], v[J0], dv[J1]);
+            dul[J1] = __shfl_up_sync(0xffffffffu, du[J1][NH - 1].y, 1);
+            dur[J1] = __shfl_down_sync(0xffffffffu, du[J1][0].x, 1);
+            dvl[J1] = __shfl_up_sync(0xffffffffu, dv[J1][NH - 1].y, 1);
+            dvr[J1] = __shfl_down_sync(0xffffffffu, dv[J1][0].x, 1);
+        }
+        if (d2) {
+            // second differences at row q-2 from DU rows q-3 (slot J0), q-2, q-1
+            PT d2u[NH], d2v[NH], uo[NH], vo[NH];
+            diff5p<T, NH>(du[J2], dul[J2], dur[J2], du[J0], du[J1], d2u);
+            diff5p<T, NH>(dv[J2], dvl[J2], dvr[J2], dv[J0], dv[J1], d2v);
+#pragma unroll
+            for (int k = 0; k < NH; ++k) {
+                const PT uc = u[J2][k], vc = v[J2][k], duc = du[J2][k], dvc = dv[J2][k];
+                if (!ADJ) {
+                    uo[k] = M::add(uc, M::fma(A1, vc, M::fma(A2, duc, M::fma(A3, dvc, M::mul(A4, d2u[k])))));
+                    vo[k] = M::add(vc, M::fma(B2, duc, M::fma(B3, dvc, M::fma(B4, d2u[k], M::mul(B5, d2v[k])))));
+                } else {
+                    uo[k] = M::add(uc, M::fma(A2, duc, M::fma(A3, dvc, M::fma(A4, d2u[k], M::mul(A5, d2v[k])))));
+                    vo[k] = M::add(vc, M::fma(B1, uc, M::fma(B2, duc, M::fma(B3, dvc, M::mul(B5, d2v[k])))));
+                }
             }
-            const T *sU = reinterpret_cast<const T *>(wbase + slot * STAGE_BYTES) + 4 * lane;
-            const T *sV = sU + CH * ROW;
+            if (seg_vec) {
+                T *ru = pU + int64_t(q) * g.P, *rv = pV + int64_t(q) * g.P;
 #pragma unroll
-            for (int j = 0; j < CH; ++j) {
-                const int q = c * CH + j;
-                if (q < n_in) {
-                    const int J0 = j % 3, J1 = (j + 2) % 3, J2 = (j + 1) % 3;  // rows q, q-1, q-2
-                    u[J0] = lds4(sU + j * ROW);
-                    v[J0] = lds4(sV + j * ROW);
-                    if (q >= 2) {
-                        du[J1] = diff5(u[J1], u[J2], u[J0]);
-                        dv[J1] = diff5(v[J1], v[J2], v[J0]);
-                    }
-                    if (q >= 4) {
-                        // second differences at row q-2 from DU rows q-3 (slot J0), q-2, q-1
-                        const V4<T> d2u = diff5(du[J2], du[J0], du[J1]);
-                        const V4<T> d2v = diff5(dv[J2], dv[J0], dv[J1]);
-                        const V4<T> &uc = u[J2], &vc = v[J2], &duc = du[J2], &dvc = dv[J2];
-                        V4<T> uo, vo;
-#define PML_OUT(k)                                                                            \
-    if (!ADJ) {                                                                               \
-        uo.k = uc.k + (a1 * vc.k + (a2 * duc.k + (a3 * dvc.k + a4 * d2u.k)));                \
-        vo.k = vc.k + (b2 * duc.k + (b3 * dvc.k + (b4 * d2u.k + b5 * d2v.k)));               \
-    } else {                                                                                  \
-        uo.k = uc.k + (a2 * duc.k + (a3 * dvc.k + (a4 * d2u.k + a5 * d2v.k)));               \
-        vo.k = vc.k + (b1 * uc.k + (b2 * duc.k + (b3 * dvc.k + b5 * d2v.k)));                \
-    }
-                        PML_OUT(x) PML_OUT(y) PML_OUT(z) PML_OUT(w)
-#undef PML_OUT
-                        const int64_t r = y0 + q - 4;
-                        if (full_vec && r >= G && r < g.T[1] - G) {
-                            const int64_t off = g.origin + r * g.P + x0;
-                            stg4(Uo + off, uo);
-                            stg4(Vo + off, vo);
-                        } else if (out_lane) {
+                for (int k = 0; k < NH; k += 2) {
+                    stg4(ru + 2 * k, V4<T>{uo[k].x, uo[k].y, uo[k + 1].x, uo[k + 1].y});
+                    stg4(rv + 2 * k, V4<T>{vo[k].x, vo[k].y, vo[k + 1].x, vo[k + 1].y});
+                }
+            } else if (out_lane) {
+                const int64_t r = y0 + q - 4;
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const int64_t x = x0 + k;
-                                if (x >= a.xr.lo && x <= a.xr.hi) {
-                                    store_wrapped(Uo, g, x, r, 0, get4(uo, k));
-                                    store_wrapped(Vo, g, x, r, 0, get4(vo, k));
-                                }
-                            }
+                for (int k = 0; k < NC; ++k) {
+                    const int64_t x = x0 + k;
+                    if (x >= a.xr.lo && x <= a.xr.hi) {
+                        const T vu = (k & 1) ? uo[k >> 1].y : uo[k >> 1].x;
+                        const T vv = (k & 1) ? vo[k >> 1].y : vo[k >> 1].x;
+                        if (x >= G && x < g.T[0] - G && r >= G && r < g.T[1] - G) {
+                            Uo[g.origin + r * g.P + x] = vu;
+                            Vo[g.origin + r * g.P + x] = vv;
+                        } else {
+                            store_wrapped(Uo, g, x, r, 0, vu);
+                            store_wrapped(Vo, g, x, r, 0, vv);
                         }
                     }
                 }
             }
-            __syncwarp();
-            if (lane == 0 && c + S < nch) {
-                fence_proxy_async();
-                const int slot2 = (use + c + S) % S;
-                unsigned char *dst = wbase + slot2 * STAGE_BYTES;
-                mbar_arrive_expect_tx(&bars[warp][slot2], STAGE_BYTES);
-                tma_load_2d(dst, &tmU, tx, ty + (c + S) * CH, &bars[warp][slot2]);
-                tma_load_2d(dst + FIELD_BYTES, &tmV, tx, ty + (c + S) * CH, &bars[warp][slot2]);
-            }
         }
-        use += nch;
-        cur += cnt;
-    }
-}
+    };
 
-template <typename T> static size_t interior2d_smem()
-{
-    return size_t(4) * Stages2D<T>::S * 2 * kRows2D * 128 * sizeof(T) + 128;
-}
-
-template <typename T, bool ADJ> static cudaError_t prep_interior2d()
-{
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_interior2d<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(interior2d_smem<T>()));
-    if (e == cudaSuccess) done = true;
-    return e;
-}
-
-int interior2d_max_blocks_per_sm(int prec, bool adjoint)
-{
-    int n = 0;
-    cudaError_t e;
-    if (prec == 32) {
-        if (adjoint) {
-            prep_interior2d<float, true>();
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d<float, true>, 128, interior2d_smem<float>());
-        } else {
-            prep_interior2d<float, false>();
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d<float, false>, 128, interior2d_smem<float>());
+    for (int c = 0; c < nch; ++c) {
+        const uint32_t uu = use + c;
+        const int slot = uu % S;
+        if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 1)) {
+            // give the copies still in flight a bounded chance to land, then stop
+            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2)
+                mbar_wait(&bars[(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0);
+            return false;
         }
-    } else {
-        if (adjoint) {
-            prep_interior2d<double, true>();
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d<double, true>, 128, interior2d_smem<double>());
+        const T *sU = reinterpret_cast<const T *>(wbase + slot * STAGE_BYTES) + NC * lane;
+        const T *sV = sU + CH * ROW;
+        if (c == 0) {   // priming rows: differences start at q = 2, outputs at q = 4
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (j < n_in) row(sU + j * ROW, sV + j * ROW, j, j, j >= 2, j >= 4);
+        } else if (c < nch - 1) {   // steady state: every row complete, no guards
+#pragma unroll
+            for (int j = 0; j < CH; ++j) row(sU + j * ROW, sV + j * ROW, j, c * CH + j, true, true);
         } else {
-            prep_interior2d<double, false>();
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d<double, false>, 128, interior2d_smem<double>());
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (c * CH + j < n_in) row(sU + j * ROW, sV + j * ROW, j, c * CH + j, true, true);
+        }
+        __syncwarp();
+        if (lane == 0 && c + S < nch) {   // slot (use + c + S) % S == slot
+            fence_proxy_async();
+            unsigned char *dst = wbase + slot * STAGE_BYTES;
+            mbar_arrive_expect_tx(&bars[slot], STAGE_BYTES);
+            tma_load_2d(dst, tmU, tx, ty + (c + S) * CH, &bars[slot]);
+            tma_load_2d(dst + FIELD_BYTES, tmV, tx, ty + (c + S) * CH, &bars[slot]);
         }
     }
-    return e == cudaSuccess ? n : 0;
-}
-
-cudaError_t launch_interior2d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
-                              void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st)
-{
-    if (a.xr.lo > a.xr.hi || a.yr.lo > a.yr.hi || grid <= 0) return cudaSuccess;
-    cudaError_t e;
-    if (prec == 32) {
-        if (adjoint) {
-            if ((e = prep_interior2d<float, true>()) != cudaSuccess) return e;
-            k_interior2d<float, true><<<grid, 128, interior2d_smem<float>(), st>>>(*tmU, *tmV, (float *)Uo, (float *)Vo, a);
-        } else {
-            if ((e = prep_interior2d<float, false>()) != cudaSuccess) return e;
-            k_interior2d<float, false><<<grid, 128, interior2d_smem<float>(), st>>>(*tmU, *tmV, (float *)Uo, (float *)Vo, a);
-        }
-    } else {
-        if (adjoint) {
-            if ((e = prep_interior2d<double, true>()) != cudaSuccess) return e;
-            k_interior2d<double, true><<<grid, 128, interior2d_smem<double>(), st>>>(*tmU, *tmV, (double *)Uo, (double *)Vo, a);
-        } else {
-            if ((e = prep_interior2d<double, false>()) != cudaSuccess) return e;
-            k_interior2d<double, false><<<grid, 128, interior2d_smem<double>(), st>>>(*tmU, *tmV, (double *)Uo, (double *)Vo, a);
-        }
-    }
-    return cudaGetLastError();
+    __syncwarp();
+    use += uint32_t(nch);
+    return true;
 }
 
 // ------------------------------------------------------------------------------------
@@ -260,8 +256,8 @@ cudaError_t launch_interior2d(int prec, bool adjoint, const CUtensorMap *tmU, co
 // barrier is needed.  Templated on the axes whose aux fields are active in the strip.
 // ------------------------------------------------------------------------------------
 
-constexpr int kL2CH = 6;     // rows per TMA box (multiple of 3: the register ring period)
-constexpr int kL2S = 4;      // TMA stages per warp
+constexpr int kL2CH = 3;     // rows per TMA box (the register ring period)
+constexpr int kL2S = 8;      // TMA stages per warp: chunks c-2, c-1, c resident, the rest in flight
 
 template <int MASK> struct Fields2 {
     static constexpr int NAX = ((MASK >> 0) & 1) + ((MASK >> 1) & 1);
@@ -335,29 +331,23 @@ __device__ __forceinline__ void issue_chunk2(T *dst, const Maps6 &maps, int32_t 
     for (int f = 0; f < F::NF; ++f) tma_load_2d(dst + f * FE, &maps.m[F::gid(f)], x, y, bar);
 }
 
+// One work item (a strip of one frame rectangle) streamed by one warp; `ring` is the
+// warp's TMA ring (kL2S stages of NF fields x kL2CH rows x 32 columns).
 template <typename T, bool ADJ, int MASK>
-__global__ void __launch_bounds__(128)
-    k_layer2d(const __grid_constant__ Maps6 maps, const Out6 out, const Layer2DArgs a, int base, int count)
+__device__ __forceinline__ void layer2d_item(const Maps6 &maps, const Out6 &out, const Layer2DArgs &a,
+                                          const LayerTile &tile, T *ring, uint64_t *bars, int lane)
 {
     using F = Fields2<MASK>;
     constexpr int NF = F::NF, CH = kL2CH, S = kL2S, FE = CH * 32, SE = NF * FE;
-    __shared__ __align__(8) uint64_t bars[4][S];
-    extern __shared__ unsigned char smem_dyn[];
-    T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * 4 + warp;
-    if (item >= count) return;   // whole warp; the kernel has no block barrier
-    T *ring = smem + warp * S * SE;
-    const LayerTile tile = a.tiles[base + item];
     const Geom &g = a.g;
     const int nout = tile.yhi - tile.ylo + 1, nin = nout + 8;
     const int nch = (nin + CH - 1) / CH;
     const int32_t tx = tile.x0 - 4 + G, ty = tile.ylo - 4 + G;
     if (lane == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
         const int npro = nch < S ? nch : S;
-        for (int c = 0; c < npro; ++c) issue_chunk2<T, MASK>(ring + c * SE, maps, tx, ty + c * CH, &bars[warp][c]);
+        for (int c = 0; c < npro; ++c) issue_chunk2<T, MASK>(ring + c * SE, maps, tx, ty + c * CH, &bars[c]);
     }
     __syncwarp();
 
@@ -366,37 +356,43 @@ __global__ void __launch_bounds__(128)
     const int64_t gx = int64_t(tile.x0) - 4 + lane;
     Sig2<T> sg;
     {
-        const int64_t xi = ((gx % g.T[0]) + g.T[0]) % g.T[0];
+        const int T0 = int(g.T[0]);
+        int xi = int(gx);
+        xi += xi < 0 ? T0 : (xi >= T0 ? -T0 : 0);
         sg.si[0] = sgx[xi];
-        sg.sm[0] = sgx[xi == 0 ? g.T[0] - 1 : xi - 1];
+        sg.sm[0] = sgx[xi == 0 ? T0 - 1 : xi - 1];
     }
-    auto ysig = [&](int q) {
-        int64_t yi = (int64_t(tile.ylo) - 4 + q) % g.T[1];
-        if (yi < 0) yi += g.T[1];
+    const int T1 = int(g.T[1]);
+    auto ysig = [&](int q) {   // rows of a work item lie within one period of [0, T1)
+        int yi = tile.ylo - 4 + q;
+        yi += yi < 0 ? T1 : (yi >= T1 ? -T1 : 0);
         sg.si[1] = sgy[yi];
-        sg.sm[1] = sgy[yi == 0 ? g.T[1] - 1 : yi - 1];
+        sg.sm[1] = sgy[yi == 0 ? T1 - 1 : yi - 1];
     };
     const bool out_lane = lane >= 4 && lane <= 27 && gx >= tile.xlo && gx <= tile.xhi;
-    const T ih = T(1.0 / a.h), ih2 = T(1.0 / (a.h * a.h)), i2h = T(0.5 / a.h);
-    const T c4 = T(a.dt / 4.0), c3 = T(a.dt / 3.0), c2 = T(a.dt / 2.0), c1 = T(a.dt);
+    const LayerConstT<T> &lk = lconst_of<T>(a.k);
+    const T ih = lk.ih, ih2 = lk.ih2, i2h = lk.i2h, c4 = lk.c4, c3 = lk.c3, c2 = lk.c2, c1 = lk.c1;
     T z4[3][NF], z3[3][NF], z2[3][NF];
 
     for (int c = 0; c < nch; ++c) {
-        if (!mbar_wait(&bars[warp][c % S], (c / S) & 1, a.err, 2)) {
-            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2) mbar_wait(&bars[warp][c2 % S], (c2 / S) & 1, nullptr, 0);
+        if (!mbar_wait(&bars[c % S], (c / S) & 1, a.err, 2)) {
+            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2) mbar_wait(&bars[c2 % S], (c2 / S) & 1, nullptr, 0);
             return;
         }
         const T *cur = ring + (c % S) * SE + lane;
         const T *prv = ring + ((c + S - 1) % S) * SE + lane;
+        const T *prv2 = ring + ((c + S - 2) % S) * SE + lane;
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
             const int p = c * CH + j;
             if (p < nin) {
                 const int PH = j % 3;
-                // own-column value of input row p - k, field f (rows of this or the previous chunk)
+                // own-column value of input row p - k (k <= 4), field f: rows of this chunk or
+                // of one of the two before it
                 auto Y = [&](int k, int f) -> T {
                     const int r = j - k;
-                    return r >= 0 ? cur[f * FE + r * 32] : prv[f * FE + (r + CH) * 32];
+                    return r >= 0 ? cur[f * FE + r * 32]
+                                  : (r >= -CH ? prv[f * FE + (r + CH) * 32] : prv2[f * FE + (r + 2 * CH) * 32]);
                 };
                 if (p >= 2) {   // level 4 at row p-1
                     T cen[NF], xm[NF], xp[NF];
@@ -499,48 +495,256 @@ __global__ void __launch_bounds__(128)
             }
         }
         __syncwarp();
-        // chunk c-1 is no longer needed (rows >= c*CH - 4 remain in use): refill it
-        if (lane == 0 && c >= 1 && c - 1 + S < nch) {
+        // chunk c-2 is no longer needed (rows >= (c+1) CH - 4 > (c-1) CH remain in use): refill it
+        if (lane == 0 && c >= 2 && c - 2 + S < nch) {
             fence_proxy_async();
-            const int st = (c - 1) % S;
-            issue_chunk2<T, MASK>(ring + st * SE, maps, tx, ty + (c - 1 + S) * CH, &bars[warp][st]);
+            const int st = (c - 2) % S;
+            issue_chunk2<T, MASK>(ring + st * SE, maps, tx, ty + (c - 2 + S) * CH, &bars[st]);
         }
     }
 }
 
-template <typename T, int MASK> static size_t layer2d_smem()
+// ------------------------------------------------------------------------------------
+// Row-parallel interior kernel (kind 0).  Input row i of a work item is row y0 - 2 + i.
+// U and V live in circular rings of RR = 32 rows (row i in slot (base + i) & 31, base
+// advancing by whole chunks across work items); TMA chunk c brings input rows
+// [c BY, c BY + BY) into one contiguous run of slots.  Block b (outputs y0 + b BY + w,
+// w = warp) needs U/V rows [b BY, b BY + BY + 4) (chunks b, b+1) and first differences of
+// rows [b BY + 1, b BY + BY + 3); it computes those of rows [b BY + 3, b BY + BY + 3)
+// (block 0 also rows 1, 2) into a second 32-row ring, and after one block barrier the
+// second differences and outputs of its BY rows.
+// ------------------------------------------------------------------------------------
+template <typename T, int BY, int NCH> struct I2R {
+    // U/V ring: NCH chunks of BY rows (two resident, NCH - 2 in flight); DU/DV ring: at
+    // least the 2 BY + 2 rows one block reads; both powers of two
+    static constexpr int ROW = 128, RR = NCH * BY, RD = BY <= 4 ? 16 : (BY <= 8 ? 32 : 64);
+    static constexpr uint32_t FB = BY * ROW * sizeof(T);      // one field of one chunk
+    static constexpr size_t SMEM = (2 * size_t(RR) + 2 * size_t(RD)) * ROW * sizeof(T) + 128;
+    static_assert((RR & (RR - 1)) == 0 && NCH >= 3 && RD >= 2 * BY + 2, "ring sizes");
+};
+
+template <typename T, bool ADJ, int BY, int NCH, int MINB>
+__global__ void __launch_bounds__(32 * BY, MINB)
+    k_interior2d_rows(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
+                      T *__restrict__ Uo, T *__restrict__ Vo, const Interior2DArgs a)
 {
-    return size_t(4) * kL2S * Fields2<MASK>::NF * kL2CH * 32 * sizeof(T) + 128;
+    using C = I2R<T, BY, NCH>;
+    using M = Pair<T>;
+    using PT = typename M::P;
+    constexpr int ROW = C::ROW, RR = C::RR, RD = C::RD, NH = 2;
+    __shared__ __align__(8) uint64_t bars[NCH];
+    __shared__ int item_sh;
+    extern __shared__ unsigned char smem_dyn[];
+    T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *const ringU = ring, *const ringV = ring + RR * ROW, *const ringDU = ring + 2 * RR * ROW,
+          *const ringDV = ring + (2 * RR + RD) * ROW;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    if (blockIdx.x == 0 && tid == 0) a.queue[1 - a.parity] = 0;
+    if (tid == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmV);
+        for (int k = 0; k < NCH; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const Geom &g = a.g;
+    const StepCoefT<T> &kc = coef_of<T>(a.c);
+    const int64_t xs0 = a.xr.lo & ~int64_t(3);
+    const int64_t nrows = a.yr.hi - a.yr.lo + 1;
+    const int rblocks = int((nrows + kI2RowsR - 1) / kI2RowsR);
+    const int nstrips = int((a.xr.hi - xs0) / 120 + 1);
+    const int n_items = nstrips * rblocks;
+    uint32_t use = 0;   // chunks consumed by this CTA so far
+    bool ok = true;
+    const int lo4 = 4 * lane;
+
+    auto ld2 = [&](const T *p, PT (&o)[NH]) {
+        const V4<T> t = lds4(p);
+        o[0] = M::mk(t.x, t.y);
+        o[1] = M::mk(t.z, t.w);
+    };
+    // first differences of U and V at input row i into the DU / DV rings
+    auto diff_row = [&](int i) {
+        const int s0 = (int(use) * BY + i) & (RR - 1), sm = (s0 - 1) & (RR - 1), sp = (s0 + 1) & (RR - 1);
+        const int d0 = i & (RD - 1);
+        PT c[NH], up[NH], dn[NH], o[NH];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const T *R = f == 0 ? ringU : ringV;
+            ld2(R + s0 * ROW + lo4, c);
+            ld2(R + sm * ROW + lo4, up);
+            ld2(R + sp * ROW + lo4, dn);
+            const T l = __shfl_up_sync(0xffffffffu, c[NH - 1].y, 1), r = __shfl_down_sync(0xffffffffu, c[0].x, 1);
+            diff5p<T, NH>(c, l, r, up, dn, o);
+            stg4((f == 0 ? ringDU : ringDV) + d0 * ROW + lo4, V4<T>{o[0].x, o[0].y, o[1].x, o[1].y});
+        }
+    };
+
+    for (;;) {
+        if (tid == 0) item_sh = atomicAdd(&a.queue[a.parity], 1);
+        __syncthreads();
+        const int item = item_sh;
+        if (item >= n_items) break;
+        const int st = item / rblocks, rb = item - st * rblocks;
+        const int64_t xs = xs0 + int64_t(120) * st;
+        const int64_t y0 = a.yr.lo + int64_t(rb) * kI2RowsR;
+        const int64_t rem = a.yr.hi - y0 + 1;
+        const int cnt = int(rem < kI2RowsR ? rem : kI2RowsR);
+        const int nblk = (cnt + BY - 1) / BY;
+        const int nch = nblk + 1;   // input rows nblk BY + 4 <= (nblk + 1) BY
+        const int32_t tx = int32_t(xs - 4 + G), ty = int32_t(y0 - 2 + G);
+        auto issue = [&](int c) {
+            const int slot = (use + c) % NCH;
+            const int row0 = (int(use) * BY + c * BY) & (RR - 1);
+            mbar_arrive_expect_tx(&bars[slot], 2 * C::FB);
+            tma_load_2d(ringU + row0 * ROW, &tmU, tx, ty + c * BY, &bars[slot]);
+            tma_load_2d(ringV + row0 * ROW, &tmV, tx, ty + c * BY, &bars[slot]);
+        };
+        auto wait_chunk = [&](int c) {
+            const uint32_t uu = use + c;
+            return mbar_wait(&bars[uu % NCH], (uu / NCH) & 1u, a.err, 5);
+        };
+        if (tid == 0) {
+            fence_proxy_async();
+            for (int c = 0; c < nch && c < NCH; ++c) issue(c);
+        }
+        const int64_t x0 = xs - 4 + lo4;
+        const bool out_lane = lane >= 1 && lane <= 30;
+        const bool col_vec = out_lane && x0 >= a.xr.lo && x0 + 3 <= a.xr.hi && x0 >= G && x0 + 3 < g.T[0] - G;
+        for (int b = 0; b < nblk; ++b) {
+            bool okw = true;
+            if (b == 0) okw = wait_chunk(0);
+            if (okw && b + 1 < nch) okw = wait_chunk(b + 1);
+            ok = __syncthreads_and(okw);
+            if (!ok) break;
+            // chunk b - 1 was last read by block b - 1 (all warps are past it): refill its slots
+            if (tid == 0 && b >= 1 && b - 1 + NCH < nch) {
+                fence_proxy_async();
+                issue(b - 1 + NCH);
+            }
+            if (b == 0) {
+                diff_row(1 + w);
+                if (w < 2) diff_row(BY + 1 + w);
+            } else {
+                diff_row(b * BY + 3 + w);
+            }
+            __syncthreads();
+            // second differences and outputs of input row i = b BY + 2 + w
+            const int i = b * BY + 2 + w;
+            const int64_t y = y0 + b * BY + w;
+            if (y < y0 + cnt) {
+                const int s0 = (int(use) * BY + i) & (RR - 1);
+                const int d0 = i & (RD - 1), dm = (i - 1) & (RD - 1), dp = (i + 1) & (RD - 1);
+                PT uc[NH], vc[NH], duc[NH], dvc[NH], d2u[NH], d2v[NH], up[NH], dn[NH], uo[NH], vo[NH];
+                ld2(ringU + s0 * ROW + lo4, uc);
+                ld2(ringV + s0 * ROW + lo4, vc);
+                ld2(ringDU + d0 * ROW + lo4, duc);
+                ld2(ringDU + dm * ROW + lo4, up);
+                ld2(ringDU + dp * ROW + lo4, dn);
+                {
+                    const T l = __shfl_up_sync(0xffffffffu, duc[NH - 1].y, 1), r = __shfl_down_sync(0xffffffffu, duc[0].x, 1);
+                    diff5p<T, NH>(duc, l, r, up, dn, d2u);
+                }
+                ld2(ringDV + d0 * ROW + lo4, dvc);
+                ld2(ringDV + dm * ROW + lo4, up);
+                ld2(ringDV + dp * ROW + lo4, dn);
+                {
+                    const T l = __shfl_up_sync(0xffffffffu, dvc[NH - 1].y, 1), r = __shfl_down_sync(0xffffffffu, dvc[0].x, 1);
+                    diff5p<T, NH>(dvc, l, r, up, dn, d2v);
+                }
+                const PT A1 = M::mk(kc.a1, kc.a1), A2 = M::mk(kc.a2, kc.a2), A3 = M::mk(kc.a3, kc.a3),
+                         A4 = M::mk(kc.a4, kc.a4), A5 = M::mk(kc.a5, kc.a5);
+                const PT B1 = M::mk(kc.b1, kc.b1), B2 = M::mk(kc.b2, kc.b2), B3 = M::mk(kc.b3, kc.b3),
+                         B4 = M::mk(kc.b4, kc.b4), B5 = M::mk(kc.b5, kc.b5);
+#pragma unroll
+                for (int k = 0; k < NH; ++k) {
+                    if (!ADJ) {
+                        uo[k] = M::add(uc[k], M::fma(A1, vc[k], M::fma(A2, duc[k], M::fma(A3, dvc[k], M::mul(A4, d2u[k])))));
+                        vo[k] = M::add(vc[k], M::fma(B2, duc[k], M::fma(B3, dvc[k], M::fma(B4, d2u[k], M::mul(B5, d2v[k])))));
+                    } else {
+                        uo[k] = M::add(uc[k], M::fma(A2, duc[k], M::fma(A3, dvc[k], M::fma(A4, d2u[k], M::mul(A5, d2v[k])))));
+                        vo[k] = M::add(vc[k], M::fma(B1, uc[k], M::fma(B2, duc[k], M::fma(B3, dvc[k], M::mul(B5, d2v[k])))));
+                    }
+                }
+                if (col_vec && y >= G && y < g.T[1] - G) {
+                    const int64_t off = g.origin + y * g.P + x0;
+                    stg4(Uo + off, V4<T>{uo[0].x, uo[0].y, uo[1].x, uo[1].y});
+                    stg4(Vo + off, V4<T>{vo[0].x, vo[0].y, vo[1].x, vo[1].y});
+                } else if (out_lane) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int64_t x = x0 + k;
+                        if (x >= a.xr.lo && x <= a.xr.hi) {
+                            store_wrapped(Uo, g, x, y, 0, (k & 1) ? uo[k >> 1].y : uo[k >> 1].x);
+                            store_wrapped(Vo, g, x, y, 0, (k & 1) ? vo[k >> 1].y : vo[k >> 1].x);
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok) break;
+        use += uint32_t(nch);
+        __syncthreads();   // the next item's prologue reuses the rings
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <typename T, bool ADJ, int MASK>
-static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, cudaStream_t st)
+// ------------------------------------------------------------------------------------
+// Launch structure of one 2D step (two kernels, disjoint outputs):
+//  1. k_layer2d: one warp per frame strip (latency bound, long); it lets the next
+//     kernel start right away (programmatic dependent launch).
+//  2. k_interior2d: persistent; warps take interior segments of kI2Rows rows from a work
+//     queue (atomic counter), so SMs that start late, while layer warps still run, or
+//     that run slower simply take fewer segments.  The counter of this launch is
+//     queue[parity]; block 0 clears queue[1 - parity] for the next launch (the next launch
+//     follows the next layer kernel, which waits for this one to finish).
+// ------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void allow_dependent_launch()
 {
-    const int n = a.class_off[MASK + 1] - a.class_off[MASK];
-    if (n <= 0) return cudaSuccess;
-    static bool done = false;
-    const size_t sm = layer2d_smem<T, MASK>();
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_layer2d<T, ADJ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
-    k_layer2d<T, ADJ, MASK><<<(n + 3) / 4, 128, sm, st>>>(m, o, a, a.class_off[MASK], n);
-    return cudaGetLastError();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 template <typename T, bool ADJ>
-static cudaError_t launch_l2_all(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, cudaStream_t st)
+__global__ void __launch_bounds__(128)
+    k_layer2d(const __grid_constant__ Maps6 maps, const Out6 out, const Layer2DArgs a)
 {
-    cudaError_t e;
-    if ((e = launch_l2<T, ADJ, 0>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l2<T, ADJ, 1>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l2<T, ADJ, 2>(m, o, a, st)) != cudaSuccess) return e;
-    return launch_l2<T, ADJ, 3>(m, o, a, st);
+    constexpr int SE = 6 * kL2CH * 32;   // ring stage sized for the largest class
+    __shared__ __align__(8) uint64_t bars[4][kL2S];
+    extern __shared__ unsigned char smem_dyn[];
+    T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    allow_dependent_launch();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * 4 + warp;
+    if (item >= a.ntiles) return;   // whole warp; the kernel has no block barrier
+    T *ring = smem + warp * kL2S * SE;
+    const LayerTile tile = a.tiles[item];
+    switch (tile.flags & 3) {
+    case 0: layer2d_item<T, ADJ, 0>(maps, out, a, tile, ring, bars[warp], lane); break;
+    case 1: layer2d_item<T, ADJ, 1>(maps, out, a, tile, ring, bars[warp], lane); break;
+    case 2: layer2d_item<T, ADJ, 2>(maps, out, a, tile, ring, bars[warp], lane); break;
+    default: layer2d_item<T, ADJ, 3>(maps, out, a, tile, ring, bars[warp], lane); break;
+    }
 }
 
-cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp,
-                           const Layer2DArgs &a, cudaStream_t st)
+template <typename T> static size_t layer2d_smem() { return size_t(4) * kL2S * 6 * kL2CH * 32 * sizeof(T) + 128; }
+
+template <typename T, bool ADJ>
+static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, cudaStream_t st)
+{
+    static bool done = false;
+    const size_t sm = layer2d_smem<T>();
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_layer2d<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    k_layer2d<T, ADJ><<<(a.ntiles + 3) / 4, 128, sm, st>>>(m, o, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp, const Layer2DArgs &a,
+                           cudaStream_t st)
 {
     if (a.ntiles <= 0) return cudaSuccess;
     Maps6 m;
@@ -549,8 +753,165 @@ cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *
         m.m[f] = tm[f];
         o.p[f] = outp[f];
     }
-    if (prec == 32) return adjoint ? launch_l2_all<float, true>(m, o, a, st) : launch_l2_all<float, false>(m, o, a, st);
-    return adjoint ? launch_l2_all<double, true>(m, o, a, st) : launch_l2_all<double, false>(m, o, a, st);
+    if (prec == 32) return adjoint ? launch_l2<float, true>(m, o, a, st) : launch_l2<float, false>(m, o, a, st);
+    return adjoint ? launch_l2<double, true>(m, o, a, st) : launch_l2<double, false>(m, o, a, st);
+}
+
+template <typename T, bool ADJ, int NC, int CH, int S, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    k_interior2d(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
+                 T *__restrict__ Uo, T *__restrict__ Vo, const Interior2DArgs a)
+{
+    constexpr size_t WB = size_t(S) * 2 * CH * 32 * NC * sizeof(T);
+    __shared__ __align__(8) uint64_t bars[4][S];
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem + warp * WB;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.queue[1 - a.parity] = 0;
+    if (lane == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmV);
+        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t use = 0;
+    const int64_t xs0 = a.xr.lo & ~int64_t(3);
+    const int64_t nrows = a.yr.hi - a.yr.lo + 1;
+    const int rblocks = int((nrows + kI2Rows - 1) / kI2Rows);
+    const int nstrips = int((a.xr.hi - xs0) / (30 * NC) + 1);
+    const int n_items = nstrips * rblocks;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&a.queue[a.parity], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int st = item / rblocks, rb = item - st * rblocks;
+        const int64_t y0 = a.yr.lo + int64_t(rb) * kI2Rows;
+        const int64_t rem = a.yr.hi - y0 + 1;
+        if (!interior2d_seg<T, ADJ, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(30 * NC) * st, y0,
+                                               int(rem < kI2Rows ? rem : kI2Rows), wbase, bars[warp], lane, use))
+            break;
+    }
+    // When this launch overlapped the layer kernel, finish only after it: later work in the
+    // stream then sees both halves of the step.  (Every layer CTA has started before this
+    // kernel could, so the wait cannot block a layer CTA from running.)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename T, bool ADJ, int NC, int CH, int S, int MINB> struct I2Kernel {
+    static constexpr size_t smem() { return size_t(4) * S * 2 * CH * 32 * NC * sizeof(T) + 128; }
+    static cudaError_t prep()
+    {
+        static bool done = false;
+        if (done) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(k_interior2d<T, ADJ, NC, CH, S, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e == cudaSuccess) done = true;
+        return e;
+    }
+    static int occupancy()
+    {
+        if (prep() != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d<T, ADJ, NC, CH, S, MINB>, 128, smem()) !=
+            cudaSuccess)
+            return 0;
+        return n;
+    }
+    static cudaError_t launch(const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo, void *Vo,
+                              const Interior2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+    {
+        cudaError_t e = prep();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = overlap_previous ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, k_interior2d<T, ADJ, NC, CH, S, MINB>, *tmU, *tmV, (T *)Uo, (T *)Vo, a);
+    }
+};
+
+template <typename T, bool ADJ, int BY, int NCH, int MINB> struct I2RKernel {
+    static constexpr size_t smem() { return I2R<T, BY, NCH>::SMEM; }
+    static cudaError_t prep()
+    {
+        static bool done = false;
+        if (done) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(k_interior2d_rows<T, ADJ, BY, NCH, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e == cudaSuccess) done = true;
+        return e;
+    }
+    static int occupancy()
+    {
+        if (prep() != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d_rows<T, ADJ, BY, NCH, MINB>, 32 * BY, smem()) !=
+            cudaSuccess)
+            return 0;
+        return n;
+    }
+    static cudaError_t launch(const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo, void *Vo,
+                              const Interior2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+    {
+        cudaError_t e = prep();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(32 * BY);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = overlap_previous ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, k_interior2d_rows<T, ADJ, BY, NCH, MINB>, *tmU, *tmV, (T *)Uo, (T *)Vo, a);
+    }
+};
+
+// dispatch over the variant tables (index v of kI2Vars32 / kI2Vars64)
+template <bool ADJ, typename F> static auto with_i2(int prec, int v, F &&f)
+{
+    if (prec == 32) {
+        switch (v) {
+        case 0: return f(I2Kernel<float, ADJ, 4, 6, 3, 3>{});
+        case 1: return f(I2RKernel<float, ADJ, 8, 8, 2>{});
+        case 2: return f(I2RKernel<float, ADJ, 4, 8, 4>{});
+        case 3: return f(I2Kernel<float, ADJ, 4, 6, 2, 4>{});
+        default: return f(I2Kernel<float, ADJ, 8, 3, 3, 2>{});
+        }
+    }
+    switch (v) {
+    case 0: return f(I2RKernel<double, ADJ, 4, 8, 3>{});
+    case 1: return f(I2RKernel<double, ADJ, 8, 4, 1>{});
+    case 2: return f(I2Kernel<double, ADJ, 4, 6, 2, 2>{});
+    default: return f(I2Kernel<double, ADJ, 4, 3, 3, 2>{});
+    }
+}
+
+int interior2d_max_blocks_per_sm(int prec, bool adjoint, int v)
+{
+    auto occ = [](auto k) { return decltype(k)::occupancy(); };
+    return adjoint ? with_i2<true>(prec, v, occ) : with_i2<false>(prec, v, occ);
+}
+
+cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                              void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
+                              bool overlap_previous)
+{
+    if (a.xr.lo > a.xr.hi || a.yr.lo > a.yr.hi || grid <= 0) return cudaSuccess;
+    auto go = [&](auto k) { return decltype(k)::launch(tmU, tmV, Uo, Vo, a, grid, st, overlap_previous); };
+    return adjoint ? with_i2<true>(prec, v, go) : with_i2<false>(prec, v, go);
 }
 
 }  // namespace pml

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
     int64_t cur = total * blockIdx.x / gridDim.x;
     const int64_t end = total * (blockIdx.x + 1) / gridDim.x;
 
-    const T a1 = T(a.c.a1), a2 = T(a.c.a2), a3 = T(a.c.a3), a4 = T(a.c.a4), a5 = T(a.c.a5);
-    const T b1 = T(a.c.b1), b2 = T(a.c.b2), b3 = T(a.c.b3), b4 = T(a.c.b4), b5 = T(a.c.b5);
+    const StepCoefT<T> &kc = coef_of<T>(a.c);
+    const T a1 = kc.a1, a2 = kc.a2, a3 = kc.a3, a4 = kc.a4, a5 = kc.a5;
+    const T b1 = kc.b1, b2 = kc.b2, b3 = kc.b3, b4 = kc.b4, b5 = kc.b5;
     uint32_t use = 0;
 
     while (cur < end) {
@@ -338,8 +339,8 @@ __device__ __forceinline__ void issue_plane3(T *stage_base, const Maps8 &maps, c
 {
     using F = Fields<MASK>;
     constexpr int PL = L3<T>::PL;
-    int64_t z = zin % g.T[2];
-    if (z < 0) z += g.T[2];
+    int64_t z = zin;
+    z += z < 0 ? g.T[2] : (z >= g.T[2] ? -g.T[2] : 0);
     mbar_arrive_expect_tx(bar, uint32_t(F::NF * PL * sizeof(T)));
 #pragma unroll
     for (int f = 0; f < F::NF; ++f)
@@ -386,19 +387,20 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
     }
     __syncthreads();
 
-    const T ih = T(1.0 / a.h), ih2 = T(1.0 / (a.h * a.h)), i2h = T(0.5 / a.h);
-    const T c4 = T(a.dt / 4.0), c3 = T(a.dt / 3.0), c2 = T(a.dt / 2.0), c1 = T(a.dt);
+    const LayerConstT<T> &lk = lconst_of<T>(a.k);
+    const T ih = lk.ih, ih2 = lk.ih2, i2h = lk.i2h, c4 = lk.c4, c3 = lk.c3, c2 = lk.c2, c1 = lk.c1;
     T z4r[3][NF], z3r[3][NF], z2r[3][NF];
     Sig3<T> sg;
     sg.si[0] = sx[cx + 1];
     sg.sm[0] = sx[cx];
     sg.si[1] = sy[cy + 1];
     sg.sm[1] = sy[cy];
-    auto zsig = [&](int64_t zl, Sig3<T> &s) {
-        int64_t z = zl % g.T[2];
-        if (z < 0) z += g.T[2];
+    const int T2 = int(g.T[2]);
+    auto zsig = [&](int64_t zl, Sig3<T> &s) {   // planes of a work item lie within [-4, 2 T2)
+        int z = int(zl);
+        z += z < 0 ? T2 : (z >= T2 ? -T2 : 0);
         s.si[2] = sgz[z];
-        s.sm[2] = sgz[z == 0 ? g.T[2] - 1 : z - 1];
+        s.sm[2] = sgz[z == 0 ? T2 - 1 : z - 1];
     };
     const bool v4 = cx >= 1 && cx <= RX - 2 && cy >= 1 && cy <= RY - 2;
     const bool v3 = cx >= 2 && cx <= RX - 3 && cy >= 2 && cy <= RY - 3;
@@ -517,8 +519,8 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         T r[NF];
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
                         const T *Y = stage + (q % S) * NF * PL;
-                        int64_t z = zl % g.T[2];
-                        if (z < 0) z += g.T[2];
+                        int64_t z = zl;
+                        z += z < 0 ? T2 : (z >= T2 ? -T2 : 0);
                         const bool edge = near_edge(g, gx, gy, z);
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {

@@ -65,6 +65,32 @@ def test_forward_parity(N, w, sigma, prec):
         assert err <= TOL[prec], (f, err)
 
 
+def test_every_interior_variant_matches_oracle():
+    """Each shape of the layer-free kernel the autotuner may pick, forward and adjoint."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    N, w = (290, 61), 7
+    T = tuple(n + 2 * w for n in N)
+    rng = np.random.default_rng(31)
+    u0 = gaussian_u0(N, w, 4) + rng.normal(scale=0.2, size=T[::-1])
+    g = oracle_grid(N, w)
+    y = g.zeros_state()
+    y[0] = u0.reshape(-1)
+    want, _ = oracle.rk4(g, y, 13, 0.5)
+    for prec in (64, 32):
+        s = make_solver(N, w, prec, adjoint=True)
+        _, nv = _lib.pml_get_variant(s.ctx)
+        assert nv >= 2
+        for v in range(nv):
+            _lib.pml_set_variant(s.ctx, v)
+            s.set_initial(torch.from_numpy(u0))
+            s.step(13)
+            for f in range(6):
+                err = rel_l2(s.read(f).double().cpu().numpy(), want[f])
+                assert err <= TOL[prec], (prec, v, f, err)
+        s.close()
+
+
 @pytest.mark.parametrize("N,w,sigma", CASES[:4])
 def test_layout_tables_bit_exact(N, w, sigma):
     rng = np.random.default_rng(3)
