@@ -241,6 +241,34 @@ pml_status pml_get_variant(const pml_ctx *ctx, int *variant, int *count);
 pml_status pml_set_variant(pml_ctx *ctx, int variant);
 pml_status pml_autotune(pml_ctx *ctx, int steps, double *times_ms, int *chosen);
 
+/*
+ * FP64 energy and norms of a dense field pair, computed without allocating any device
+ * memory.  The paper has no counterpart: this serves callers that cannot allocate device
+ * memory when they need the numbers, such as services that reserve all their memory at
+ * start-up and must not allocate afterwards, or processes whose device memory is owned by
+ * another allocator or capped by a fixed budget.
+ *
+ *   ndim, T      2 or 3 axes, T[a] vertices per axis; U, V are dense row-major
+ *                [T2][T1][T0] device arrays of the given precision (32 or 64)
+ *   wlo, whi     inclusive window per axis, 0 <= wlo <= whi < T
+ *   h            grid spacing; ref: NULL or a device FP64 array of the window shape
+ *   cuda_stream  stream the two reduction kernels run on; the call synchronises it
+ *   out          host double[5]: the energy eq:Energy over the window (forward
+ *                differences wrap periodically at the box edge), max |U|, ||U||_2,
+ *                ||U - ref||_2, max |U - ref|, exactly as pml_norms reports them
+ *
+ * The per-row partial sums live in one fixed array of this library's device memory
+ * (16384 rows x 5 doubles, 640 KB, held on every device that uses it until the process
+ * exits).  A window with more than 16384 rows (y extent times z extent) is rejected with
+ * PML_EINVAL.  The first call on a device looks up that array's device address, so make it
+ * before any stream capture.  Every call reuses the same array and overwrites the partials
+ * it reads, so results never mix across calls; but two calls whose kernels overlap on the
+ * GPU (other streams, other host threads) race for it: serialise them.
+ */
+pml_status pml_norms_dense_static(int ndim, const int64_t *T, int precision, const void *U, const void *V,
+                                  const int64_t *wlo, const int64_t *whi, double h, const double *ref,
+                                  void *cuda_stream, double *out);
+
 void pml_destroy(pml_ctx *ctx);
 const char *pml_last_error(const pml_ctx *ctx);
 const char *pml_status_string(pml_status s);

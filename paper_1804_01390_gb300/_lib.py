@@ -48,7 +48,7 @@ EXPORTED = (
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
     "pml_adjoint_read_field", "pml_state_bytes", "pml_save_state", "pml_load_state",
     "pml_get_variant", "pml_set_variant", "pml_autotune",
-    "pml_profile_enable", "pml_profile_read", "pml_destroy", "pml_last_error",
+    "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static", "pml_destroy", "pml_last_error",
     "pml_status_string",
 )
 
@@ -110,6 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_get_variant": [P, P, P],
         "pml_set_variant": [P, ctypes.c_int],
         "pml_autotune": [P, ctypes.c_int, P, P],
+        "pml_norms_dense_static": [ctypes.c_int, P, ctypes.c_int, P, P, P, P, ctypes.c_double, P, P, P],
         "pml_profile_read": [P, P, P],
     }
     for name, args in sig.items():
@@ -260,6 +261,19 @@ def pml_profile_read(ctx):
     n = np.zeros(3, dtype=np.int64)
     _check(load().pml_profile_read(ctx, ms.ctypes.data, n.ctypes.data), ctx)
     return ms, n
+
+
+def pml_norms_dense_static(ndim, T, precision, U, V, wlo, whi, h, ref, stream):
+    """Energy and norms of dense device arrays U, V (pointers) over the inclusive window
+    wlo..whi, with no device allocation.  Returns a numpy array of 5 doubles."""
+    import numpy as np
+    Ta = np.ascontiguousarray(list(T) + [1] * (3 - len(T)), dtype=np.int64)
+    lo = np.ascontiguousarray(list(wlo) + [0] * (3 - len(wlo)), dtype=np.int64)
+    hi = np.ascontiguousarray(list(whi) + [0] * (3 - len(whi)), dtype=np.int64)
+    out = np.zeros(5, dtype=np.float64)
+    _check(load().pml_norms_dense_static(int(ndim), Ta.ctypes.data, int(precision), U, V, lo.ctypes.data,
+                                         hi.ctypes.data, float(h), ref, stream, out.ctypes.data))
+    return out
 
 
 def pml_destroy(ctx):

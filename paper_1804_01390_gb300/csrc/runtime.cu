@@ -559,6 +559,11 @@ pml_status encode_interior_maps(pml_ctx *c)
 
 }  // namespace
 
+namespace pml {
+// error text of context-free calls (read back by pml_last_error(NULL))
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace pml
+
 extern "C" {
 
 const char *pml_status_string(pml_status s)
