@@ -272,6 +272,35 @@ def run_ours(args, ws, rank, local):
         s.close()
         del s
 
+    # ---- 3D (512^3 + 24-cell layer, FP32, 8 Ricker sources) ---------------------------
+    d3 = None
+    if not args.no_3d:
+        wl3 = wk.cfg3() if args.n3 is None else wk.cfg3(N=args.n3)
+        K3 = max(K // 20, 10)
+        s = PMLSolver(wl3.N, wl3.w, dt=wl3.dt, precision=32, device=dev)
+        u3 = torch.from_numpy(wk.initial_field(wl3, dtype=np.float32)).to(dev)
+        s.set_initial(u3)
+        src = wl3.sources
+        s.set_sources(src["coords"], src["amp"], src["f_peak"], src["t_delay"])
+        ms3, _ = timed_steps(s, K3, min(W, 3), ws, profile=False)
+        ms3 = max_over_ranks(ms3, ws, dev)
+        ms3p, prof3 = timed_steps(s, K3, 0, ws, profile=True)
+        m3, n3 = prof3
+        pts3 = wl3.points
+        int3 = int(np.prod([n - 2 for n in wl3.N]))
+        t_int3 = m3[0] / max(n3[0], 1) / 1e3
+        ach3 = int3 * 16 / t_int3 / 1e9
+        d3 = {"workload": "3D %d^3 interior + %d-cell quadratic PML (T = %d^3), Gaussian s=6 + 8 Ricker sources, FP32"
+                          % (wl3.N[0], wl3.w, wl3.T[0]),
+              "value": pts3 * K3 * ws / (ms3 / 1e3) / 1e9, "unit": UNIT, "steps": K3, "ms_per_step": ms3 / K3,
+              "roofline": {"bound": "hbm", "kernel": "k_interior3d<float>", "achieved": ach3, "peak": hbm_peak,
+                           "unit": "GB/s", "frac": ach3 / hbm_peak, "avg_launch_ms": t_int3 * 1e3,
+                           "bytes_per_launch": int3 * 16},
+              "kernel_ms_per_step": {"interior": m3[0] / max(n3[0], 1), "layer": m3[1] / max(n3[0], 1),
+                                     "points": m3[2] / max(n3[0], 1)}}
+        s.close()
+        del s, u3
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -293,6 +322,7 @@ def run_ours(args, ws, rank, local):
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
+            "cfg3": d3,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -367,6 +397,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--n3", type=int, default=None, help="3D physical side (default 512)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
     ap.add_argument("--n", type=int, default=None,

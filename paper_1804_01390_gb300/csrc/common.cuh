@@ -279,6 +279,8 @@ struct Interior3DArgs {
     Range xr, yr, zr;
     StepCoef c;
     DeviceError *err;
+    int *queue;                // work counters (this launch: queue[parity])
+    int parity;
 };
 cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
                               void *Uo, void *Vo, const Interior3DArgs &a, int grid,

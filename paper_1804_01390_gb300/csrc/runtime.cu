@@ -340,7 +340,7 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
                     }
                     int fl = 0;
                     if (axis_active(c, 0, x0 - 4, x0 + TX + 4)) fl |= 1;
-                    if (axis_active(c, 1, L.ylo - 4, (d3 ? y0 + TY : L.yhi + 1) + 4)) fl |= 2;
+                    if (d3 ? axis_active(c, 1, y0 - 4, y0 + TY + 4) : axis_active(c, 1, L.ylo - 4, L.yhi + 5)) fl |= 2;
                     if (d3 && axis_active(c, 2, L.zlo - 4, L.zhi + 5)) fl |= 4;
                     L.flags = fl;
                     t.push_back(L);
@@ -508,6 +508,10 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
     } else {
         Interior3DArgs a{};
         a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
+        int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
+        a.queue = c->dqueue + (adjoint ? 2 : 0);
+        a.parity = int(nl & 1);
+        if (!range_empty(ir[0]) && !range_empty(ir[1]) && !range_empty(ir[2])) ++nl;
         long pi = prof_begin(c, 0);
         e = launch_interior3d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
                               adjoint ? c->grid_int_adj : c->grid_int, c->st);

@@ -23,6 +23,7 @@ namespace pml {
 constexpr int kBY3 = 8;        // interior output rows per CTA
 constexpr int kStrip3 = 120;   // interior output columns per CTA (lanes 1..30)
 constexpr int kS3 = 4;         // interior TMA plane stages
+constexpr int kZSeg3 = 64;     // z planes per interior work item
 
 int interior3d_box_rows(int) { return 1; }
 int interior3d_tile_y() { return kBY3; }
@@ -77,18 +78,26 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
     const int64_t nstrips = (a.xr.hi - xs0) / kStrip3 + 1;
     const int64_t nty = (a.yr.hi - a.yr.lo) / kBY3 + 1;
     const int64_t nz = a.zr.hi - a.zr.lo + 1;
-    const int64_t total = nstrips * nty * nz;
-    int64_t cur = total * blockIdx.x / gridDim.x;
-    const int64_t end = total * (blockIdx.x + 1) / gridDim.x;
+    const int nzs = int((nz + kZSeg3 - 1) / kZSeg3);
+    const int n_items = int(nstrips * nty) * nzs;
+    __shared__ int item_sh;
+    if (blockIdx.x == 0 && tid == 0) a.queue[1 - a.parity] = 0;
 
     const StepCoefT<T> &kc = coef_of<T>(a.c);
     const T a1 = kc.a1, a2 = kc.a2, a3 = kc.a3, a4 = kc.a4, a5 = kc.a5;
     const T b1 = kc.b1, b2 = kc.b2, b3 = kc.b3, b4 = kc.b4, b5 = kc.b5;
     uint32_t use = 0;
 
-    while (cur < end) {
-        const int64_t col = cur / nz, zi = cur - col * nz;
-        const int64_t cnt = (nz - zi) < (end - cur) ? (nz - zi) : (end - cur);
+    for (;;) {
+        // work item: (x strip s, y tile t, z segment) taken from the queue
+        if (tid == 0) item_sh = atomicAdd(&a.queue[a.parity], 1);
+        __syncthreads();
+        const int item = item_sh;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int64_t col = item / nzs, zs = item - col * nzs;
+        const int64_t zi = zs * kZSeg3;
+        const int64_t cnt = (nz - zi) < kZSeg3 ? (nz - zi) : kZSeg3;
         const int64_t s = col / nty, t = col - s * nty;
         const int64_t xs = xs0 + kStrip3 * s, y0 = a.yr.lo + kBY3 * t, z0 = a.zr.lo + zi;
         const int n_in = int(cnt) + 4;
@@ -195,7 +204,6 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
         __syncthreads();
         if (!ok) return;
         use += n_in;
-        cur += cnt;
     }
 }
 
