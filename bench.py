@@ -301,6 +301,62 @@ def run_ours(args, ws, rank, local):
         s.close()
         del s, u3
 
+    # ---- batched: 96 grids of uneven sizes, one launch pair per step, graph replay ------
+    d4 = None
+    if not args.no_batch:
+        from paper_1804_01390_gb300.solver import PMLBatch
+        wls = wk.cfg4() if args.n4 is None else wk.cfg4(hi=args.n4, lo=min(256, args.n4))
+        K4 = 32 * max(K // 64, 2)
+        solvers = []
+        for wl4 in wls:
+            s4 = PMLSolver(wl4.N, wl4.w, dt=wl4.dt, precision=32, device=dev)
+            solvers.append(s4)
+        inits4 = [torch.from_numpy(wk.initial_field(wl4, dtype=np.float32)).to(dev) for wl4 in wls]
+        for s4, u4 in zip(solvers, inits4):
+            s4.set_initial(u4)
+        b4 = PMLBatch(solvers)
+        var4, tune4 = b4.autotune(32)
+        for s4, u4 in zip(solvers, inits4):
+            s4.set_initial(u4)
+        stream4 = solvers[0].stream
+        b4.step(max(W, 3))
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream4)
+        b4.step(K4)
+        e1.record(stream4)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms4 = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        b4.profile(True)
+        b4.step(64)
+        m4, n4 = b4.profile_read()
+        b4.profile(False)
+        pts4 = sum(wl4.points for wl4 in wls)
+        int4 = 0
+        for s4 in solvers:
+            int4 += int(np.prod([int(s4.layout(a)[2].sum()) for a in range(2)]))
+        t_int4 = m4[0] / max(n4[0], 1) / 1e3
+        ach4 = int4 * 16 / t_int4 / 1e9
+        ngrid, items4, tiles4, ctas4 = b4.info()
+        d4 = {"workload": "96 independent 2D grids, sides uniform in [%d, %d], quadratic PML 16..32 cells, "
+                          "one Gaussian s=4 each, FP32" % (min(min(w.N) for w in wls), max(max(w.N) for w in wls)),
+              "value": pts4 * K4 * ws / (ms4 / 1e3) / 1e9, "unit": UNIT, "steps": K4, "ms_per_step": ms4 / K4,
+              "points": pts4, "interior_points": int4, "variant": var4, "autotune_ms_per_step": list(tune4),
+              "work_items": items4, "layer_tiles": tiles4, "interior_ctas": ctas4,
+              "launch": "CUDA graph of 32 steps (one layer + one interior launch per step over all grids)",
+              "roofline": {"bound": "hbm", "kernel": "k_interior2d_batch<float>", "achieved": ach4, "peak": hbm_peak,
+                           "unit": "GB/s", "frac": ach4 / hbm_peak, "avg_launch_ms": t_int4 * 1e3,
+                           "bytes_per_launch": int4 * 16},
+              "kernel_ms_per_step": {"interior": m4[0] / max(n4[0], 1), "layer": m4[1] / max(n4[1], 1)}}
+        b4.close()
+        for s4 in solvers:
+            s4.close()
+        del solvers, inits4, b4
+        torch.cuda.synchronize()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -322,7 +378,7 @@ def run_ours(args, ws, rank, local):
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
-            "cfg3": d3,
+            "cfg3": d3, "batched": d4,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -399,6 +455,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--n3", type=int, default=None, help="3D physical side (default 512)")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--n4", type=int, default=None, help="largest side of the batched grids (default 2048)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
     ap.add_argument("--n", type=int, default=None,

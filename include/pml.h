@@ -269,6 +269,45 @@ pml_status pml_norms_dense_static(int ndim, const int64_t *T, int precision, con
                                   const int64_t *wlo, const int64_t *whi, double h, const double *ref,
                                   void *cuda_stream, double *out);
 
+/*
+ * Batched stepping of many independent 2D grids ("shots" of uneven sizes).  The paper
+ * has no counterpart: each grid is an ordinary context (pml_create) and keeps its own
+ * sizes, layer width, damping, h and dt; a batch advances all of them together with one
+ * layer-kernel launch and one interior-kernel launch per step, both spanning every grid
+ * (work items of all grids share one queue), and replays runs of 32 steps from a CUDA
+ * graph it captures once per kernel variant.  Each step of each grid is the same RK4
+ * step of Eq. 3 as pml_step computes.
+ *
+ * pml_batch_create: the contexts must all be 2D, of one precision, on one stream, and
+ *   distinct; they must outlive the batch.  The batch allocates its own device tables
+ *   (one descriptor of about 2.6 KB per grid plus the layer tile list) with cudaMalloc.
+ * pml_batch_step: n steps of every grid (asynchronous on the contexts' stream).  All
+ *   contexts must be at the same ping-pong parity (as after pml_set_initial, or after
+ *   equal numbers of steps) and have no sources or receivers (PML_ESTATE otherwise).
+ *   Each context's step counter advances by n; pml_step, pml_read_field, pml_norms and
+ *   the rest keep working on each context between batch steps.
+ * pml_batch_get_variant / pml_batch_set_variant / pml_batch_autotune: as for a single
+ *   context, over the batched interior kernel's variants (columns per lane, rows per TMA
+ *   box, pipeline depth, resident CTAs per SM, rows per work item); autotuning advances
+ *   every grid by (steps + 2) * count steps.
+ * pml_batch_profile_enable / pml_batch_profile_read: event timing of every launch
+ *   (kinds 0 interior, 1 layer); while enabled, steps are launched one by one without the
+ *   graph and without overlap.
+ * pml_batch_info: info[0] grids, info[1] interior work items, info[2] layer tiles,
+ *   info[3] CTAs of the interior launch.
+ * Errors of batch calls are described by pml_last_error(NULL).
+ */
+typedef struct pml_batch pml_batch;
+pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out);
+pml_status pml_batch_step(pml_batch *batch, int64_t n);
+pml_status pml_batch_get_variant(const pml_batch *batch, int *variant, int *count);
+pml_status pml_batch_set_variant(pml_batch *batch, int variant);
+pml_status pml_batch_autotune(pml_batch *batch, int steps, double *times_ms, int *chosen);
+pml_status pml_batch_profile_enable(pml_batch *batch, int enable);
+pml_status pml_batch_profile_read(pml_batch *batch, double ms[2], int64_t launches[2]);
+pml_status pml_batch_info(const pml_batch *batch, int64_t info[4]);
+void pml_batch_destroy(pml_batch *batch);
+
 void pml_destroy(pml_ctx *ctx);
 const char *pml_last_error(const pml_ctx *ctx);
 const char *pml_status_string(pml_status s);

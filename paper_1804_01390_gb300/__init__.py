@@ -9,11 +9,14 @@ input generators work without a GPU); the first call that needs it loads it and
 fails loudly if it has not been built.
 """
 
-__all__ = ["PMLSolver"]
+__all__ = ["PMLSolver", "PMLBatch"]
 
 
 def __getattr__(name):
     if name == "PMLSolver":
         from .solver import PMLSolver
         return PMLSolver
+    if name == "PMLBatch":
+        from .solver import PMLBatch
+        return PMLBatch
     raise AttributeError(name)

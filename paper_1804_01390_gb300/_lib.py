@@ -48,8 +48,10 @@ EXPORTED = (
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
     "pml_adjoint_read_field", "pml_state_bytes", "pml_save_state", "pml_load_state",
     "pml_get_variant", "pml_set_variant", "pml_autotune",
-    "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static", "pml_destroy", "pml_last_error",
-    "pml_status_string",
+    "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
+    "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
+    "pml_batch_autotune", "pml_batch_profile_enable", "pml_batch_profile_read", "pml_batch_info",
+    "pml_batch_destroy", "pml_destroy", "pml_last_error", "pml_status_string",
 )
 
 
@@ -112,11 +114,21 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_autotune": [P, ctypes.c_int, P, P],
         "pml_norms_dense_static": [ctypes.c_int, P, ctypes.c_int, P, P, P, P, ctypes.c_double, P, P, P],
         "pml_profile_read": [P, P, P],
+        "pml_batch_create": [ctypes.c_int, P, ctypes.POINTER(P)],
+        "pml_batch_step": [P, i64],
+        "pml_batch_get_variant": [P, P, P],
+        "pml_batch_set_variant": [P, ctypes.c_int],
+        "pml_batch_autotune": [P, ctypes.c_int, P, P],
+        "pml_batch_profile_enable": [P, ctypes.c_int],
+        "pml_batch_profile_read": [P, P, P],
+        "pml_batch_info": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = st
+    lib.pml_batch_destroy.argtypes = [P]
+    lib.pml_batch_destroy.restype = None
     lib.pml_destroy.argtypes = [P]
     lib.pml_destroy.restype = None
     lib.pml_last_error.argtypes = [P]
@@ -274,6 +286,65 @@ def pml_norms_dense_static(ndim, T, precision, U, V, wlo, whi, h, ref, stream):
     _check(load().pml_norms_dense_static(int(ndim), Ta.ctypes.data, int(precision), U, V, lo.ctypes.data,
                                          hi.ctypes.data, float(h), ref, stream, out.ctypes.data))
     return out
+
+
+def pml_batch_create(ctxs):
+    """Batch of 2D contexts (a list of context handles); returns the batch handle."""
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    out = ctypes.c_void_p(0)
+    _check(load().pml_batch_create(len(ctxs), arr, ctypes.byref(out)))
+    return out.value
+
+
+def pml_batch_step(batch, n):
+    _check(load().pml_batch_step(batch, int(n)))
+
+
+def pml_batch_get_variant(batch):
+    """Returns (current variant, number of variants)."""
+    v = ctypes.c_int(0)
+    n = ctypes.c_int(0)
+    _check(load().pml_batch_get_variant(batch, ctypes.byref(v), ctypes.byref(n)))
+    return int(v.value), int(n.value)
+
+
+def pml_batch_set_variant(batch, variant):
+    _check(load().pml_batch_set_variant(batch, int(variant)))
+
+
+def pml_batch_autotune(batch, steps):
+    """Returns (chosen variant, per-variant ms per step)."""
+    import numpy as np
+    _, n = pml_batch_get_variant(batch)
+    times = np.zeros(n, dtype=np.float64)
+    ch = ctypes.c_int(0)
+    _check(load().pml_batch_autotune(batch, int(steps), times.ctypes.data, ctypes.byref(ch)))
+    return int(ch.value), times
+
+
+def pml_batch_profile_enable(batch, enable):
+    _check(load().pml_batch_profile_enable(batch, int(enable)))
+
+
+def pml_batch_profile_read(batch):
+    """Returns (ms[2], launches[2]) for kinds interior, layer."""
+    import numpy as np
+    ms = np.zeros(2, dtype=np.float64)
+    n = np.zeros(2, dtype=np.int64)
+    _check(load().pml_batch_profile_read(batch, ms.ctypes.data, n.ctypes.data))
+    return ms, n
+
+
+def pml_batch_info(batch):
+    """Returns (grids, interior work items, layer tiles, interior CTAs)."""
+    import numpy as np
+    info = np.zeros(4, dtype=np.int64)
+    _check(load().pml_batch_info(batch, info.ctypes.data))
+    return tuple(int(x) for x in info)
+
+
+def pml_batch_destroy(batch):
+    load().pml_batch_destroy(batch)
 
 
 def pml_destroy(ctx):

@@ -273,6 +273,36 @@ constexpr int kLayerTW = 24, kLayer2LY = 16;
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U,V,Px,Qx,Py,Qy*/,
                            void *const *out /*[6]*/, const Layer2DArgs &a, cudaStream_t st);
 
+// Batched 2D step over many independent grids: one interior launch and one layer launch
+// per step for the whole batch.  Per-grid descriptors (tensor maps included) live in device
+// memory; work items of all grids share one queue.
+struct GridDesc2 {   // aligned as CUtensorMap
+    CUtensorMap tm_int[2][2];  // [input parity][U, V], interior box of the batch's variant
+    CUtensorMap tm_lay[2][6];  // [input parity][field], layer box
+    void *out[2][6];           // output buffers when the input parity is p
+    Interior2DArgs in;         // geometry, layer-free ranges, coefficients
+    Layer2DArgs lay;           // geometry, constants, sigma (tiles: the batch list)
+    int rblocks, nstrips;      // interior work items of this grid: nstrips x rblocks
+};
+struct Batch2DArgs {
+    const GridDesc2 *desc;
+    const int *item_off;       // [ngrid + 1] first interior item of each grid
+    const LayerTile *tiles;    // layer tiles of all grids
+    const int *tile_grid;      // grid of each tile
+    int ngrid, n_items, ntiles;
+    int *queue;
+    int parity;                // input parity of every grid; this launch counts on queue[parity]
+};
+int batch2d_variants(int prec);
+int batch2d_box_cols(int prec, int v);     // interior tensor-map box of variant v
+int batch2d_box_rows(int prec, int v);
+int batch2d_item_rows(int prec, int v);    // output rows per interior work item
+int batch2d_strip_cols(int prec, int v);   // output columns per interior work item
+int batch2d_interior_blocks_per_sm(int prec, int v);
+cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st,
+                                    bool overlap_previous);
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, cudaStream_t st);
+
 // 3D counterparts.
 struct Interior3DArgs {
     Geom g;

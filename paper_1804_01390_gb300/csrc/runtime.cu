@@ -1090,3 +1090,392 @@ pml_status pml_load_state(pml_ctx *c, const void *src, int on_device)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Batched stepping of many independent 2D contexts: one layer launch and one interior
+// launch per step for the whole batch, runs of kBatchGraphSteps steps replayed from a
+// CUDA graph captured once per kernel variant.
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr int kBatchGraphSteps = 32;   // even: a replay starts and ends at input parity 0
+}
+
+struct pml_batch {
+    std::vector<pml_ctx *> ctx;
+    int prec = 0, var = 0, sm_count = 0;
+    cudaStream_t st = nullptr;    // the contexts' stream (work and graph replays)
+    cudaStream_t cap = nullptr;   // private stream the graph is captured on
+    char *mem = nullptr;
+    GridDesc2 *ddesc = nullptr;
+    int *ditem_off = nullptr, *dtile_grid = nullptr, *dqueue = nullptr;
+    LayerTile *dtiles = nullptr;
+    int n_items = 0, ntiles = 0, grid_int = 0;
+    int64_t launches = 0;         // interior launches so far; its parity is the queue's
+    cudaGraphExec_t exec = nullptr;
+    bool pdl = true;              // interior launches overlap the layer launch
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_n = 0;
+};
+
+namespace {
+
+pml_status bfail(pml_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_create_error = buf;
+    return s;
+}
+
+#define PML_BCU(call, what)                                                                 \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return bfail(PML_ECUDA, "%s: %s", (what), cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device tables of the current variant: one descriptor per grid and the first interior
+// work item of each grid.  The caller has synchronised the stream.
+pml_status batch_upload(pml_batch *b)
+{
+    const int ng = int(b->ctx.size());
+    const uint32_t box[3] = {uint32_t(batch2d_box_cols(b->prec, b->var)), uint32_t(batch2d_box_rows(b->prec, b->var)), 1};
+    const int rows = batch2d_item_rows(b->prec, b->var), cols = batch2d_strip_cols(b->prec, b->var);
+    std::vector<GridDesc2> desc(static_cast<size_t>(ng));
+    std::vector<int> off(static_cast<size_t>(ng) + 1, 0);
+    int64_t items = 0;
+    for (int i = 0; i < ng; ++i) {
+        pml_ctx *c = b->ctx[size_t(i)];
+        GridDesc2 &d = desc[size_t(i)];
+        std::memset(static_cast<void *>(&d), 0, sizeof d);
+        for (int p = 0; p < 2; ++p) {
+            for (int f = 0; f < 2; ++f)
+                if (encode_map(c, &d.tm_int[p][f], c->fld[p][f], box) != PML_OK)
+                    return bfail(PML_ECUDA, "grid %d: %s", i, c->err.c_str());
+            for (int f = 0; f < 6; ++f) {
+                d.tm_lay[p][f] = c->tm_lay[p][f];
+                d.out[p][f] = c->fld[1 - p][f];
+            }
+        }
+        d.in.g = c->g;
+        d.in.xr = c->ir[0];
+        d.in.yr = c->ir[1];
+        step_coef(c, false, &d.in.c);
+        d.in.err = c->derr;
+        d.lay.g = c->g;
+        d.lay.k = layer_const(c);
+        d.lay.sig[0] = c->dsig[0];
+        d.lay.sig[1] = c->dsig[1];
+        d.lay.err = c->derr;
+        int64_t n = 0;
+        if (!range_empty(c->ir[0]) && !range_empty(c->ir[1])) {
+            d.rblocks = int((c->ir[1].hi - c->ir[1].lo + 1 + rows - 1) / rows);
+            d.nstrips = int((c->ir[0].hi - (c->ir[0].lo & ~int64_t(3))) / cols + 1);
+            n = int64_t(d.rblocks) * d.nstrips;
+        }
+        off[size_t(i)] = int(items);
+        items += n;
+        if (items > (int64_t(1) << 30)) return bfail(PML_EINVAL, "batch has too many interior work items");
+    }
+    off[size_t(ng)] = int(items);
+    b->n_items = int(items);
+    PML_BCU(cudaMemcpy(b->ddesc, desc.data(), desc.size() * sizeof(GridDesc2), cudaMemcpyHostToDevice), "upload batch descriptors");
+    PML_BCU(cudaMemcpy(b->ditem_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "upload batch offsets");
+    // (also sets the kernels' shared-memory limits, which must not happen during capture)
+    const int bps = batch2d_interior_blocks_per_sm(b->prec, b->var);
+    if (bps <= 0 || batch2d_interior_blocks_per_sm(b->prec, 0) <= 0)
+        return bfail(PML_ECUDA, "batched interior kernel cannot be resident");
+    b->grid_int = bps * b->sm_count;
+    return PML_OK;
+}
+
+long bprof_begin(pml_batch *b, int kind, cudaStream_t st)
+{
+    if (!b->prof_on) return -1;
+    if (b->prof_n == b->prof_kind.size()) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1; }
+        b->prof_ev.push_back(e0);
+        b->prof_ev.push_back(e1);
+        b->prof_kind.push_back(kind);
+    }
+    const size_t i = b->prof_n++;
+    b->prof_kind[i] = kind;
+    cudaEventRecord(b->prof_ev[2 * i], st);
+    return long(i);
+}
+
+void bprof_end(pml_batch *b, long i, cudaStream_t st)
+{
+    if (i >= 0) cudaEventRecord(b->prof_ev[2 * size_t(i) + 1], st);
+}
+
+// One step of every grid from input parity p (which is also the queue parity).
+pml_status batch_enqueue(pml_batch *b, int p, cudaStream_t st, bool timed)
+{
+    Batch2DArgs a{};
+    a.desc = b->ddesc;
+    a.item_off = b->ditem_off;
+    a.tiles = b->dtiles;
+    a.tile_grid = b->dtile_grid;
+    a.ngrid = int(b->ctx.size());
+    a.n_items = b->n_items;
+    a.ntiles = b->ntiles;
+    a.queue = b->dqueue;
+    a.parity = p;
+    long pi = timed ? bprof_begin(b, 1, st) : -1;
+    cudaError_t e = launch_batch2d_layer(b->prec, a, st);
+    bprof_end(b, pi, st);
+    if (e != cudaSuccess) return bfail(PML_ECUDA, "batched layer kernel: %s", cudaGetErrorString(e));
+    pi = timed ? bprof_begin(b, 0, st) : -1;
+    e = launch_batch2d_interior(b->prec, b->var, a, b->grid_int, st, b->pdl && b->ntiles > 0 && !timed);
+    bprof_end(b, pi, st);
+    if (e != cudaSuccess) return bfail(PML_ECUDA, "batched interior kernel: %s", cudaGetErrorString(e));
+    return PML_OK;
+}
+
+void batch_drop_graph(pml_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+// Capture kBatchGraphSteps steps from input parity 0 on the private stream.  If the
+// driver refuses the programmatic (overlapping) edges in a graph, capture plain ones.
+pml_status batch_capture(pml_batch *b)
+{
+    batch_drop_graph(b);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        cudaGraph_t g = nullptr;
+        PML_BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+        pml_status s = PML_OK;
+        for (int k = 0; k < kBatchGraphSteps && s == PML_OK; ++k) s = batch_enqueue(b, k & 1, b->cap, false);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (s == PML_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (s == PML_OK && e == cudaSuccess) return PML_OK;
+        cudaGetLastError();
+        b->exec = nullptr;
+        if (!b->pdl) return s != PML_OK ? s : bfail(PML_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        b->pdl = false;
+    }
+    return bfail(PML_ECUDA, "graph capture failed");
+}
+
+}  // namespace
+
+extern "C" {
+
+pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
+{
+    if (!out) return bfail(PML_EINVAL, "pml_batch_create: out is NULL");
+    *out = nullptr;
+    if (count < 1 || !ctxs) return bfail(PML_EINVAL, "pml_batch_create: need count >= 1 contexts");
+    for (int i = 0; i < count; ++i) {
+        const pml_ctx *c = ctxs[i];
+        if (!c) return bfail(PML_EINVAL, "pml_batch_create: context %d is NULL", i);
+        if (c->nd != 2) return bfail(PML_EINVAL, "pml_batch_create: context %d is not 2D", i);
+        if (c->prec != ctxs[0]->prec) return bfail(PML_EINVAL, "pml_batch_create: contexts mix precisions");
+        if (c->st != ctxs[0]->st) return bfail(PML_EINVAL, "pml_batch_create: contexts use different streams");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return bfail(PML_EINVAL, "pml_batch_create: context %d appears twice", i);
+    }
+    pml_batch *b = new pml_batch();
+    b->ctx.assign(ctxs, ctxs + count);
+    b->prec = ctxs[0]->prec;
+    b->st = ctxs[0]->st;
+    b->sm_count = ctxs[0]->sm_count;
+    auto bail = [&](pml_status s) {
+        const std::string msg = g_create_error;
+        pml_batch_destroy(b);
+        g_create_error = msg;
+        return s;
+    };
+    // layer tiles of all grids (the forward lists every context built at creation)
+    std::vector<LayerTile> tiles;
+    std::vector<int> tile_grid;
+    for (int i = 0; i < count; ++i) {
+        int co[9];
+        std::vector<LayerTile> t = build_tiles(b->ctx[size_t(i)], b->ctx[size_t(i)]->ir, co);
+        tiles.insert(tiles.end(), t.begin(), t.end());
+        tile_grid.insert(tile_grid.end(), t.size(), i);
+    }
+    if (tiles.size() > size_t(1) << 30) return bail(bfail(PML_EINVAL, "batch has too many layer tiles"));
+    b->ntiles = int(tiles.size());
+    size_t off = 0;
+    const size_t o_desc = off; off += align_up(size_t(count) * sizeof(GridDesc2), kAlign);
+    const size_t o_item = off; off += align_up((size_t(count) + 1) * sizeof(int), kAlign);
+    const size_t o_tile = off; off += align_up(std::max<size_t>(tiles.size(), 1) * sizeof(LayerTile), kAlign);
+    const size_t o_tg = off; off += align_up(std::max<size_t>(tiles.size(), 1) * sizeof(int), kAlign);
+    const size_t o_q = off; off += kAlign;
+    cudaError_t e = cudaMalloc(&b->mem, off);
+    if (e != cudaSuccess) { b->mem = nullptr; return bail(bfail(PML_ENOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e))); }
+    b->ddesc = reinterpret_cast<GridDesc2 *>(b->mem + o_desc);
+    b->ditem_off = reinterpret_cast<int *>(b->mem + o_item);
+    b->dtiles = reinterpret_cast<LayerTile *>(b->mem + o_tile);
+    b->dtile_grid = reinterpret_cast<int *>(b->mem + o_tg);
+    b->dqueue = reinterpret_cast<int *>(b->mem + o_q);
+    if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess) return bail(bfail(PML_ECUDA, "stream synchronize: %s", cudaGetErrorString(e)));
+    if (!tiles.empty()) {
+        e = cudaMemcpy(b->dtiles, tiles.data(), tiles.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->dtile_grid, tile_grid.data(), tile_grid.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(b->dqueue, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(bfail(PML_ECUDA, "batch tables: %s", cudaGetErrorString(e)));
+    pml_status s = batch_upload(b);
+    if (s != PML_OK) return bail(s);
+    *out = b;
+    return PML_OK;
+}
+
+pml_status pml_batch_step(pml_batch *b, int64_t n)
+{
+    if (!b) return bfail(PML_EINVAL, "pml_batch_step: batch is NULL");
+    if (n < 0) return bfail(PML_EINVAL, "pml_batch_step: n must be >= 0");
+    const int p0 = b->ctx[0]->cur;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const pml_ctx *c = b->ctx[i];
+        if (c->cur != p0)
+            return bfail(PML_ESTATE, "pml_batch_step: contexts 0 and %zu are at different step parities", i);
+        if (c->ns > 0 || c->nr > 0)
+            return bfail(PML_ESTATE, "pml_batch_step: context %zu has sources or receivers (step it with pml_step)", i);
+    }
+    if (n == 0) return PML_OK;
+    int p = p0;
+    if ((b->launches & 1) != p) {   // realign the queue parity with the field parity
+        PML_BCU(cudaMemsetAsync(b->dqueue, 0, 2 * sizeof(int), b->st), "reset batch queue");
+        b->launches = p;
+    }
+    int64_t left = n;
+    while (left > 0) {
+        if (p == 0 && left >= kBatchGraphSteps && !b->prof_on) {
+            if (!b->exec) {
+                pml_status s = batch_capture(b);
+                if (s != PML_OK) return s;
+            }
+            PML_BCU(cudaGraphLaunch(b->exec, b->st), "graph launch");
+            left -= kBatchGraphSteps;
+            b->launches += kBatchGraphSteps;
+            continue;
+        }
+        pml_status s = batch_enqueue(b, p, b->st, b->prof_on);
+        if (s != PML_OK) return s;
+        p ^= 1;
+        --left;
+        ++b->launches;
+    }
+    for (pml_ctx *c : b->ctx) {
+        c->cur = p;
+        c->step += n;
+    }
+    return PML_OK;
+}
+
+pml_status pml_batch_get_variant(const pml_batch *b, int *variant, int *count)
+{
+    if (!b) return bfail(PML_EINVAL, "pml_batch_get_variant: batch is NULL");
+    if (variant) *variant = b->var;
+    if (count) *count = batch2d_variants(b->prec);
+    return PML_OK;
+}
+
+pml_status pml_batch_set_variant(pml_batch *b, int variant)
+{
+    if (!b) return bfail(PML_EINVAL, "pml_batch_set_variant: batch is NULL");
+    const int n = batch2d_variants(b->prec);
+    if (variant < 0 || variant >= n) return bfail(PML_EINVAL, "pml_batch_set_variant: variant %d not in [0, %d)", variant, n);
+    PML_BCU(cudaStreamSynchronize(b->st), "stream synchronize");
+    batch_drop_graph(b);
+    const int old = b->var;
+    b->var = variant;
+    pml_status s = batch_upload(b);
+    if (s != PML_OK) {
+        b->var = old;
+        batch_upload(b);
+    }
+    return s;
+}
+
+pml_status pml_batch_autotune(pml_batch *b, int steps, double *times_ms, int *chosen)
+{
+    if (!b) return bfail(PML_EINVAL, "pml_batch_autotune: batch is NULL");
+    if (steps < 1) return bfail(PML_EINVAL, "pml_batch_autotune: steps must be >= 1");
+    const int n = batch2d_variants(b->prec);
+    cudaEvent_t e0, e1;
+    PML_BCU(cudaEventCreate(&e0), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return bfail(PML_ECUDA, "event"); }
+    int best = b->var;
+    double best_ms = 1e300;
+    pml_status s = PML_OK;
+    for (int v = 0; v < n && s == PML_OK; ++v) {
+        if ((s = pml_batch_set_variant(b, v)) != PML_OK) break;
+        if ((s = pml_batch_step(b, 2)) != PML_OK) break;   // warm-up (and graph capture below)
+        cudaEventRecord(e0, b->st);
+        if ((s = pml_batch_step(b, steps)) != PML_OK) break;
+        cudaEventRecord(e1, b->st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { s = bfail(PML_ECUDA, "autotune synchronize"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = double(ms) / steps;
+        if (times_ms) times_ms[v] = per;
+        if (per < best_ms) { best_ms = per; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PML_OK) return s;
+    if (chosen) *chosen = best;
+    return pml_batch_set_variant(b, best);
+}
+
+pml_status pml_batch_profile_enable(pml_batch *b, int enable)
+{
+    if (!b) return bfail(PML_EINVAL, "pml_batch_profile_enable: batch is NULL");
+    b->prof_on = enable != 0;
+    return PML_OK;
+}
+
+pml_status pml_batch_profile_read(pml_batch *b, double ms[2], int64_t launches[2])
+{
+    if (!b || !ms || !launches) return bfail(PML_EINVAL, "pml_batch_profile_read: NULL argument");
+    PML_BCU(cudaStreamSynchronize(b->st), "stream synchronize");
+    for (int k = 0; k < 2; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (size_t i = 0; i < b->prof_n; ++i) {
+        float t = 0.f;
+        PML_BCU(cudaEventElapsedTime(&t, b->prof_ev[2 * i], b->prof_ev[2 * i + 1]), "event time");
+        ms[b->prof_kind[i]] += double(t);
+        launches[b->prof_kind[i]] += 1;
+    }
+    b->prof_n = 0;
+    return PML_OK;
+}
+
+pml_status pml_batch_info(const pml_batch *b, int64_t info[4])
+{
+    if (!b || !info) return bfail(PML_EINVAL, "pml_batch_info: NULL argument");
+    info[0] = int64_t(b->ctx.size());
+    info[1] = b->n_items;
+    info[2] = b->ntiles;
+    info[3] = b->grid_int;
+    return PML_OK;
+}
+
+void pml_batch_destroy(pml_batch *b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    else cudaDeviceSynchronize();
+    batch_drop_graph(b);
+    for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
+}
+
+}  // extern "C"
+

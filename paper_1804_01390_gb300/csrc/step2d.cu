@@ -914,4 +914,171 @@ cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *
     return adjoint ? with_i2<true>(prec, v, go) : with_i2<false>(prec, v, go);
 }
 
+// ------------------------------------------------------------------------------------
+// Batched 2D step: the per-item code above, with the grid of each work item read from a
+// descriptor table in device memory.  Interior items of all grids form one queue (the
+// owning grid found by binary search over item_off); layer tiles of all grids form one
+// list.  Variants differ in the warp-streaming shape and in the rows per work item.
+// ------------------------------------------------------------------------------------
+struct BVar {
+    int nc, ch, s, minb, rows;
+};
+constexpr BVar kB32[] = {{4, 6, 3, 3, 64}, {4, 6, 2, 4, 64}, {8, 3, 3, 2, 64}, {4, 6, 3, 3, 32}};
+constexpr BVar kB64[] = {{4, 6, 2, 2, 64}, {4, 3, 3, 2, 64}, {4, 6, 2, 2, 32}};
+constexpr int kNB32 = sizeof(kB32) / sizeof(BVar), kNB64 = sizeof(kB64) / sizeof(BVar);
+
+int batch2d_variants(int prec) { return prec == 32 ? kNB32 : kNB64; }
+static const BVar &bvar(int prec, int v) { return prec == 32 ? kB32[v] : kB64[v]; }
+int batch2d_box_cols(int prec, int v) { return 32 * bvar(prec, v).nc; }
+int batch2d_box_rows(int prec, int v) { return bvar(prec, v).ch; }
+int batch2d_item_rows(int prec, int v) { return bvar(prec, v).rows; }
+int batch2d_strip_cols(int prec, int v) { return 30 * bvar(prec, v).nc; }
+
+template <typename T, bool ADJ, int NC, int CH, int S, int MINB, int ROWS>
+__global__ void __launch_bounds__(128, MINB) k_interior2d_batch(const Batch2DArgs b)
+{
+    constexpr size_t WB = size_t(S) * 2 * CH * 32 * NC * sizeof(T);
+    __shared__ __align__(8) uint64_t bars[4][S];
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem + warp * WB;
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.queue[1 - b.parity] = 0;
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t use = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&b.queue[b.parity], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= b.n_items) break;
+        int lo = 0, hi = b.ngrid - 1;   // last grid whose first item is <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.item_off[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const GridDesc2 &d = b.desc[lo];
+        const Interior2DArgs &a = d.in;
+        const int k = item - b.item_off[lo];
+        const int st = k / d.rblocks, rb = k - st * d.rblocks;
+        const int64_t y0 = a.yr.lo + int64_t(rb) * ROWS;
+        const int64_t rem = a.yr.hi - y0 + 1;
+        const int64_t xs = (a.xr.lo & ~int64_t(3)) + int64_t(30 * NC) * st;
+        if (!interior2d_seg<T, ADJ, NC, CH, S>(&d.tm_int[b.parity][0], &d.tm_int[b.parity][1],
+                                               static_cast<T *>(d.out[b.parity][0]),
+                                               static_cast<T *>(d.out[b.parity][1]), a, xs, y0,
+                                               int(rem < ROWS ? rem : ROWS), wbase, bars[warp], lane, use))
+            break;
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(128) k_layer2d_batch(const Batch2DArgs b)
+{
+    constexpr int SE = 6 * kL2CH * 32;
+    __shared__ __align__(8) uint64_t bars[4][kL2S];
+    extern __shared__ unsigned char smem_dyn[];
+    T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    allow_dependent_launch();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * 4 + warp;
+    if (item >= b.ntiles) return;   // whole warp; the kernel has no block barrier
+    T *ring = smem + warp * kL2S * SE;
+    const LayerTile tile = b.tiles[item];
+    const GridDesc2 &d = b.desc[b.tile_grid[item]];
+    const Maps6 &maps = *reinterpret_cast<const Maps6 *>(&d.tm_lay[b.parity][0]);
+    const Out6 &out = *reinterpret_cast<const Out6 *>(&d.out[b.parity][0]);
+    switch (tile.flags & 3) {
+    case 0: layer2d_item<T, ADJ, 0>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
+    case 1: layer2d_item<T, ADJ, 1>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
+    case 2: layer2d_item<T, ADJ, 2>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
+    default: layer2d_item<T, ADJ, 3>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
+    }
+}
+
+template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct BKernel {
+    static constexpr size_t smem() { return size_t(4) * S * 2 * CH * 32 * NC * sizeof(T) + 128; }
+    static auto fn() { return k_interior2d_batch<T, false, NC, CH, S, MINB, ROWS>; }
+    static cudaError_t prep()
+    {
+        static bool done = false;
+        if (done) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_layer2d_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(layer2d_smem<T>()));
+        if (e == cudaSuccess) done = true;
+        return e;
+    }
+    static int occupancy()
+    {
+        if (prep() != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn(), 128, smem()) != cudaSuccess) return 0;
+        return n;
+    }
+    static cudaError_t launch(const Batch2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+    {
+        cudaError_t e = prep();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = overlap_previous ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, fn(), a);
+    }
+};
+
+// dispatch over kB32 / kB64
+template <typename F> static auto with_b2(int prec, int v, F &&f)
+{
+    if (prec == 32) {
+        switch (v) {
+        case 0: return f(BKernel<float, 4, 6, 3, 3, 64>{});
+        case 1: return f(BKernel<float, 4, 6, 2, 4, 64>{});
+        case 2: return f(BKernel<float, 8, 3, 3, 2, 64>{});
+        default: return f(BKernel<float, 4, 6, 3, 3, 32>{});
+        }
+    }
+    switch (v) {
+    case 0: return f(BKernel<double, 4, 6, 2, 2, 64>{});
+    case 1: return f(BKernel<double, 4, 3, 3, 2, 64>{});
+    default: return f(BKernel<double, 4, 6, 2, 2, 32>{});
+    }
+}
+
+int batch2d_interior_blocks_per_sm(int prec, int v)
+{
+    return with_b2(prec, v, [](auto k) { return decltype(k)::occupancy(); });
+}
+
+cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st,
+                                    bool overlap_previous)
+{
+    if (a.n_items <= 0 || grid <= 0) return cudaSuccess;
+    return with_b2(prec, v, [&](auto k) { return decltype(k)::launch(a, grid, st, overlap_previous); });
+}
+
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, cudaStream_t st)
+{
+    if (a.ntiles <= 0) return cudaSuccess;
+    cudaError_t e = with_b2(prec, 0, [](auto k) { return decltype(k)::prep(); });
+    if (e != cudaSuccess) return e;
+    if (prec == 32) k_layer2d_batch<float, false><<<(a.ntiles + 3) / 4, 128, layer2d_smem<float>(), st>>>(a);
+    else k_layer2d_batch<double, false><<<(a.ntiles + 3) / 4, 128, layer2d_smem<double>(), st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace pml

@@ -197,3 +197,53 @@ class PMLSolver:
 
     def load_state(self, src):
         _lib.pml_load_state(self.ctx, src.data_ptr(), src.device.type == "cuda")
+
+
+class PMLBatch:
+    """Many independent 2D solvers advanced together (``pml_batch_*``).
+
+    All solvers must be 2D, of one precision and on one stream; they keep working on
+    their own between batch steps (``read``, ``norms``, ``step``).  The batch holds
+    references to them so that they outlive it.
+    """
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.handle = _lib.pml_batch_create([s.ctx for s in self.solvers])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pml_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        _lib.pml_batch_step(self.handle, int(n))
+
+    @property
+    def variant(self):
+        return _lib.pml_batch_get_variant(self.handle)[0]
+
+    @property
+    def variant_count(self):
+        return _lib.pml_batch_get_variant(self.handle)[1]
+
+    def set_variant(self, v):
+        _lib.pml_batch_set_variant(self.handle, int(v))
+
+    def autotune(self, steps):
+        return _lib.pml_batch_autotune(self.handle, int(steps))
+
+    def profile(self, enable=True):
+        _lib.pml_batch_profile_enable(self.handle, int(enable))
+
+    def profile_read(self):
+        return _lib.pml_batch_profile_read(self.handle)
+
+    def info(self):
+        return _lib.pml_batch_info(self.handle)

@@ -52,3 +52,19 @@ def test_host_only_calls_without_gpu(lib):
     with pytest.raises(_lib.PMLError):
         _lib.pml_workspace_bytes(2, (2, 2), 1, 32)       # n + 2w < 8
     assert _lib.pml_status_string(_lib.PML_EUNSTABLE).startswith("time step")
+
+
+def test_batch_argument_checks_without_gpu(lib):
+    """pml_batch_* reject empty and NULL arguments before touching a device."""
+    import ctypes
+    from paper_1804_01390_gb300 import _lib
+    L = _lib.load()
+    out = ctypes.c_void_p(0)
+    assert L.pml_batch_create(0, None, ctypes.byref(out)) == _lib.PML_EINVAL
+    assert "count >= 1" in _lib.pml_last_error(None)
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.pml_batch_create(2, arr, ctypes.byref(out)) == _lib.PML_EINVAL
+    assert L.pml_batch_step(None, 1) == _lib.PML_EINVAL
+    assert L.pml_batch_set_variant(None, 0) == _lib.PML_EINVAL
+    assert L.pml_batch_info(None, None) == _lib.PML_EINVAL
+    L.pml_batch_destroy(None)
