@@ -126,15 +126,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after `limit` polls (each poll suspends for a hardware-defined
-// interval), records the failure and returns false.  No wait in this library can spin
-// forever.
-constexpr uint32_t kWaitLimit = 1u << 24;
+// Bounded wait: gives up after `limit_ns` nanoseconds of the global timer (checked every
+// 256 polls), records the failure and returns false.  No wait in this library can spin
+// forever.  The default limit is far above any legitimate wait (a few microseconds).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+constexpr uint64_t kDrainLimitNs = 100000000ull;   // 0.1 s, waits on the error path
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DeviceError *err, int where)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DeviceError *err, int where,
+                                          uint64_t limit_ns = kWaitLimitNs)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) break;
+    }
     if (err) {
         atomicCAS(&err->code, 0, 1);
         err->where = where;
@@ -266,12 +280,19 @@ struct Layer2DArgs {
     const LayerTile *tiles;
     int ntiles;
     DeviceError *err;
+    int *queue;                // work counters (this launch: queue[parity]; clears the other)
+    int parity;
 };
-// 2D layer work items: 24 output columns (one warp, halo 4 lanes per side) by at most
-// kLayer2LY output rows of one frame rectangle
-constexpr int kLayerTW = 24, kLayer2LY = 16;
+// 2D layer work items: one strip of layer2d_tile_cols() output columns (one warp, halo
+// 4 columns per side) by a run of rows, taken by the warps from a work queue
+constexpr int kLayer2BandRows = 64;  // most output rows of one item of the y band
+constexpr int kLayer2SlabRows = 32;  // most output rows of one item of an x slab
+int layer2d_grid(int prec, int ntiles, int sm_count);   // CTAs of one layer launch (warps loop over items)
+int layer2d_box_rows();               // rows of the layer kernel's TMA box
+int layer2d_box_cols(int prec);       // columns of the layer kernel's TMA box (one strip)
+int layer2d_tile_cols(int prec);      // output columns of one layer strip (box minus the halo)
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U,V,Px,Qx,Py,Qy*/,
-                           void *const *out /*[6]*/, const Layer2DArgs &a, cudaStream_t st);
+                           void *const *out /*[6]*/, const Layer2DArgs &a, int grid, cudaStream_t st);
 
 // Batched 2D step over many independent grids: one interior launch and one layer launch
 // per step for the whole batch.  Per-grid descriptors (tensor maps included) live in device
@@ -290,8 +311,8 @@ struct Batch2DArgs {
     const LayerTile *tiles;    // layer tiles of all grids
     const int *tile_grid;      // grid of each tile
     int ngrid, n_items, ntiles;
-    int *queue;
-    int parity;                // input parity of every grid; this launch counts on queue[parity]
+    int *queue;                // interior work counters [2], then layer work counters [2]
+    int parity;                // input parity of every grid; a launch counts on counter [parity]
 };
 int batch2d_variants(int prec);
 int batch2d_box_cols(int prec, int v);     // interior tensor-map box of variant v
@@ -301,7 +322,7 @@ int batch2d_strip_cols(int prec, int v);   // output columns per interior work i
 int batch2d_interior_blocks_per_sm(int prec, int v);
 cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st,
                                     bool overlap_previous);
-cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, cudaStream_t st);
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, cudaStream_t st);
 
 // 3D counterparts.
 struct Interior3DArgs {

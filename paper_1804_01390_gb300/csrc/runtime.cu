@@ -62,7 +62,7 @@ Geom make_geom(int nd, const int64_t T[3])
 size_t tile_bound(int nd, int prec, const int64_t T[3])
 {
     if (nd == 2)
-        return size_t(4) * size_t(T[0] / kLayerTW + 2) * size_t(T[1] / kLayer2LY + 2);
+        return size_t(3) * size_t(T[0] / layer2d_tile_cols(prec) + 3) * size_t(T[1] / kLayer2SlabRows + 2);
     const int TX = prec == 32 ? kLayer3TXf : kLayer3TXd, TY = prec == 32 ? kLayer3TYf : kLayer3TYd;
     return size_t(5) * size_t(T[0] / TX + 2) * size_t(T[1] / TY + 2) * size_t(T[2] / kLayer3LZ + 2);
 }
@@ -131,8 +131,8 @@ struct pml_ctx {
     int class_off[9] = {}, class_off_adj[9] = {};
     double *dpart = nullptr, *dnorm = nullptr, *dgrad = nullptr;
     DeviceError *derr = nullptr;
-    int *dqueue = nullptr;              // work counters of the persistent 2D step (fwd 0/1, adj 2/3)
-    int64_t launches_fwd = 0, launches_adj = 0;
+    int *dqueue = nullptr;              // work counters: interior fwd 0/1, adj 2/3; 2D layer fwd 4/5, adj 6/7
+    int64_t launches_fwd = 0, launches_adj = 0, launches_layer_fwd = 0, launches_layer_adj = 0;
     int ns = 0, nr = 0;
     int64_t *dsrc_off = nullptr, *drec_off = nullptr;
     int32_t *dsrc_xyz = nullptr;
@@ -315,36 +315,69 @@ std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
     return out;
 }
 
-// Layer tiles of the frame.  2D: kLayerTW x kLayerTH output tiles.  3D: (x, y) column
-// tiles streamed over z segments of at most kLayer3LZ planes (zlo..zhi, unwrapped), sorted
-// by flags so that each class runs with its own field count.
+// Layer tiles of the frame, sorted by flags (bit a: aux fields of axis a reach the tile's
+// footprint) so that each class runs with its own field count.
+//  2D: strips of layer2d_tile_cols() output columns streamed down the rows by one warp.  The rows
+//      outside ir[1] form one band across the periodic seam of y (unwrapped rows
+//      ir[1].hi + 1 .. T1 + ir[1].lo - 1), cut into near-equal runs of at most
+//      kLayer2BandRows rows over the full width; the columns outside ir[0] (rows ir[1])
+//      are cut into runs of at most kLayer2SlabRows rows.
+//  3D: (x, y) column tiles streamed over z segments of at most kLayer3LZ planes (zlo..zhi,
+//      unwrapped).
 std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_off[9])
 {
     std::vector<LayerTile> t;
-    const bool d3 = c->nd == 3;
-    const int TX = d3 ? layer3d_tile_x(c->prec) : kLayerTW;
-    const int TY = d3 ? layer3d_tile_y(c->prec) : kLayer2LY;
-    const int TZ = d3 ? kLayer3LZ : 1;
-    for (const Rect &r : frame_rects(c, ir)) {
-        for (int64_t z0 = r.lo[2]; z0 <= r.hi[2]; z0 += TZ)
-            for (int64_t y0 = r.lo[1]; y0 <= r.hi[1]; y0 += TY)
-                for (int64_t x0 = r.lo[0] & ~int64_t(3); x0 <= r.hi[0]; x0 += TX) {
+    if (c->nd == 2) {
+        const int TW = layer2d_tile_cols(c->prec);
+        auto add = [&](int64_t xlo, int64_t xhi, int64_t ylo, int64_t yhi, int64_t maxrows) {
+            const int64_t H = yhi - ylo + 1;
+            if (xhi < xlo || H <= 0) return;
+            const int64_t nseg = (H + maxrows - 1) / maxrows;
+            int64_t y0 = ylo;
+            for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+                const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
+                for (int64_t x0 = xlo & ~int64_t(3); x0 <= xhi; x0 += TW) {
                     LayerTile L{};
-                    L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = int32_t(z0);
-                    L.xlo = int32_t(r.lo[0]); L.xhi = int32_t(r.hi[0]);
-                    L.ylo = int32_t(r.lo[1]); L.yhi = int32_t(r.hi[1]);
-                    L.zlo = int32_t(z0); L.zhi = int32_t(std::min<int64_t>(z0 + TZ - 1, r.hi[2]));
-                    if (!d3) {   // 2D: a run of at most kLayer2LY rows streamed by one warp
-                        L.zlo = 0; L.zhi = 0;
-                        L.ylo = int32_t(y0); L.yhi = int32_t(std::min<int64_t>(y0 + TY - 1, r.hi[1]));
-                    }
+                    L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = 0;
+                    L.xlo = int32_t(xlo); L.xhi = int32_t(xhi);
+                    L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
                     int fl = 0;
-                    if (axis_active(c, 0, x0 - 4, x0 + TX + 4)) fl |= 1;
-                    if (d3 ? axis_active(c, 1, y0 - 4, y0 + TY + 4) : axis_active(c, 1, L.ylo - 4, L.yhi + 5)) fl |= 2;
-                    if (d3 && axis_active(c, 2, L.zlo - 4, L.zhi + 5)) fl |= 4;
+                    if (axis_active(c, 0, x0 - 4, x0 + TW + 4)) fl |= 1;
+                    if (axis_active(c, 1, L.ylo - 4, L.yhi + 5)) fl |= 2;
                     L.flags = fl;
                     t.push_back(L);
                 }
+                y0 += len;
+            }
+        };
+        const int64_t T0 = c->T[0], T1 = c->T[1];
+        if (range_empty(ir[0]) || range_empty(ir[1])) {
+            add(0, T0 - 1, 0, T1 - 1, kLayer2BandRows);
+        } else {
+            const int64_t band = T1 - (ir[1].hi - ir[1].lo + 1);
+            if (band > 0) add(0, T0 - 1, ir[1].hi + 1, ir[1].hi + band, kLayer2BandRows);
+            if (ir[0].lo > 0) add(0, ir[0].lo - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
+            if (ir[0].hi < T0 - 1) add(ir[0].hi + 1, T0 - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
+        }
+    } else {
+        const int TX = layer3d_tile_x(c->prec), TY = layer3d_tile_y(c->prec), TZ = kLayer3LZ;
+        for (const Rect &r : frame_rects(c, ir)) {
+            for (int64_t z0 = r.lo[2]; z0 <= r.hi[2]; z0 += TZ)
+                for (int64_t y0 = r.lo[1]; y0 <= r.hi[1]; y0 += TY)
+                    for (int64_t x0 = r.lo[0] & ~int64_t(3); x0 <= r.hi[0]; x0 += TX) {
+                        LayerTile L{};
+                        L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = int32_t(z0);
+                        L.xlo = int32_t(r.lo[0]); L.xhi = int32_t(r.hi[0]);
+                        L.ylo = int32_t(r.lo[1]); L.yhi = int32_t(r.hi[1]);
+                        L.zlo = int32_t(z0); L.zhi = int32_t(std::min<int64_t>(z0 + TZ - 1, r.hi[2]));
+                        int fl = 0;
+                        if (axis_active(c, 0, x0 - 4, x0 + TX + 4)) fl |= 1;
+                        if (axis_active(c, 1, y0 - 4, y0 + TY + 4)) fl |= 2;
+                        if (axis_active(c, 2, L.zlo - 4, L.zhi + 5)) fl |= 4;
+                        L.flags = fl;
+                        t.push_back(L);
+                    }
+        }
     }
     std::stable_sort(t.begin(), t.end(), [](const LayerTile &a, const LayerTile &b) { return a.flags < b.flags; });
     for (int m = 0; m <= 8; ++m) class_off[m] = 0;
@@ -489,8 +522,12 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
         l.err = c->derr;
+        int64_t &ll = adjoint ? c->launches_layer_adj : c->launches_layer_fwd;
+        l.queue = c->dqueue + (adjoint ? 6 : 4);
+        l.parity = int(ll & 1);
+        if (l.ntiles > 0) ++ll;
         long pi = prof_begin(c, 1);
-        e = launch_layer2d(c->prec, adjoint, tl, out, l, c->st);
+        e = launch_layer2d(c->prec, adjoint, tl, out, l, layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st);
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel");
         Interior2DArgs a{};
@@ -673,7 +710,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     {
         cudaError_t e = cudaMemsetAsync(c->ws, 0, plan.sig[0], c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(DeviceError), c->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->dqueue, 0, 4 * sizeof(int), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->dqueue, 0, 8 * sizeof(int), c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->dgrad, 0, kMaxSources * sizeof(double), c->st);
         if (e != cudaSuccess) { cuda_fail(c, e, "clear workspace"); return bail(PML_ECUDA); }
     }
@@ -709,7 +746,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         if (c->nd == 2) {
             box_int[0] = uint32_t(interior2d_box_cols(precision, c->ivar));
             box_int[1] = uint32_t(interior2d_box_rows(precision, c->ivar)); box_int[2] = 1;
-            box_lay[0] = 32; box_lay[1] = 3; box_lay[2] = 1;   // one warp's 32 columns x 3 rows
+            box_lay[0] = uint32_t(layer2d_box_cols(precision)); box_lay[1] = uint32_t(layer2d_box_rows());
+            box_lay[2] = 1;   // one warp's strip
         } else {
             box_int[0] = 128; box_int[1] = uint32_t(interior3d_tile_y() + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
             box_lay[0] = uint32_t(layer3d_tile_x(precision) + 8); box_lay[1] = uint32_t(layer3d_tile_y(precision) + 8);
@@ -1229,7 +1267,7 @@ pml_status batch_enqueue(pml_batch *b, int p, cudaStream_t st, bool timed)
     a.queue = b->dqueue;
     a.parity = p;
     long pi = timed ? bprof_begin(b, 1, st) : -1;
-    cudaError_t e = launch_batch2d_layer(b->prec, a, st);
+    cudaError_t e = launch_batch2d_layer(b->prec, a, layer2d_grid(b->prec, b->ntiles, b->sm_count), st);
     bprof_end(b, pi, st);
     if (e != cudaSuccess) return bfail(PML_ECUDA, "batched layer kernel: %s", cudaGetErrorString(e));
     pi = timed ? bprof_begin(b, 0, st) : -1;
@@ -1305,6 +1343,20 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
         tiles.insert(tiles.end(), t.begin(), t.end());
         tile_grid.insert(tile_grid.end(), t.size(), i);
     }
+    {   // one class after another across all grids (warps that run the same class share code)
+        std::vector<size_t> order(tiles.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](size_t a, size_t b) { return tiles[a].flags < tiles[b].flags; });
+        std::vector<LayerTile> t2(tiles.size());
+        std::vector<int> g2(tiles.size());
+        for (size_t k = 0; k < order.size(); ++k) {
+            t2[k] = tiles[order[k]];
+            g2[k] = tile_grid[order[k]];
+        }
+        tiles.swap(t2);
+        tile_grid.swap(g2);
+    }
     if (tiles.size() > size_t(1) << 30) return bail(bfail(PML_EINVAL, "batch has too many layer tiles"));
     b->ntiles = int(tiles.size());
     size_t off = 0;
@@ -1325,7 +1377,7 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
         e = cudaMemcpy(b->dtiles, tiles.data(), tiles.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->dtile_grid, tile_grid.data(), tile_grid.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemset(b->dqueue, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->dqueue, 0, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(bfail(PML_ECUDA, "batch tables: %s", cudaGetErrorString(e)));
     pml_status s = batch_upload(b);
@@ -1349,7 +1401,7 @@ pml_status pml_batch_step(pml_batch *b, int64_t n)
     if (n == 0) return PML_OK;
     int p = p0;
     if ((b->launches & 1) != p) {   // realign the queue parity with the field parity
-        PML_BCU(cudaMemsetAsync(b->dqueue, 0, 2 * sizeof(int), b->st), "reset batch queue");
+        PML_BCU(cudaMemsetAsync(b->dqueue, 0, 4 * sizeof(int), b->st), "reset batch queues");
         b->launches = p;
     }
     int64_t left = n;

@@ -212,7 +212,7 @@ __device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUt
         if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 1)) {
             // give the copies still in flight a bounded chance to land, then stop
             for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2)
-                mbar_wait(&bars[(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0);
+                mbar_wait(&bars[(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0, kDrainLimitNs);
             return false;
         }
         const T *sU = reinterpret_cast<const T *>(wbase + slot * STAGE_BYTES) + NC * lane;
@@ -247,17 +247,34 @@ __device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUt
 // Layer frame: Horner form with the full operator of Eq. 3 (or its transpose), streamed
 // down the rows by independent warps.
 //
-// A warp owns 32 consecutive columns (lane = column; lanes 4..27 are its kL2W outputs,
-// lanes 0..3 and 28..31 the halo of the four applications of A) and a run of rows of one
-// frame rectangle.  When input row p arrives, level 4 (z4 = y + dt/4 A y) produces row
-// p-1, level 3 row p-2, level 2 row p-3 and level 1 (y' = y + dt A z2) the output row
-// p-4.  Row neighbours of each level come from three-row register rings, column
-// neighbours from shuffles, the base y of every level from the warp's TMA ring; no block
-// barrier is needed.  Templated on the axes whose aux fields are active in the strip.
+// A warp owns 32 consecutive columns (lane = column; lanes 4..27 are its 24 outputs,
+// lanes 0..3 and 28..31 the halo of the four applications of A) and a run of rows of the
+// frame.  Input rows arrive through the warp's TMA ring, kL2CH rows per box.  The four
+// Horner levels z4 = y + dt/4 A y, z3 = y + dt/3 A z4, z2 = y + dt/2 A z3 and
+// y' = y + dt A z2 are skewed by two rows each: when input row p arrives, level 4 gives
+// row p-1, level 3 row p-3, level 2 row p-5 and level 1 the output row p-7.  Each level
+// then reads only rows finished in earlier iterations, so the four evaluations of one
+// iteration are independent and overlap in the pipeline.  Row neighbours of each level
+// come from four-row register rings, column neighbours from shuffles, the base y of
+// every level from the TMA ring; no block barrier is needed.  Templated on the axes whose
+// aux fields are active in the strip.
 // ------------------------------------------------------------------------------------
 
-constexpr int kL2CH = 3;     // rows per TMA box (the register ring period)
-constexpr int kL2S = 8;      // TMA stages per warp: chunks c-2, c-1, c resident, the rest in flight
+constexpr int kL2CH = 4;         // rows per TMA box
+constexpr int kL2SigRows = 80;   // sigma_y table rows per warp (input rows of an item)
+template <typename T> struct L2Cfg {
+    static constexpr int W = 1;                         // columns per lane
+    static constexpr int COLS = 32 * W;                 // columns of one strip (box width)
+    static constexpr int OUT = COLS - 8;                // output columns of one strip
+    // TMA ring per warp: S boxes of kL2CH rows, RR = S kL2CH rows (a power of two) per
+    // field; boxes c-2, c-1, c are being read, the others are in flight
+    static constexpr int S = 4;
+    static constexpr int RR = S * kL2CH;
+    static constexpr int MINB = sizeof(T) == 4 ? 4 : 2;   // resident CTAs per SM (the launch's cap)
+    static constexpr int WE = 6 * RR * COLS;   // ring elements per warp, sized for the largest class
+    static constexpr size_t smem() { return size_t(4) * WE * sizeof(T) + 128; }
+    static_assert((RR & (RR - 1)) == 0, "ring rows must be a power of two");
+};
 
 template <int MASK> struct Fields2 {
     static constexpr int NAX = ((MASK >> 0) & 1) + ((MASK >> 1) & 1);
@@ -272,43 +289,75 @@ template <int MASK> struct Fields2 {
     }
 };
 
-template <typename T> struct Sig2 {
-    T si[2], sm[2];   // sigma_a[i_a], sigma_a[i_a - 1]
+// Lane vectors: W adjacent columns per lane.  W = 2 (FP32) uses the packed FP32x2
+// instructions (each lane of the pair rounds exactly like the scalar operation).
+template <typename T, int W> struct LV;
+template <typename T> struct LV<T, 1> {
+    using V = T;
+    static __device__ __forceinline__ V bc(T a) { return a; }
+    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+    static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
+    static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return ::fma(a, b, c); }
+    static __device__ __forceinline__ V sel(V m, V x) { return m != T(0) ? x : T(0); }   // x where m != 0
+    static __device__ __forceinline__ V left(V c) { return __shfl_up_sync(0xffffffffu, c, 1); }
+    static __device__ __forceinline__ V right(V c) { return __shfl_down_sync(0xffffffffu, c, 1); }
+    static __device__ __forceinline__ V ld(const T *p) { return *p; }
+};
+template <> struct LV<float, 2> {
+    using V = float2;
+    static __device__ __forceinline__ V bc(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V sel(V m, V x) { return make_float2(m.x != 0.f ? x.x : 0.f, m.y != 0.f ? x.y : 0.f); }
+    static __device__ __forceinline__ V left(V c) { return make_float2(__shfl_up_sync(0xffffffffu, c.y, 1), c.x); }
+    static __device__ __forceinline__ V right(V c) { return make_float2(c.y, __shfl_down_sync(0xffffffffu, c.x, 1)); }
+    static __device__ __forceinline__ V ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 };
 
-// A z (or A^T z) at one vertex; N(f, d): d = 0 centre, 1 x-, 2 x+, 3 y-, 4 y+.
-template <typename T, bool ADJ, int MASK, typename Get>
-__device__ __forceinline__ void apply_A2(const Get &N, const Sig2<T> &s, T ih, T ih2, T i2h, T *o)
+template <typename V> struct Sig2 {
+    V si[2], sm[2];   // sigma_a[i_a], sigma_a[i_a - 1]
+};
+
+// A z (or A^T z) at the lane's vertices; N(f, d): d = 0 centre, 1 x-, 2 x+, 3 y-, 4 y+.
+template <typename O, bool ADJ, int MASK, typename Get>
+__device__ __forceinline__ void apply_A2(const Get &N, const Sig2<typename O::V> &s, typename O::V ih,
+                                         typename O::V ih2, typename O::V i2h, typename O::V *o)
 {
     using F = Fields2<MASK>;
-    const T half = T(0.5);
+    using V = typename O::V;
+    const V m2 = O::bc(-2), mhalf = O::bc(-0.5);
     if (!ADJ) {
-        const T U0 = N(0, 0);
-        const T lap = ((N(0, 2) + N(0, 1)) - T(2) * U0) + ((N(0, 4) + N(0, 3)) - T(2) * U0);
-        T aV = lap * ih2;
+        const V U0 = N(0, 0);
+        const V lap = O::add(O::fma(m2, U0, O::add(N(0, 2), N(0, 1))), O::fma(m2, U0, O::add(N(0, 4), N(0, 3))));
+        V aV = O::mul(lap, ih2);
         o[0] = N(1, 0);
 #pragma unroll
         for (int k = 0; k < F::NAX; ++k) {
             const int ax = F::axis(k), fp = 2 + 2 * k, fq = 3 + 2 * k, dm = 1 + 2 * ax, dp = 2 + 2 * ax;
-            const T si = s.si[ax], sm = s.sm[ax];
-            aV += (si * N(fq, dp) - sm * N(fp, dm)) * ih;
-            const T dU = (N(0, dp) - N(0, dm)) * i2h;
-            o[fp] = si != T(0) ? -half * (sm * N(fp, dm) + si * N(fp, 0)) - dU : T(0);
-            o[fq] = sm != T(0) ? -half * (sm * N(fq, 0) + si * N(fq, dp)) - dU : T(0);
+            const V si = s.si[ax], sm = s.sm[ax];
+            const V phm = N(fp, dm), psp = N(fq, dp);
+            aV = O::fma(O::sub(O::mul(si, psp), O::mul(sm, phm)), ih, aV);
+            const V ndU = O::mul(O::sub(N(0, dm), N(0, dp)), i2h);   // -(U(+) - U(-)) / 2h
+            o[fp] = O::sel(si, O::fma(mhalf, O::fma(sm, phm, O::mul(si, N(fp, 0))), ndU));
+            o[fq] = O::sel(sm, O::fma(mhalf, O::fma(sm, N(fq, 0), O::mul(si, psp)), ndU));
         }
         o[1] = aV;
     } else {
-        const T V0 = N(1, 0);
-        const T lap = ((N(1, 2) + N(1, 1)) - T(2) * V0) + ((N(1, 4) + N(1, 3)) - T(2) * V0);
-        T aU = lap * ih2;
+        const V V0 = N(1, 0);
+        const V lap = O::add(O::fma(m2, V0, O::add(N(1, 2), N(1, 1))), O::fma(m2, V0, O::add(N(1, 4), N(1, 3))));
+        V aU = O::mul(lap, ih2);
         o[1] = N(0, 0);
 #pragma unroll
         for (int k = 0; k < F::NAX; ++k) {
             const int ax = F::axis(k), fp = 2 + 2 * k, fq = 3 + 2 * k, dm = 1 + 2 * ax, dp = 2 + 2 * ax;
-            const T si = s.si[ax], sm = s.sm[ax];
-            aU += ((N(fp, dp) - N(fp, dm)) + (N(fq, dp) - N(fq, dm))) * i2h;
-            o[fp] = si != T(0) ? -si * N(1, dp) * ih - half * si * (N(fp, dp) + N(fp, 0)) : T(0);
-            o[fq] = sm != T(0) ? sm * N(1, dm) * ih - half * sm * (N(fq, 0) + N(fq, dm)) : T(0);
+            const V si = s.si[ax], sm = s.sm[ax];
+            aU = O::fma(O::add(O::sub(N(fp, dp), N(fp, dm)), O::sub(N(fq, dp), N(fq, dm))), i2h, aU);
+            // -si V(+)/h - si/2 (Phi(+) + Phi),  sm V(-)/h - sm/2 (Psi + Psi(-))
+            o[fp] = O::sel(si, O::mul(si, O::fma(mhalf, O::add(N(fp, dp), N(fp, 0)), O::mul(O::bc(-1), O::mul(N(1, dp), ih)))));
+            o[fq] = O::sel(sm, O::mul(sm, O::fma(mhalf, O::add(N(fq, 0), N(fq, dm)), O::mul(N(1, dm), ih))));
         }
         o[0] = aU;
     }
@@ -322,186 +371,267 @@ struct Out6 {
 };
 
 template <typename T, int MASK>
-__device__ __forceinline__ void issue_chunk2(T *dst, const Maps6 &maps, int32_t x, int32_t y, uint64_t *bar)
+__device__ __forceinline__ void issue_rows2(T *ring, const Maps6 &maps, int32_t x, int32_t y, int row0, uint64_t *bar)
 {
     using F = Fields2<MASK>;
-    constexpr int FE = kL2CH * 32;
-    mbar_arrive_expect_tx(bar, uint32_t(F::NF * FE * sizeof(T)));
+    constexpr int RR = L2Cfg<T>::RR, COLS = L2Cfg<T>::COLS;
+    mbar_arrive_expect_tx(bar, uint32_t(F::NF * kL2CH * COLS * sizeof(T)));
 #pragma unroll
-    for (int f = 0; f < F::NF; ++f) tma_load_2d(dst + f * FE, &maps.m[F::gid(f)], x, y, bar);
+    for (int f = 0; f < F::NF; ++f) tma_load_2d(ring + (f * RR + row0) * COLS, &maps.m[F::gid(f)], x, y, bar);
 }
 
-// One work item (a strip of one frame rectangle) streamed by one warp; `ring` is the
-// warp's TMA ring (kL2S stages of NF fields x kL2CH rows x 32 columns).
+// One work item (a strip of the frame) streamed by one warp.  Lane l holds columns
+// x0 - 4 + W l .. + W - 1 (W = L2Cfg::W); the outputs are the columns x0 .. x0 + OUT - 1
+// of lanes 4/W .. 31 - 4/W.  `ring` is the warp's row ring ([NF][RR][COLS]; input row q
+// of the item sits in ring row (kL2CH use + q) mod RR), `sy` its sigma_y table
+// (2 x kL2SigRows).  The warp's barriers are initialised once per kernel; `use` counts
+// the boxes this warp has consumed and gives each box's slot and phase parity.  Output
+// rows ylo..yhi may run past T1 - 1 (the band across the periodic seam of y): rows and
+// box coordinates wrap by T1.  One loop iteration handles one input row p; the register
+// rings hold three rows of each level and rotate by one row per iteration (a compact loop
+// body keeps the instruction stream in cache).
 template <typename T, bool ADJ, int MASK>
-__device__ __forceinline__ void layer2d_item(const Maps6 &maps, const Out6 &out, const Layer2DArgs &a,
-                                          const LayerTile &tile, T *ring, uint64_t *bars, int lane)
+__device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out, const Layer2DArgs &a,
+                                             const LayerTile &tile, T *ring, T *sy, uint64_t *bars, int lane,
+                                             uint32_t &use)
 {
     using F = Fields2<MASK>;
-    constexpr int NF = F::NF, CH = kL2CH, S = kL2S, FE = CH * 32, SE = NF * FE;
+    constexpr int W = L2Cfg<T>::W, COLS = L2Cfg<T>::COLS;
+    using O = LV<T, W>;
+    using V = typename O::V;
+    constexpr int NF = F::NF, CH = kL2CH, S = L2Cfg<T>::S, RR = L2Cfg<T>::RR;
     const Geom &g = a.g;
+    const int T1 = int(g.T[1]);
     const int nout = tile.yhi - tile.ylo + 1, nin = nout + 8;
-    const int nch = (nin + CH - 1) / CH;
-    const int32_t tx = tile.x0 - 4 + G, ty = tile.ylo - 4 + G;
+    const int nch = (nin + CH - 1) / CH;          // boxes that hold input rows
+    const int32_t tx = tile.x0 - 4 + G;
+    auto box_y = [&](int c) -> int32_t {          // box row of box c (rows stay in -4 .. T1 + 3)
+        int y = tile.ylo - 4 + c * CH;
+        if (y > T1) y -= T1;
+        return int32_t(y + G);
+    };
+    auto issue = [&](int c) {
+        const uint32_t k = use + uint32_t(c);
+        issue_rows2<T, MASK>(ring, maps, tx, box_y(c), int((k % S) * CH), &bars[k % S]);
+    };
     if (lane == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-        const int npro = nch < S ? nch : S;
-        for (int c = 0; c < npro; ++c) issue_chunk2<T, MASK>(ring + c * SE, maps, tx, ty + c * CH, &bars[c]);
+        fence_proxy_async();   // earlier generic reads of the ring before async writes
+        for (int c = 0; c < nch && c < S; ++c) issue(c);
+    }
+    if (MASK & 2) {   // sigma_y[row], sigma_y[row - 1] of every input row
+        const T *sgy = static_cast<const T *>(a.sig[1]);
+        for (int q = lane; q < nin; q += 32) {
+            int yi = tile.ylo - 4 + q;
+            yi += yi < 0 ? T1 : 0;
+            yi -= yi >= T1 ? T1 : 0;
+            yi -= yi >= T1 ? T1 : 0;
+            sy[q] = sgy[yi];
+            sy[kL2SigRows + q] = sgy[yi == 0 ? T1 - 1 : yi - 1];
+        }
     }
     __syncwarp();
 
-    const T *sgx = static_cast<const T *>(a.sig[0]);
-    const T *sgy = static_cast<const T *>(a.sig[1]);
-    const int64_t gx = int64_t(tile.x0) - 4 + lane;
-    Sig2<T> sg;
+    const int64_t gx0 = int64_t(tile.x0) - 4 + W * lane;   // first column of the lane
+    Sig2<V> sgx;
     {
+        const T *sgxp = static_cast<const T *>(a.sig[0]);
         const int T0 = int(g.T[0]);
-        int xi = int(gx);
-        xi += xi < 0 ? T0 : (xi >= T0 ? -T0 : 0);
-        sg.si[0] = sgx[xi];
-        sg.sm[0] = sgx[xi == 0 ? T0 - 1 : xi - 1];
-    }
-    const int T1 = int(g.T[1]);
-    auto ysig = [&](int q) {   // rows of a work item lie within one period of [0, T1)
-        int yi = tile.ylo - 4 + q;
-        yi += yi < 0 ? T1 : (yi >= T1 ? -T1 : 0);
-        sg.si[1] = sgy[yi];
-        sg.sm[1] = sgy[yi == 0 ? T1 - 1 : yi - 1];
-    };
-    const bool out_lane = lane >= 4 && lane <= 27 && gx >= tile.xlo && gx <= tile.xhi;
-    const LayerConstT<T> &lk = lconst_of<T>(a.k);
-    const T ih = lk.ih, ih2 = lk.ih2, i2h = lk.i2h, c4 = lk.c4, c3 = lk.c3, c2 = lk.c2, c1 = lk.c1;
-    T z4[3][NF], z3[3][NF], z2[3][NF];
-
-    for (int c = 0; c < nch; ++c) {
-        if (!mbar_wait(&bars[c % S], (c / S) & 1, a.err, 2)) {
-            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2) mbar_wait(&bars[c2 % S], (c2 / S) & 1, nullptr, 0);
-            return;
+        T si[W], sm[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int xi = int((((gx0 + k) % T0) + T0) % T0);
+            si[k] = sgxp[xi];
+            sm[k] = sgxp[xi == 0 ? T0 - 1 : xi - 1];
         }
-        const T *cur = ring + (c % S) * SE + lane;
-        const T *prv = ring + ((c + S - 1) % S) * SE + lane;
-        const T *prv2 = ring + ((c + S - 2) % S) * SE + lane;
+        if constexpr (W == 1) {
+            sgx.si[0] = si[0];
+            sgx.sm[0] = sm[0];
+        } else {
+            sgx.si[0] = make_float2(si[0], si[W - 1]);
+            sgx.sm[0] = make_float2(sm[0], sm[W - 1]);
+        }
+        sgx.si[1] = O::bc(T(0));
+        sgx.sm[1] = O::bc(T(0));
+    }
+    auto sig_at = [&](int q) {   // sigma of input row q (clamped: rows outside feed nothing)
+        Sig2<V> s = sgx;
+        if (MASK & 2) {
+            q = q < 0 ? 0 : (q >= nin ? nin - 1 : q);
+            s.si[1] = O::bc(sy[q]);
+            s.sm[1] = O::bc(sy[kL2SigRows + q]);
+        }
+        return s;
+    };
+    bool out_col[W];
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
-            const int p = c * CH + j;
-            if (p < nin) {
-                const int PH = j % 3;
-                // own-column value of input row p - k (k <= 4), field f: rows of this chunk or
-                // of one of the two before it
-                auto Y = [&](int k, int f) -> T {
-                    const int r = j - k;
-                    return r >= 0 ? cur[f * FE + r * 32]
-                                  : (r >= -CH ? prv[f * FE + (r + CH) * 32] : prv2[f * FE + (r + 2 * CH) * 32]);
-                };
-                if (p >= 2) {   // level 4 at row p-1
-                    T cen[NF], xm[NF], xp[NF];
+    for (int k = 0; k < W; ++k)
+        out_col[k] = gx0 + k >= tile.x0 && gx0 + k < tile.x0 + L2Cfg<T>::OUT && gx0 + k >= tile.xlo &&
+                     gx0 + k <= tile.xhi;
+    bool any_out = false;
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        cen[f] = Y(1, f);
-                        xm[f] = __shfl_up_sync(0xffffffffu, cen[f], 1);
-                        xp[f] = __shfl_down_sync(0xffffffffu, cen[f], 1);
-                    }
-                    auto N = [&](int f, int d) -> T {
-                        switch (d) {
-                        case 0: return cen[f];
-                        case 1: return xm[f];
-                        case 2: return xp[f];
-                        case 3: return Y(2, f);
-                        default: return Y(0, f);
-                        }
-                    };
-                    ysig(p - 1);
-                    T r[NF];
-                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
+    for (int k = 0; k < W; ++k) any_out = any_out || out_col[k];
+    const LayerConstT<T> &lk = lconst_of<T>(a.k);
+    const V ih = O::bc(lk.ih), ih2 = O::bc(lk.ih2), i2h = O::bc(lk.i2h), c4 = O::bc(lk.c4), c3 = O::bc(lk.c3),
+            c2 = O::bc(lk.c2), c1 = O::bc(lk.c1);
+    const int qmax = nch * CH - 1;                 // last row the boxes brought in
+    const uint32_t rbase = uint32_t(CH) * use;
+    // the lane's values of input row q (clamped into the rows brought in), field f at + f RR COLS
+    auto rowp = [&](int q) -> const T * {
+        q = q < 0 ? 0 : (q > qmax ? qmax : q);
+        return ring + int((rbase + uint32_t(q)) & uint32_t(RR - 1)) * COLS + W * lane;
+    };
+    // level rings: [0] row r-1, [1] row r, [2] row r+1 of the row r the level reads
+    V z4[3][NF], z3[3][NF], z2[3][NF];
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) z4[(PH + 2) % 3][f] = cen[f] + c4 * r[f];
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) z4[k][f] = z3[k][f] = z2[k][f] = O::bc(T(0));
+
+#pragma unroll 1
+    for (int p = 0; p < nin + 3; ++p) {
+        if ((p & (CH - 1)) == 0) {
+            const int c = p / CH;
+            // box c - 3 was last read in iteration p - 2: refill its slot with box c - 3 + S
+            if (c >= 3 && c - 3 + S < nch) {
+                __syncwarp();
+                if (lane == 0) {
+                    fence_proxy_async();
+                    issue(c - 3 + S);
                 }
-                if (p >= 4) {   // level 3 at row p-2
-                    T xm[NF], xp[NF];
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        xm[f] = __shfl_up_sync(0xffffffffu, z4[(PH + 1) % 3][f], 1);
-                        xp[f] = __shfl_down_sync(0xffffffffu, z4[(PH + 1) % 3][f], 1);
+            }
+            if (c < nch) {
+                const uint32_t k = use + uint32_t(c);
+                if (!mbar_wait(&bars[k % S], (k / S) & 1, a.err, 2)) {
+                    for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2) {
+                        const uint32_t k2 = use + uint32_t(c2);
+                        mbar_wait(&bars[k2 % S], (k2 / S) & 1, nullptr, 0, kDrainLimitNs);
                     }
-                    auto N = [&](int f, int d) -> T {
-                        switch (d) {
-                        case 0: return z4[(PH + 1) % 3][f];
-                        case 1: return xm[f];
-                        case 2: return xp[f];
-                        case 3: return z4[PH][f];
-                        default: return z4[(PH + 2) % 3][f];
-                        }
-                    };
-                    ysig(p - 2);
-                    T r[NF];
-                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) z3[(PH + 1) % 3][f] = Y(2, f) + c3 * r[f];
+                    return false;
                 }
-                if (p >= 6) {   // level 2 at row p-3
-                    T xm[NF], xp[NF];
+            }
+        }
+        const T *y0 = rowp(p), *y1 = rowp(p - 1), *y2 = rowp(p - 2), *y3 = rowp(p - 3), *y5 = rowp(p - 5),
+                *y7 = rowp(p - 7);
+        constexpr int FS = RR * COLS;   // field stride in the ring
+        V n4[NF], n3[NF], n2[NF], r[NF];
+        // level 4 at row p-1 (input rows p-2, p-1, p)
+        {
+            V cen[NF], xm[NF], xp[NF];
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        xm[f] = __shfl_up_sync(0xffffffffu, z3[PH][f], 1);
-                        xp[f] = __shfl_down_sync(0xffffffffu, z3[PH][f], 1);
-                    }
-                    auto N = [&](int f, int d) -> T {
-                        switch (d) {
-                        case 0: return z3[PH][f];
-                        case 1: return xm[f];
-                        case 2: return xp[f];
-                        case 3: return z3[(PH + 2) % 3][f];
-                        default: return z3[(PH + 1) % 3][f];
-                        }
-                    };
-                    ysig(p - 3);
-                    T r[NF];
-                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) z2[PH][f] = Y(3, f) + c2 * r[f];
+            for (int f = 0; f < NF; ++f) {
+                cen[f] = O::ld(y1 + f * FS);
+                xm[f] = O::left(cen[f]);
+                xp[f] = O::right(cen[f]);
+            }
+            auto N = [&](int f, int d) -> V {
+                switch (d) {
+                case 0: return cen[f];
+                case 1: return xm[f];
+                case 2: return xp[f];
+                case 3: return O::ld(y2 + f * FS);
+                default: return O::ld(y0 + f * FS);
                 }
-                if (p >= 8) {   // level 1: output row p-4
-                    T xm[NF], xp[NF];
+            };
+            apply_A2<O, ADJ, MASK>(N, sig_at(p - 1), ih, ih2, i2h, r);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        xm[f] = __shfl_up_sync(0xffffffffu, z2[(PH + 2) % 3][f], 1);
-                        xp[f] = __shfl_down_sync(0xffffffffu, z2[(PH + 2) % 3][f], 1);
-                    }
-                    auto N = [&](int f, int d) -> T {
-                        switch (d) {
-                        case 0: return z2[(PH + 2) % 3][f];
-                        case 1: return xm[f];
-                        case 2: return xp[f];
-                        case 3: return z2[(PH + 1) % 3][f];
-                        default: return z2[PH][f];
-                        }
-                    };
-                    ysig(p - 4);
-                    T r[NF];
-                    apply_A2<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-                    if (out_lane) {
-                        const int64_t y = int64_t(tile.ylo) + p - 8;
-                        const bool edge = near_edge(g, gx, y, 0);
+            for (int f = 0; f < NF; ++f) n4[f] = O::fma(c4, r[f], cen[f]);
+        }
+        // level 3 at row p-3 (z4 rows p-4, p-3, p-2)
+        {
+            V xm[NF], xp[NF];
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            const T val = Y(4, f) + c1 * r[f];
-                            T *dst = static_cast<T *>(out.p[F::gid(f)]);
-                            if (edge) store_wrapped(dst, g, gx, y, 0, val);
-                            else dst[g.origin + gx + y * g.P] = val;
-                        }
+            for (int f = 0; f < NF; ++f) {
+                xm[f] = O::left(z4[1][f]);
+                xp[f] = O::right(z4[1][f]);
+            }
+            auto N = [&](int f, int d) -> V {
+                switch (d) {
+                case 0: return z4[1][f];
+                case 1: return xm[f];
+                case 2: return xp[f];
+                case 3: return z4[0][f];
+                default: return z4[2][f];
+                }
+            };
+            apply_A2<O, ADJ, MASK>(N, sig_at(p - 3), ih, ih2, i2h, r);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) n3[f] = O::fma(c3, r[f], O::ld(y3 + f * FS));
+        }
+        // level 2 at row p-5 (z3 rows p-6, p-5, p-4)
+        {
+            V xm[NF], xp[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                xm[f] = O::left(z3[1][f]);
+                xp[f] = O::right(z3[1][f]);
+            }
+            auto N = [&](int f, int d) -> V {
+                switch (d) {
+                case 0: return z3[1][f];
+                case 1: return xm[f];
+                case 2: return xp[f];
+                case 3: return z3[0][f];
+                default: return z3[2][f];
+                }
+            };
+            apply_A2<O, ADJ, MASK>(N, sig_at(p - 5), ih, ih2, i2h, r);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) n2[f] = O::fma(c2, r[f], O::ld(y5 + f * FS));
+        }
+        // level 1 at row p-7 (z2 rows p-8, p-7, p-6): output row p-11 of the item
+        {
+            V xm[NF], xp[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                xm[f] = O::left(z2[1][f]);
+                xp[f] = O::right(z2[1][f]);
+            }
+            auto N = [&](int f, int d) -> V {
+                switch (d) {
+                case 0: return z2[1][f];
+                case 1: return xm[f];
+                case 2: return xp[f];
+                case 3: return z2[0][f];
+                default: return z2[2][f];
+                }
+            };
+            apply_A2<O, ADJ, MASK>(N, sig_at(p - 7), ih, ih2, i2h, r);
+            const int ro = p - 11;
+            if (any_out && ro >= 0 && ro < nout) {
+                int64_t y = int64_t(tile.ylo) + ro;
+                if (y >= T1) y -= T1;
+                bool edge = false;
+#pragma unroll
+                for (int k = 0; k < W; ++k) edge = edge || near_edge(g, gx0 + k, y, 0);
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < W; ++k) all = all && out_col[k];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const V val = O::fma(c1, r[f], O::ld(y7 + f * FS));
+                    T *dst = static_cast<T *>(out.p[F::gid(f)]);
+                    if (!edge && all) {
+                        *reinterpret_cast<V *>(dst + g.origin + gx0 + y * g.P) = val;
+                    } else {
+                        const T *vv = reinterpret_cast<const T *>(&val);
+#pragma unroll
+                        for (int k = 0; k < W; ++k)
+                            if (out_col[k]) store_wrapped(dst, g, gx0 + k, y, 0, vv[k]);
                     }
                 }
             }
         }
-        __syncwarp();
-        // chunk c-2 is no longer needed (rows >= (c+1) CH - 4 > (c-1) CH remain in use): refill it
-        if (lane == 0 && c >= 2 && c - 2 + S < nch) {
-            fence_proxy_async();
-            const int st = (c - 2) % S;
-            issue_chunk2<T, MASK>(ring + st * SE, maps, tx, ty + (c - 2 + S) * CH, &bars[st]);
+        // rotate the rings by one row
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            z4[0][f] = z4[1][f]; z4[1][f] = z4[2][f]; z4[2][f] = n4[f];
+            z3[0][f] = z3[1][f]; z3[1][f] = z3[2][f]; z3[2][f] = n3[f];
+            z2[0][f] = z2[1][f]; z2[1][f] = z2[2][f]; z2[2][f] = n2[f];
         }
     }
+    __syncwarp();
+    use += uint32_t(nch);
+    return true;
 }
 
 // ------------------------------------------------------------------------------------
@@ -616,7 +746,14 @@ __global__ void __launch_bounds__(32 * BY, MINB)
             if (b == 0) okw = wait_chunk(0);
             if (okw && b + 1 < nch) okw = wait_chunk(b + 1);
             ok = __syncthreads_and(okw);
-            if (!ok) break;
+            if (!ok) {   // let the copies in flight (chunks b .. b + NCH - 2 at most) land
+                if (tid == 0)
+                    for (int c = b; c < nch && c < b + NCH; ++c) {
+                        const uint32_t uu = use + c;
+                        mbar_wait(&bars[uu % NCH], (uu / NCH) & 1u, nullptr, 0, kDrainLimitNs);
+                    }
+                break;
+            }
             // chunk b - 1 was last read by block b - 1 (all warps are past it): refill its slots
             if (tid == 0 && b >= 1 && b - 1 + NCH < nch) {
                 fence_proxy_async();
@@ -705,32 +842,52 @@ __device__ __forceinline__ void allow_dependent_launch()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Each warp takes items from a work queue (atomic counter) until the list is done; tiles
+// are sorted by class, so warps run the same class at the same time.
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, L2Cfg<T>::MINB)
     k_layer2d(const __grid_constant__ Maps6 maps, const Out6 out, const Layer2DArgs a)
 {
-    constexpr int SE = 6 * kL2CH * 32;   // ring stage sized for the largest class
-    __shared__ __align__(8) uint64_t bars[4][kL2S];
+    constexpr int S = L2Cfg<T>::S, WE = L2Cfg<T>::WE;
+    __shared__ __align__(8) uint64_t bars[4][S];
+    __shared__ T sig_sh[4][2 * kL2SigRows];
     extern __shared__ unsigned char smem_dyn[];
     T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
     allow_dependent_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * 4 + warp;
-    if (item >= a.ntiles) return;   // whole warp; the kernel has no block barrier
-    T *ring = smem + warp * kL2S * SE;
-    const LayerTile tile = a.tiles[item];
-    switch (tile.flags & 3) {
-    case 0: layer2d_item<T, ADJ, 0>(maps, out, a, tile, ring, bars[warp], lane); break;
-    case 1: layer2d_item<T, ADJ, 1>(maps, out, a, tile, ring, bars[warp], lane); break;
-    case 2: layer2d_item<T, ADJ, 2>(maps, out, a, tile, ring, bars[warp], lane); break;
-    default: layer2d_item<T, ADJ, 3>(maps, out, a, tile, ring, bars[warp], lane); break;
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    T *ring = smem + warp * WE;
+    uint32_t use = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.queue[1 - a.parity] = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&a.queue[a.parity], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.ntiles) break;
+        const LayerTile tile = a.tiles[item];
+        bool ok;
+        switch (tile.flags & 3) {
+        case 0: ok = layer2d_item<T, ADJ, 0>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 1: ok = layer2d_item<T, ADJ, 1>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 2: ok = layer2d_item<T, ADJ, 2>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        default: ok = layer2d_item<T, ADJ, 3>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        }
+        if (!ok) break;
     }
 }
 
-template <typename T> static size_t layer2d_smem() { return size_t(4) * kL2S * 6 * kL2CH * 32 * sizeof(T) + 128; }
+template <typename T> static size_t layer2d_smem() { return L2Cfg<T>::smem(); }
+
+int layer2d_box_rows() { return kL2CH; }
+int layer2d_box_cols(int prec) { return prec == 32 ? L2Cfg<float>::COLS : L2Cfg<double>::COLS; }
+int layer2d_tile_cols(int prec) { return prec == 32 ? L2Cfg<float>::OUT : L2Cfg<double>::OUT; }
 
 template <typename T, bool ADJ>
-static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, cudaStream_t st)
+static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st)
 {
     static bool done = false;
     const size_t sm = layer2d_smem<T>();
@@ -739,22 +896,29 @@ static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a
         if (e != cudaSuccess) return e;
         done = true;
     }
-    k_layer2d<T, ADJ><<<(a.ntiles + 3) / 4, 128, sm, st>>>(m, o, a);
+    k_layer2d<T, ADJ><<<grid, 128, sm, st>>>(m, o, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp, const Layer2DArgs &a,
-                           cudaStream_t st)
+int layer2d_grid(int prec, int ntiles, int sm_count)
 {
-    if (a.ntiles <= 0) return cudaSuccess;
+    const int need = (ntiles + 3) / 4;
+    const int cap = (prec == 32 ? L2Cfg<float>::MINB : L2Cfg<double>::MINB) * sm_count;
+    return need < cap ? need : cap;
+}
+
+cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp, const Layer2DArgs &a,
+                           int grid, cudaStream_t st)
+{
+    if (a.ntiles <= 0 || grid <= 0) return cudaSuccess;
     Maps6 m;
     Out6 o;
     for (int f = 0; f < 6; ++f) {
         m.m[f] = tm[f];
         o.p[f] = outp[f];
     }
-    if (prec == 32) return adjoint ? launch_l2<float, true>(m, o, a, st) : launch_l2<float, false>(m, o, a, st);
-    return adjoint ? launch_l2<double, true>(m, o, a, st) : launch_l2<double, false>(m, o, a, st);
+    if (prec == 32) return adjoint ? launch_l2<float, true>(m, o, a, grid, st) : launch_l2<float, false>(m, o, a, grid, st);
+    return adjoint ? launch_l2<double, true>(m, o, a, grid, st) : launch_l2<double, false>(m, o, a, grid, st);
 }
 
 template <typename T, bool ADJ, int NC, int CH, int S, int MINB>
@@ -963,7 +1127,7 @@ __global__ void __launch_bounds__(128, MINB) k_interior2d_batch(const Batch2DArg
             else hi = mid - 1;
         }
         const GridDesc2 &d = b.desc[lo];
-        const Interior2DArgs &a = d.in;
+        const Interior2DArgs a = d.in;   // a local copy: stores to the fields cannot alias it
         const int k = item - b.item_off[lo];
         const int st = k / d.rblocks, rb = k - st * d.rblocks;
         const int64_t y0 = a.yr.lo + int64_t(rb) * ROWS;
@@ -979,26 +1143,42 @@ __global__ void __launch_bounds__(128, MINB) k_interior2d_batch(const Batch2DArg
 }
 
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(128) k_layer2d_batch(const Batch2DArgs b)
+__global__ void __launch_bounds__(128, L2Cfg<T>::MINB) k_layer2d_batch(const Batch2DArgs b)
 {
-    constexpr int SE = 6 * kL2CH * 32;
-    __shared__ __align__(8) uint64_t bars[4][kL2S];
+    constexpr int S = L2Cfg<T>::S, WE = L2Cfg<T>::WE;
+    __shared__ __align__(8) uint64_t bars[4][S];
+    __shared__ T sig_sh[4][2 * kL2SigRows];
     extern __shared__ unsigned char smem_dyn[];
     T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
     allow_dependent_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * 4 + warp;
-    if (item >= b.ntiles) return;   // whole warp; the kernel has no block barrier
-    T *ring = smem + warp * kL2S * SE;
-    const LayerTile tile = b.tiles[item];
-    const GridDesc2 &d = b.desc[b.tile_grid[item]];
-    const Maps6 &maps = *reinterpret_cast<const Maps6 *>(&d.tm_lay[b.parity][0]);
-    const Out6 &out = *reinterpret_cast<const Out6 *>(&d.out[b.parity][0]);
-    switch (tile.flags & 3) {
-    case 0: layer2d_item<T, ADJ, 0>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
-    case 1: layer2d_item<T, ADJ, 1>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
-    case 2: layer2d_item<T, ADJ, 2>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
-    default: layer2d_item<T, ADJ, 3>(maps, out, d.lay, tile, ring, bars[warp], lane); break;
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    T *ring = smem + warp * WE;
+    uint32_t use = 0;
+    int *const lq = b.queue + 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) lq[1 - b.parity] = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&lq[b.parity], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= b.ntiles) break;
+        const LayerTile tile = b.tiles[item];
+        const GridDesc2 &d = b.desc[b.tile_grid[item]];
+        const Maps6 &maps = *reinterpret_cast<const Maps6 *>(&d.tm_lay[b.parity][0]);
+        const Out6 out = *reinterpret_cast<const Out6 *>(&d.out[b.parity][0]);
+        const Layer2DArgs la = d.lay;   // local copies: stores to the fields cannot alias them
+        bool ok;
+        switch (tile.flags & 3) {
+        case 0: ok = layer2d_item<T, ADJ, 0>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 1: ok = layer2d_item<T, ADJ, 1>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 2: ok = layer2d_item<T, ADJ, 2>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        default: ok = layer2d_item<T, ADJ, 3>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        }
+        if (!ok) break;
     }
 }
 
@@ -1071,13 +1251,13 @@ cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int g
     return with_b2(prec, v, [&](auto k) { return decltype(k)::launch(a, grid, st, overlap_previous); });
 }
 
-cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, cudaStream_t st)
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, cudaStream_t st)
 {
-    if (a.ntiles <= 0) return cudaSuccess;
+    if (a.ntiles <= 0 || grid <= 0) return cudaSuccess;
     cudaError_t e = with_b2(prec, 0, [](auto k) { return decltype(k)::prep(); });
     if (e != cudaSuccess) return e;
-    if (prec == 32) k_layer2d_batch<float, false><<<(a.ntiles + 3) / 4, 128, layer2d_smem<float>(), st>>>(a);
-    else k_layer2d_batch<double, false><<<(a.ntiles + 3) / 4, 128, layer2d_smem<double>(), st>>>(a);
+    if (prec == 32) k_layer2d_batch<float, false><<<grid, 128, layer2d_smem<float>(), st>>>(a);
+    else k_layer2d_batch<double, false><<<grid, 128, layer2d_smem<double>(), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
         const bool o_row = k >= 2 && k <= kBY3 + 1 && y <= a.yr.hi;
         V4<T> u[3], v[3], du[3], dv[3];
         bool ok = true;
+        int pfail = n_in;   // first plane whose wait gave up
 
         for (int p0 = 0; p0 < n_in && ok; p0 += 3) {
 #pragma unroll
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
                     }
                 }
                 ok = __syncthreads_and(ok);
+                if (!ok && pfail == n_in) pfail = p;
                 if (p < n_in && ok) {
                     if (tid == 0 && p >= 1 && p - 1 + S < n_in) {
                         fence_proxy_async();
@@ -202,7 +204,12 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
             }
         }
         __syncthreads();
-        if (!ok) return;
+        if (!ok) {   // let the copies in flight (planes pfail .. pfail + S - 2 at most) land
+            if (tid == 0)
+                for (int q = pfail; q < n_in && q < pfail + S; ++q)
+                    mbar_wait(&bars[(use + q) % S], ((use + q) / S) & 1u, nullptr, 0, kDrainLimitNs);
+            return;
+        }
         use += n_in;
     }
 }
@@ -418,6 +425,7 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
     const bool in_rect = v1 && gx >= tile.xlo && gx <= tile.xhi && gy >= tile.ylo && gy <= tile.yhi;
 
     bool ok = true;
+    int pfail = nin;   // first plane whose wait gave up
     for (int p0 = 0; p0 < nin && ok; p0 += 3) {
 #pragma unroll
         for (int PH = 0; PH < 3; ++PH) {
@@ -541,7 +549,10 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                 }
             }
             ok = __syncthreads_and(ok);
-            if (!ok) break;
+            if (!ok) {
+                pfail = p;
+                break;
+            }
             if (p < nin && tid == 0 && p >= 4 && p - 4 + S < nin) {
                 fence_proxy_async();
                 const int st = (p - 4) % S;
@@ -549,6 +560,9 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
             }
         }
     }
+    if (!ok && tid == 0)   // let the copies in flight (planes pfail .. pfail + S - 5 at most) land
+        for (int q = pfail; q < nin && q < pfail + S; ++q)
+            mbar_wait(&bars[q % S], (q / S) & 1, nullptr, 0, kDrainLimitNs);
 }
 
 template <typename T, int MASK> static size_t layer3d_smem()
