@@ -338,6 +338,7 @@ cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, co
                               cudaStream_t st);
 int interior3d_box_rows(int prec);
 int interior3d_tile_y();
+int interior3d_box_cols(int prec);   // box width of the 3D interior kernel (one strip plus halo)
 int interior3d_max_blocks_per_sm(int prec, bool adjoint);
 
 struct Layer3DArgs {

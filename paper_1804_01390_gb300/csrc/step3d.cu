@@ -3,11 +3,11 @@
 // layer-free region, Horner form with the full operator in the layer frame), with the
 // 7-point difference and streaming along z.
 //
-//  * k_interior3d: a CTA owns a 120-column x strip by kBY3 output rows and streams z.
+//  * k_interior3d: a CTA owns a 30 NC-column x strip by kBY3 output rows and streams z.
 //    One warp per region row (kBY3 + 4 rows: halo 2 in y); TMA brings one z-plane box of
 //    U and V per stage; each lane keeps three planes of U, V, DU, DV in registers (z
-//    neighbours), y neighbours come from the shared-memory plane, x neighbours from
-//    shuffles.  DU/DV planes go through a 3-slot shared ring for the second difference.
+//    neighbours; NC = 2 columns per lane, so two CTAs fit on an SM), y neighbours come
+//    from the shared-memory plane, x neighbours from shuffles.  DU/DV planes go through a 3-slot shared ring for the second difference.
 //
 //  * k_layer3d: a CTA owns an (x, y) column tile of the frame and streams z; one thread
 //    per region column (halo 4 in x and y).  The four Horner levels run pipelined in z:
@@ -21,30 +21,79 @@
 namespace pml {
 
 constexpr int kBY3 = 8;        // interior output rows per CTA
-constexpr int kStrip3 = 120;   // interior output columns per CTA (lanes 1..30)
 constexpr int kS3 = 4;         // interior TMA plane stages
 constexpr int kZSeg3 = 64;     // z planes per interior work item
+template <typename T> struct I3Cfg {
+    static constexpr int NC = 2;                         // columns per lane
+    static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;  // resident CTAs per SM
+};
 
 int interior3d_box_rows(int) { return 1; }
 int interior3d_tile_y() { return kBY3; }
+int interior3d_box_cols(int prec) { return 32 * (prec == 32 ? I3Cfg<float>::NC : I3Cfg<double>::NC); }
 
-template <typename T>
-__device__ __forceinline__ V4<T> diff7(const V4<T> &c, const V4<T> &ym, const V4<T> &yp, const V4<T> &zm,
-                                       const V4<T> &zp)
+// NC adjacent columns of one lane
+template <typename T, int NC> struct VN {
+    T c[NC];
+};
+template <typename T, int NC> __device__ __forceinline__ VN<T, NC> ldsN(const T *p)
 {
-    const T l = __shfl_up_sync(0xffffffffu, c.w, 1);
-    const T r = __shfl_down_sync(0xffffffffu, c.x, 1);
-    V4<T> o;
-    o.x = (((l + c.y) + (ym.x + yp.x)) + (zm.x + zp.x)) - T(6) * c.x;
-    o.y = (((c.x + c.z) + (ym.y + yp.y)) + (zm.y + zp.y)) - T(6) * c.y;
-    o.z = (((c.y + c.w) + (ym.z + yp.z)) + (zm.z + zp.z)) - T(6) * c.z;
-    o.w = (((c.z + r) + (ym.w + yp.w)) + (zm.w + zp.w)) - T(6) * c.w;
+    VN<T, NC> v;
+    if constexpr (sizeof(T) * NC == 8) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v.c[0] = t.x;
+        v.c[1] = t.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < NC; q += 16 / int(sizeof(T))) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(p + q);
+                v.c[q] = t.x; v.c[q + 1] = t.y; v.c[q + 2] = t.z; v.c[q + 3] = t.w;
+            } else {
+                const double2 t = *reinterpret_cast<const double2 *>(p + q);
+                v.c[q] = t.x; v.c[q + 1] = t.y;
+            }
+        }
+    }
+    return v;
+}
+template <typename T, int NC> __device__ __forceinline__ void stN(T *p, const VN<T, NC> &v)
+{
+    if constexpr (sizeof(T) * NC == 8) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v.c[0], v.c[1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NC; q += 16 / int(sizeof(T))) {
+            if constexpr (sizeof(T) == 4)
+                *reinterpret_cast<float4 *>(p + q) = make_float4(v.c[q], v.c[q + 1], v.c[q + 2], v.c[q + 3]);
+            else
+                *reinterpret_cast<double2 *>(p + q) = make_double2(v.c[q], v.c[q + 1]);
+        }
+    }
+}
+
+// Unscaled 7-point difference of one lane's NC columns; x neighbours beyond the lane from
+// the neighbouring lanes.
+template <typename T, int NC>
+__device__ __forceinline__ VN<T, NC> diff7(const VN<T, NC> &c, const VN<T, NC> &ym, const VN<T, NC> &yp,
+                                           const VN<T, NC> &zm, const VN<T, NC> &zp)
+{
+    const T l = __shfl_up_sync(0xffffffffu, c.c[NC - 1], 1);
+    const T r = __shfl_down_sync(0xffffffffu, c.c[0], 1);
+    VN<T, NC> o;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const T left = q == 0 ? l : c.c[q - 1], right = q == NC - 1 ? r : c.c[q + 1];
+        o.c[q] = (((left + right) + (ym.c[q] + yp.c[q])) + (zm.c[q] + zp.c[q])) - T(6) * c.c[q];
+    }
     return o;
 }
 
 template <typename T> struct I3 {
+    static constexpr int NC = I3Cfg<T>::NC;
     static constexpr int NW = kBY3 + 4;
-    static constexpr int ROW = 128;
+    static constexpr int ROW = 32 * NC;         // box width (lane 0 and lane 31 hold the x halo)
+    static constexpr int STRIP = 30 * NC;       // output columns per CTA
     static constexpr uint32_t FIELD = NW * ROW * sizeof(T);
     static constexpr uint32_t STAGE = 2 * FIELD;
     static constexpr uint32_t DPLANE = 2 * (kBY3 + 2) * ROW * sizeof(T);
@@ -52,12 +101,13 @@ template <typename T> struct I3 {
 };
 
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
+__global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
     k_interior3d(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
                  T *__restrict__ Uo, T *__restrict__ Vo, const Interior3DArgs a)
 {
     using C = I3<T>;
-    constexpr int ROW = C::ROW, NW = C::NW, S = kS3, DR = kBY3 + 2;
+    constexpr int NC = C::NC, ROW = C::ROW, NW = C::NW, S = kS3, DR = kBY3 + 2;
+    using VT = VN<T, NC>;
     __shared__ __align__(8) uint64_t bars[S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
@@ -74,8 +124,9 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
     __syncthreads();
 
     const Geom &g = a.g;
-    const int64_t xs0 = a.xr.lo & ~int64_t(3);
-    const int64_t nstrips = (a.xr.hi - xs0) / kStrip3 + 1;
+    // strips start where the box's first column (xs - NC) is a multiple of 4 (TMA alignment)
+    const int64_t xs0 = a.xr.lo - ((a.xr.lo - NC + G) & 3);
+    const int64_t nstrips = (a.xr.hi - xs0) / C::STRIP + 1;
     const int64_t nty = (a.yr.hi - a.yr.lo) / kBY3 + 1;
     const int64_t nz = a.zr.hi - a.zr.lo + 1;
     const int nzs = int((nz + kZSeg3 - 1) / kZSeg3);
@@ -99,9 +150,9 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
         const int64_t zi = zs * kZSeg3;
         const int64_t cnt = (nz - zi) < kZSeg3 ? (nz - zi) : kZSeg3;
         const int64_t s = col / nty, t = col - s * nty;
-        const int64_t xs = xs0 + kStrip3 * s, y0 = a.yr.lo + kBY3 * t, z0 = a.zr.lo + zi;
+        const int64_t xs = xs0 + C::STRIP * s, y0 = a.yr.lo + kBY3 * t, z0 = a.zr.lo + zi;
         const int n_in = int(cnt) + 4;
-        const int32_t tx = int32_t(xs - 4 + G), ty = int32_t(y0 - 2 + G), tz = int32_t(z0 - 2 + G);
+        const int32_t tx = int32_t(xs - NC + G), ty = int32_t(y0 - 2 + G), tz = int32_t(z0 - 2 + G);
 
         if (tid == 0) {
             fence_proxy_async();
@@ -115,13 +166,14 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
             }
         }
 
-        const int64_t x0 = xs - 4 + 4 * lane;
+        const int64_t x0 = xs - NC + NC * lane;
         const int64_t y = y0 - 2 + k;
         const bool out_lane = lane >= 1 && lane <= 30;
-        const bool full_vec = out_lane && x0 >= a.xr.lo && x0 + 3 <= a.xr.hi && x0 >= G && x0 + 3 < g.T[0] - G;
+        const bool full_vec =
+            out_lane && x0 >= a.xr.lo && x0 + NC - 1 <= a.xr.hi && x0 >= G && x0 + NC - 1 < g.T[0] - G;
         const bool d_row = k >= 1 && k <= kBY3 + 2;
         const bool o_row = k >= 2 && k <= kBY3 + 1 && y <= a.yr.hi;
-        V4<T> u[3], v[3], du[3], dv[3];
+        VT u[3], v[3], du[3], dv[3];
         bool ok = true;
         int pfail = n_in;   // first plane whose wait gave up
 
@@ -137,20 +189,20 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
                     } else {
                         const T *sU = reinterpret_cast<const T *>(smem + st * C::STAGE);
                         const T *sV = sU + NW * ROW;
-                        u[PH] = lds4(sU + k * ROW + 4 * lane);
-                        v[PH] = lds4(sV + k * ROW + 4 * lane);
+                        u[PH] = ldsN<T, NC>(sU + k * ROW + NC * lane);
+                        v[PH] = ldsN<T, NC>(sV + k * ROW + NC * lane);
                         const int J1 = (PH + 2) % 3, J2 = (PH + 1) % 3;   // planes p-1, p-2
                         if (p >= 2 && d_row) {
                             const int sp = (use + p - 1) % S;
                             const T *pU = reinterpret_cast<const T *>(smem + sp * C::STAGE);
                             const T *pV = pU + NW * ROW;
-                            du[J1] = diff7(u[J1], lds4(pU + (k - 1) * ROW + 4 * lane), lds4(pU + (k + 1) * ROW + 4 * lane),
-                                           u[J2], u[PH]);
-                            dv[J1] = diff7(v[J1], lds4(pV + (k - 1) * ROW + 4 * lane), lds4(pV + (k + 1) * ROW + 4 * lane),
-                                           v[J2], v[PH]);
+                            du[J1] = diff7(u[J1], ldsN<T, NC>(pU + (k - 1) * ROW + NC * lane),
+                                           ldsN<T, NC>(pU + (k + 1) * ROW + NC * lane), u[J2], u[PH]);
+                            dv[J1] = diff7(v[J1], ldsN<T, NC>(pV + (k - 1) * ROW + NC * lane),
+                                           ldsN<T, NC>(pV + (k + 1) * ROW + NC * lane), v[J2], v[PH]);
                             T *db = dbuf + size_t((p - 1) % 3) * 2 * DR * ROW;
-                            stg4(db + (k - 1) * ROW + 4 * lane, du[J1]);
-                            stg4(db + DR * ROW + (k - 1) * ROW + 4 * lane, dv[J1]);
+                            stN(db + (k - 1) * ROW + NC * lane, du[J1]);
+                            stN(db + DR * ROW + (k - 1) * ROW + NC * lane, dv[J1]);
                         }
                     }
                 }
@@ -168,34 +220,34 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), 1)
                     if (p >= 4 && o_row) {
                         const int J1 = (PH + 2) % 3, J2 = (PH + 1) % 3;
                         const T *db = dbuf + size_t((p - 2) % 3) * 2 * DR * ROW;
-                        const V4<T> d2u = diff7(du[J2], lds4(db + (k - 2) * ROW + 4 * lane), lds4(db + k * ROW + 4 * lane),
-                                                du[PH], du[J1]);
-                        const V4<T> d2v = diff7(dv[J2], lds4(db + DR * ROW + (k - 2) * ROW + 4 * lane),
-                                                lds4(db + DR * ROW + k * ROW + 4 * lane), dv[PH], dv[J1]);
-                        const V4<T> &uc = u[J2], &vc = v[J2], &duc = du[J2], &dvc = dv[J2];
-                        V4<T> uo, vo;
-#define PML_OUT(q)                                                                            \
-    if (!ADJ) {                                                                               \
-        uo.q = uc.q + (a1 * vc.q + (a2 * duc.q + (a3 * dvc.q + a4 * d2u.q)));                \
-        vo.q = vc.q + (b2 * duc.q + (b3 * dvc.q + (b4 * d2u.q + b5 * d2v.q)));               \
-    } else {                                                                                  \
-        uo.q = uc.q + (a2 * duc.q + (a3 * dvc.q + (a4 * d2u.q + a5 * d2v.q)));               \
-        vo.q = vc.q + (b1 * uc.q + (b2 * duc.q + (b3 * dvc.q + b5 * d2v.q)));                \
-    }
-                        PML_OUT(x) PML_OUT(y) PML_OUT(z) PML_OUT(w)
-#undef PML_OUT
+                        const VT d2u = diff7(du[J2], ldsN<T, NC>(db + (k - 2) * ROW + NC * lane),
+                                             ldsN<T, NC>(db + k * ROW + NC * lane), du[PH], du[J1]);
+                        const VT d2v = diff7(dv[J2], ldsN<T, NC>(db + DR * ROW + (k - 2) * ROW + NC * lane),
+                                             ldsN<T, NC>(db + DR * ROW + k * ROW + NC * lane), dv[PH], dv[J1]);
+                        const VT &uc = u[J2], &vc = v[J2], &duc = du[J2], &dvc = dv[J2];
+                        VT uo, vo;
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) {
+                            if (!ADJ) {
+                                uo.c[q] = uc.c[q] + (a1 * vc.c[q] + (a2 * duc.c[q] + (a3 * dvc.c[q] + a4 * d2u.c[q])));
+                                vo.c[q] = vc.c[q] + (b2 * duc.c[q] + (b3 * dvc.c[q] + (b4 * d2u.c[q] + b5 * d2v.c[q])));
+                            } else {
+                                uo.c[q] = uc.c[q] + (a2 * duc.c[q] + (a3 * dvc.c[q] + (a4 * d2u.c[q] + a5 * d2v.c[q])));
+                                vo.c[q] = vc.c[q] + (b1 * uc.c[q] + (b2 * duc.c[q] + (b3 * dvc.c[q] + b5 * d2v.c[q])));
+                            }
+                        }
                         const int64_t z = z0 + p - 4;
                         if (full_vec && y >= G && y < g.T[1] - G && z >= G && z < g.T[2] - G) {
                             const int64_t off = g.origin + z * g.PS + y * g.P + x0;
-                            stg4(Uo + off, uo);
-                            stg4(Vo + off, vo);
+                            stN(Uo + off, uo);
+                            stN(Vo + off, vo);
                         } else if (out_lane) {
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
+                            for (int q = 0; q < NC; ++q) {
                                 const int64_t x = x0 + q;
                                 if (x >= a.xr.lo && x <= a.xr.hi) {
-                                    store_wrapped(Uo, g, x, y, z, get4(uo, q));
-                                    store_wrapped(Vo, g, x, y, z, get4(vo, q));
+                                    store_wrapped(Uo, g, x, y, z, uo.c[q]);
+                                    store_wrapped(Vo, g, x, y, z, vo.c[q]);
                                 }
                             }
                         }
