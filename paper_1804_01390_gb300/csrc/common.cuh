@@ -236,6 +236,18 @@ __device__ __forceinline__ void store_wrapped(T *base, const Geom &g, int64_t x,
             for (int a = 0; a < nx; ++a) base[g.origin + xs[a] + ys[b] * g.P + zs[c] * g.PS] = v;
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start (its CTAs only
+// start once every CTA of this grid has called this), and wait for the previous kernel's
+// grid to complete (so that completion of this grid implies completion of that one).
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void wait_prerequisite_grid()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ bool near_edge(const Geom &g, int64_t x, int64_t y, int64_t z)
 {
     bool e = x < G || x >= g.T[0] - G || y < G || y >= g.T[1] - G;
@@ -334,7 +346,7 @@ struct Interior3DArgs {
     int parity;
 };
 cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
-                              void *Uo, void *Vo, const Interior3DArgs &a, int grid,
+                              void *Uo, void *Vo, const Interior3DArgs &a, int grid, bool overlap_previous,
                               cudaStream_t st);
 int interior3d_box_rows(int prec);
 int interior3d_tile_y();
@@ -351,11 +363,13 @@ struct Layer3DArgs {
     DeviceError *err;
 };
 // 3D layer column tiles (x, y output extent; halo 4 on each side) and z segment length
-constexpr int kLayer3TXf = 28, kLayer3TYf = 8;   // FP32: 36 x 16 region columns
+constexpr int kLayer3TXf = 28, kLayer3TYf = 9;   // FP32: 36 x 17 region columns (20 warps)
 constexpr int kLayer3TXd = 12, kLayer3TYd = 4;   // FP64: 20 x 12 region columns
 constexpr int kLayer3LZ = 64;
 int layer3d_tile_x(int prec);
 int layer3d_tile_y(int prec);
+// The eight class launches follow each other with programmatic dependent launch (their
+// outputs are disjoint), the first one after all earlier work of the stream.
 cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,
                            void *const *out /*[8]*/, const Layer3DArgs &a, cudaStream_t st);
 

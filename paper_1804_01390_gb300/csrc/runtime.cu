@@ -543,17 +543,8 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         if (e != cudaSuccess) return cuda_fail(c, e, "interior 2D kernel");
         if (!range_empty(ir[0]) && !range_empty(ir[1])) ++nl;
     } else {
-        Interior3DArgs a{};
-        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
-        int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
-        a.queue = c->dqueue + (adjoint ? 2 : 0);
-        a.parity = int(nl & 1);
-        if (!range_empty(ir[0]) && !range_empty(ir[1]) && !range_empty(ir[2])) ++nl;
-        long pi = prof_begin(c, 0);
-        e = launch_interior3d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
-                              adjoint ? c->grid_int_adj : c->grid_int, c->st);
-        prof_end(c, pi);
-        if (e != cudaSuccess) return cuda_fail(c, e, "interior 3D kernel");
+        // layer classes first (chained), then the interior kernel overlapping them; all
+        // read only the step's input and write disjoint outputs
         Layer3DArgs l{};
         l.g = c->g; l.k = layer_const(c);
         for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
@@ -561,10 +552,21 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
         for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
         l.err = c->derr;
-        pi = prof_begin(c, 1);
+        long pi = prof_begin(c, 1);
         e = launch_layer3d(c->prec, adjoint, tl, out, l, c->st);
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "layer 3D kernel");
+        Interior3DArgs a{};
+        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
+        int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
+        a.queue = c->dqueue + (adjoint ? 2 : 0);
+        a.parity = int(nl & 1);
+        if (!range_empty(ir[0]) && !range_empty(ir[1]) && !range_empty(ir[2])) ++nl;
+        pi = prof_begin(c, 0);
+        e = launch_interior3d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
+                              adjoint ? c->grid_int_adj : c->grid_int, l.ntiles > 0 && !c->prof_on, c->st);
+        prof_end(c, pi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "interior 3D kernel");
     }
     return PML_OK;
 }

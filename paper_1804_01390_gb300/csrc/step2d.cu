@@ -837,10 +837,6 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 //     follows the next layer kernel, which waits for this one to finish).
 // ------------------------------------------------------------------------------------
 
-__device__ __forceinline__ void allow_dependent_launch()
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Each warp takes items from a work queue (atomic counter) until the list is done; tiles
 // are sorted by class, so warps run the same class at the same time.

@@ -264,6 +264,8 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
         }
         use += n_in;
     }
+    // When this launch overlapped the layer kernels, finish only after them.
+    wait_prerequisite_grid();
 }
 
 template <typename T, bool ADJ> static cudaError_t prep_interior3d()
@@ -292,22 +294,43 @@ int interior3d_max_blocks_per_sm(int prec, bool adjoint)
     return adjoint ? occ_interior3d<double, true>() : occ_interior3d<double, false>();
 }
 
+// Launch with programmatic stream serialization when overlap_previous: the kernel may
+// start while the previous kernel of the stream (the layer kernels, whose outputs are
+// disjoint from its own) still runs, and finishes after it.
+template <typename K, typename... Args>
+static cudaError_t launch_pdl(K kernel, int grid, int threads, size_t smem, cudaStream_t st, bool overlap_previous,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap_previous ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
-                              void *Uo, void *Vo, const Interior3DArgs &a, int grid, cudaStream_t st)
+                              void *Uo, void *Vo, const Interior3DArgs &a, int grid, bool overlap_previous,
+                              cudaStream_t st)
 {
     if (a.xr.lo > a.xr.hi || a.yr.lo > a.yr.hi || a.zr.lo > a.zr.hi || grid <= 0) return cudaSuccess;
     cudaError_t e;
     const int threads = 32 * (kBY3 + 4);
 #define PML_LAUNCH(TT, AA)                                                                              \
     if ((e = prep_interior3d<TT, AA>()) != cudaSuccess) return e;                                       \
-    k_interior3d<TT, AA><<<grid, threads, I3<TT>::SMEM, st>>>(*tmU, *tmV, (TT *)Uo, (TT *)Vo, a);
+    return launch_pdl(k_interior3d<TT, AA>, grid, threads, I3<TT>::SMEM, st, overlap_previous, *tmU, *tmV, \
+                      (TT *)Uo, (TT *)Vo, a);
     if (prec == 32) {
         if (adjoint) { PML_LAUNCH(float, true) } else { PML_LAUNCH(float, false) }
     } else {
         if (adjoint) { PML_LAUNCH(double, true) } else { PML_LAUNCH(double, false) }
     }
 #undef PML_LAUNCH
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------
@@ -318,8 +341,12 @@ template <typename T> struct L3 {
     // region (x, y) = tile + halo 4 on each side; one thread per region column
     static constexpr int RX = sizeof(T) == 4 ? kLayer3TXf + 8 : kLayer3TXd + 8;
     static constexpr int RY = sizeof(T) == 4 ? kLayer3TYf + 8 : kLayer3TYd + 8;
-    static constexpr int PL = RX * RY;
-    static constexpr int S = 6;   // resident planes p-4..p plus one in flight
+    static constexpr int PL = RX * RY;                 // threads; elements of one TMA box
+    static constexpr int PLS = (PL + 31) / 32 * 32;    // shared-memory stride of one field plane
+                                                       // (TMA destinations must be 128-byte aligned)
+    // plane ring: resident planes p-4..p plus one in flight; the 8-field FP32 class keeps
+    // none in flight so that its shared memory fits
+    static constexpr int stages(int nf) { return sizeof(T) == 4 && nf == 8 ? 5 : 6; }
 };
 
 template <int MASK> struct Fields {
@@ -405,13 +432,13 @@ __device__ __forceinline__ void issue_plane3(T *stage_base, const Maps8 &maps, c
                                              const Geom &g, uint64_t *bar)
 {
     using F = Fields<MASK>;
-    constexpr int PL = L3<T>::PL;
+    constexpr int PL = L3<T>::PL, PLS = L3<T>::PLS;
     int64_t z = zin;
     z += z < 0 ? g.T[2] : (z >= g.T[2] ? -g.T[2] : 0);
     mbar_arrive_expect_tx(bar, uint32_t(F::NF * PL * sizeof(T)));
 #pragma unroll
     for (int f = 0; f < F::NF; ++f)
-        tma_load_3d(stage_base + f * PL, &maps.m[F::gid(f)], tile.x0 - 4 + G, tile.y0 - 4 + G, int32_t(z + G), bar);
+        tma_load_3d(stage_base + f * PLS, &maps.m[F::gid(f)], tile.x0 - 4 + G, tile.y0 - 4 + G, int32_t(z + G), bar);
 }
 
 template <typename T, bool ADJ, int MASK>
@@ -419,13 +446,14 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
     k_layer3d(const __grid_constant__ Maps8 maps, const Out8 out, const Layer3DArgs a, int tile_base)
 {
     using F = Fields<MASK>;
-    constexpr int NF = F::NF, RX = L3<T>::RX, RY = L3<T>::RY, PL = L3<T>::PL, S = L3<T>::S;
+    constexpr int NF = F::NF, RX = L3<T>::RX, RY = L3<T>::RY, PL = L3<T>::PL, PLS = L3<T>::PLS, S = L3<T>::stages(F::NF);
     extern __shared__ unsigned char smem_dyn[];
     T *stage = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
-    T *Zb = stage + S * NF * PL;   // [3 levels][2 slots][NF][PL]
-    __shared__ T sx[RX + 1], sy[RY + 1];
+    T *Zb = stage + S * NF * PLS;   // [3 levels][2 slots][NF][PLS]
+    __shared__ T sx[RX + 1], sy[RY + 1], sz[kLayer3LZ + 9];
     __shared__ __align__(8) uint64_t bars[S];
 
+    allow_dependent_launch();
     const LayerTile tile = a.tiles[tile_base + blockIdx.x];
     const Geom &g = a.g;
     const int tid = threadIdx.x, cx = tid % RX, cy = tid / RX;
@@ -437,7 +465,7 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
         const int npro = nin < S ? nin : S;
-        for (int p = 0; p < npro; ++p) issue_plane3<T, MASK>(stage + p * NF * PL, maps, tile, zin0 + p, g, &bars[p]);
+        for (int p = 0; p < npro; ++p) issue_plane3<T, MASK>(stage + p * NF * PLS, maps, tile, zin0 + p, g, &bars[p]);
     }
     const T *sgx = static_cast<const T *>(a.sig[0]);
     const T *sgy = static_cast<const T *>(a.sig[1]);
@@ -452,6 +480,11 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
         if (i < 0) i += g.T[1];
         sy[k] = sgy[i];
     }
+    for (int k = tid; k <= nin; k += PL) {   // sz[k] = sigma_z[zin0 - 1 + k]
+        int64_t i = (zin0 - 1 + k) % g.T[2];
+        if (i < 0) i += g.T[2];
+        sz[k] = sgz[i];
+    }
     __syncthreads();
 
     const LayerConstT<T> &lk = lconst_of<T>(a.k);
@@ -463,11 +496,10 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
     sg.si[1] = sy[cy + 1];
     sg.sm[1] = sy[cy];
     const int T2 = int(g.T[2]);
-    auto zsig = [&](int64_t zl, Sig3<T> &s) {   // planes of a work item lie within [-4, 2 T2)
-        int z = int(zl);
-        z += z < 0 ? T2 : (z >= T2 ? -T2 : 0);
-        s.si[2] = sgz[z];
-        s.sm[2] = sgz[z == 0 ? T2 - 1 : z - 1];
+    auto zsig = [&](int64_t zl, Sig3<T> &s) {   // plane zl = zin0 + q of the work item
+        const int q = int(zl - zin0);
+        s.si[2] = sz[q + 1];
+        s.sm[2] = sz[q];
     };
     const bool v4 = cx >= 1 && cx <= RX - 2 && cy >= 1 && cy <= RY - 2;
     const bool v3 = cx >= 2 && cx <= RX - 3 && cy >= 2 && cy <= RY - 3;
@@ -488,10 +520,10 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                     // level 4 at plane q = p-1 from the input planes in the stage ring
                     if (p >= 2 && v4) {
                         const int q = p - 1;
-                        const T *Pc = stage + (q % S) * NF * PL, *Pm = stage + ((q - 1) % S) * NF * PL,
-                                *Pp = stage + (p % S) * NF * PL;
+                        const T *Pc = stage + (q % S) * NF * PLS, *Pm = stage + ((q - 1) % S) * NF * PLS,
+                                *Pp = stage + (p % S) * NF * PLS;
                         auto N = [&](int f, int d) -> T {
-                            const int o = f * PL + tid;
+                            const int o = f * PLS + tid;
                             switch (d) {
                             case 0: return Pc[o];
                             case 1: return Pc[o - 1];
@@ -505,25 +537,25 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         zsig(zin0 + q, sg);
                         T r[NF];
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-                        T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PL;
+                        T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PLS;
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Pc[f * PL + tid] + c4 * r[f];
+                            const T val = Pc[f * PLS + tid] + c4 * r[f];
                             z4r[(PH + 2) % 3][f] = val;
-                            zb[f * PL + tid] = val;
+                            zb[f * PLS + tid] = val;
                         }
                     }
                     // level 3 at plane q = p-2 (z neighbours: own ring; x/y: level-4 plane)
                     if (p >= 4 && v3) {
                         const int q = p - 2;
-                        const T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PL;
+                        const T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PLS;
                         auto N = [&](int f, int d) -> T {
                             switch (d) {
                             case 0: return z4r[(PH + 1) % 3][f];
-                            case 1: return zb[f * PL + tid - 1];
-                            case 2: return zb[f * PL + tid + 1];
-                            case 3: return zb[f * PL + tid - RX];
-                            case 4: return zb[f * PL + tid + RX];
+                            case 1: return zb[f * PLS + tid - 1];
+                            case 2: return zb[f * PLS + tid + 1];
+                            case 3: return zb[f * PLS + tid - RX];
+                            case 4: return zb[f * PLS + tid + RX];
                             case 5: return z4r[PH][f];
                             default: return z4r[(PH + 2) % 3][f];
                             }
@@ -531,26 +563,26 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         zsig(zin0 + q, sg);
                         T r[NF];
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-                        const T *Y = stage + (q % S) * NF * PL;
-                        T *zo = Zb + ((1 * 2 + (q & 1)) * NF) * PL;
+                        const T *Y = stage + (q % S) * NF * PLS;
+                        T *zo = Zb + ((1 * 2 + (q & 1)) * NF) * PLS;
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Y[f * PL + tid] + c3 * r[f];
+                            const T val = Y[f * PLS + tid] + c3 * r[f];
                             z3r[(PH + 1) % 3][f] = val;
-                            zo[f * PL + tid] = val;
+                            zo[f * PLS + tid] = val;
                         }
                     }
                     // level 2 at plane q = p-3
                     if (p >= 6 && v2) {
                         const int q = p - 3;
-                        const T *zb = Zb + ((1 * 2 + (q & 1)) * NF) * PL;
+                        const T *zb = Zb + ((1 * 2 + (q & 1)) * NF) * PLS;
                         auto N = [&](int f, int d) -> T {
                             switch (d) {
                             case 0: return z3r[PH][f];
-                            case 1: return zb[f * PL + tid - 1];
-                            case 2: return zb[f * PL + tid + 1];
-                            case 3: return zb[f * PL + tid - RX];
-                            case 4: return zb[f * PL + tid + RX];
+                            case 1: return zb[f * PLS + tid - 1];
+                            case 2: return zb[f * PLS + tid + 1];
+                            case 3: return zb[f * PLS + tid - RX];
+                            case 4: return zb[f * PLS + tid + RX];
                             case 5: return z3r[(PH + 2) % 3][f];
                             default: return z3r[(PH + 1) % 3][f];
                             }
@@ -558,26 +590,26 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         zsig(zin0 + q, sg);
                         T r[NF];
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-                        const T *Y = stage + (q % S) * NF * PL;
-                        T *zo = Zb + ((2 * 2 + (q & 1)) * NF) * PL;
+                        const T *Y = stage + (q % S) * NF * PLS;
+                        T *zo = Zb + ((2 * 2 + (q & 1)) * NF) * PLS;
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Y[f * PL + tid] + c2 * r[f];
+                            const T val = Y[f * PLS + tid] + c2 * r[f];
                             z2r[PH][f] = val;
-                            zo[f * PL + tid] = val;
+                            zo[f * PLS + tid] = val;
                         }
                     }
                     // level 1 (output) at plane q = p-4
                     if (p >= 8 && in_rect) {
                         const int q = p - 4;
-                        const T *zb = Zb + ((2 * 2 + (q & 1)) * NF) * PL;
+                        const T *zb = Zb + ((2 * 2 + (q & 1)) * NF) * PLS;
                         auto N = [&](int f, int d) -> T {
                             switch (d) {
                             case 0: return z2r[(PH + 2) % 3][f];
-                            case 1: return zb[f * PL + tid - 1];
-                            case 2: return zb[f * PL + tid + 1];
-                            case 3: return zb[f * PL + tid - RX];
-                            case 4: return zb[f * PL + tid + RX];
+                            case 1: return zb[f * PLS + tid - 1];
+                            case 2: return zb[f * PLS + tid + 1];
+                            case 3: return zb[f * PLS + tid - RX];
+                            case 4: return zb[f * PLS + tid + RX];
                             case 5: return z2r[(PH + 1) % 3][f];
                             default: return z2r[PH][f];
                             }
@@ -586,13 +618,13 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         zsig(zl, sg);
                         T r[NF];
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
-                        const T *Y = stage + (q % S) * NF * PL;
+                        const T *Y = stage + (q % S) * NF * PLS;
                         int64_t z = zl;
                         z += z < 0 ? T2 : (z >= T2 ? -T2 : 0);
                         const bool edge = near_edge(g, gx, gy, z);
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Y[f * PL + tid] + c1 * r[f];
+                            const T val = Y[f * PLS + tid] + c1 * r[f];
                             T *dst = static_cast<T *>(out.p[F::gid(f)]);
                             if (edge) store_wrapped(dst, g, gx, gy, z, val);
                             else dst[g.origin + gx + gy * g.P + z * g.PS] = val;
@@ -608,22 +640,26 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
             if (p < nin && tid == 0 && p >= 4 && p - 4 + S < nin) {
                 fence_proxy_async();
                 const int st = (p - 4) % S;
-                issue_plane3<T, MASK>(stage + st * NF * PL, maps, tile, zin0 + p - 4 + S, g, &bars[st]);
+                issue_plane3<T, MASK>(stage + st * NF * PLS, maps, tile, zin0 + p - 4 + S, g, &bars[st]);
             }
         }
     }
     if (!ok && tid == 0)   // let the copies in flight (planes pfail .. pfail + S - 5 at most) land
         for (int q = pfail; q < nin && q < pfail + S; ++q)
             mbar_wait(&bars[q % S], (q / S) & 1, nullptr, 0, kDrainLimitNs);
+    // a class launched to overlap the previous one finishes only after it
+    wait_prerequisite_grid();
 }
 
 template <typename T, int MASK> static size_t layer3d_smem()
 {
-    return (size_t(L3<T>::S) + 6) * Fields<MASK>::NF * L3<T>::PL * sizeof(T) + 128;
+    return (size_t(L3<T>::stages(Fields<MASK>::NF)) + 6) * Fields<MASK>::NF * L3<T>::PLS * sizeof(T) + 128;
 }
 
+// One class's launch; `first` marks the first class launch of the step (fully ordered
+// after earlier work), later ones overlap their predecessor.
 template <typename T, bool ADJ, int MASK>
-static cudaError_t launch_l3(const Maps8 &m, const Out8 &o, const Layer3DArgs &a, cudaStream_t st)
+static cudaError_t launch_l3(const Maps8 &m, const Out8 &o, const Layer3DArgs &a, cudaStream_t st, bool &first)
 {
     const int n = a.class_off[MASK + 1] - a.class_off[MASK];
     if (n <= 0) return cudaSuccess;
@@ -634,22 +670,26 @@ static cudaError_t launch_l3(const Maps8 &m, const Out8 &o, const Layer3DArgs &a
         if (e != cudaSuccess) return e;
         done = true;
     }
-    k_layer3d<T, ADJ, MASK><<<n, L3<T>::PL, sm, st>>>(m, o, a, a.class_off[MASK]);
-    return cudaGetLastError();
+    const bool overlap = !first;
+    first = false;
+    return launch_pdl(k_layer3d<T, ADJ, MASK>, n, L3<T>::PL, sm, st, overlap, m, o, a, a.class_off[MASK]);
 }
 
+// Classes with the most fields per tile (the longest tiles) first, so that the short
+// face tiles fill the tail.
 template <typename T, bool ADJ>
 static cudaError_t launch_l3_all(const Maps8 &m, const Out8 &o, const Layer3DArgs &a, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = launch_l3<T, ADJ, 0>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l3<T, ADJ, 1>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l3<T, ADJ, 2>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l3<T, ADJ, 3>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l3<T, ADJ, 4>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l3<T, ADJ, 5>(m, o, a, st)) != cudaSuccess) return e;
-    if ((e = launch_l3<T, ADJ, 6>(m, o, a, st)) != cudaSuccess) return e;
-    return launch_l3<T, ADJ, 7>(m, o, a, st);
+    bool first = true;
+    if ((e = launch_l3<T, ADJ, 7>(m, o, a, st, first)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 6>(m, o, a, st, first)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 5>(m, o, a, st, first)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 3>(m, o, a, st, first)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 4>(m, o, a, st, first)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 2>(m, o, a, st, first)) != cudaSuccess) return e;
+    if ((e = launch_l3<T, ADJ, 1>(m, o, a, st, first)) != cudaSuccess) return e;
+    return launch_l3<T, ADJ, 0>(m, o, a, st, first);
 }
 
 int layer3d_tile_x(int prec) { return prec == 32 ? kLayer3TXf : kLayer3TXd; }
