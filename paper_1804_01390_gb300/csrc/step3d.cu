@@ -81,10 +81,20 @@ __device__ __forceinline__ VN<T, NC> diff7(const VN<T, NC> &c, const VN<T, NC> &
     const T l = __shfl_up_sync(0xffffffffu, c.c[NC - 1], 1);
     const T r = __shfl_down_sync(0xffffffffu, c.c[0], 1);
     VN<T, NC> o;
+    if constexpr (sizeof(T) == 4 && NC == 2) {   // packed FP32x2: one instruction per pair
+        const float2 cc = make_float2(c.c[0], c.c[1]);
+        float2 t = __fadd2_rn(make_float2(l, c.c[0]), make_float2(c.c[1], r));
+        t = __fadd2_rn(t, __fadd2_rn(make_float2(ym.c[0], ym.c[1]), make_float2(yp.c[0], yp.c[1])));
+        t = __fadd2_rn(t, __fadd2_rn(make_float2(zm.c[0], zm.c[1]), make_float2(zp.c[0], zp.c[1])));
+        t = __ffma2_rn(make_float2(-6.f, -6.f), cc, t);
+        o.c[0] = t.x;
+        o.c[1] = t.y;
+    } else {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        const T left = q == 0 ? l : c.c[q - 1], right = q == NC - 1 ? r : c.c[q + 1];
-        o.c[q] = (((left + right) + (ym.c[q] + yp.c[q])) + (zm.c[q] + zp.c[q])) - T(6) * c.c[q];
+        for (int q = 0; q < NC; ++q) {
+            const T left = q == 0 ? l : c.c[q - 1], right = q == NC - 1 ? r : c.c[q + 1];
+            o.c[q] = (((left + right) + (ym.c[q] + yp.c[q])) + (zm.c[q] + zp.c[q])) - T(6) * c.c[q];
+        }
     }
     return o;
 }
@@ -226,6 +236,22 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
                                              ldsN<T, NC>(db + DR * ROW + k * ROW + NC * lane), dv[PH], dv[J1]);
                         const VT &uc = u[J2], &vc = v[J2], &duc = du[J2], &dvc = dv[J2];
                         VT uo, vo;
+                        if constexpr (sizeof(T) == 4 && NC == 2) {   // packed FP32x2
+                            auto P = [](const VT &x) { return make_float2(x.c[0], x.c[1]); };
+                            auto B = [](T x) { return make_float2(x, x); };
+                            float2 tu, tv;
+                            if (!ADJ) {
+                                tu = __ffma2_rn(B(a1), P(vc), __ffma2_rn(B(a2), P(duc), __ffma2_rn(B(a3), P(dvc), __fmul2_rn(B(a4), P(d2u)))));
+                                tv = __ffma2_rn(B(b2), P(duc), __ffma2_rn(B(b3), P(dvc), __ffma2_rn(B(b4), P(d2u), __fmul2_rn(B(b5), P(d2v)))));
+                            } else {
+                                tu = __ffma2_rn(B(a2), P(duc), __ffma2_rn(B(a3), P(dvc), __ffma2_rn(B(a4), P(d2u), __fmul2_rn(B(a5), P(d2v)))));
+                                tv = __ffma2_rn(B(b1), P(uc), __ffma2_rn(B(b2), P(duc), __ffma2_rn(B(b3), P(dvc), __fmul2_rn(B(b5), P(d2v)))));
+                            }
+                            tu = __fadd2_rn(P(uc), tu);
+                            tv = __fadd2_rn(P(vc), tv);
+                            uo.c[0] = tu.x; uo.c[1] = tu.y;
+                            vo.c[0] = tv.x; vo.c[1] = tv.y;
+                        } else
 #pragma unroll
                         for (int q = 0; q < NC; ++q) {
                             if (!ADJ) {
