@@ -357,6 +357,31 @@ def run_ours(args, ws, rank, local):
         del solvers, inits4, b4
         torch.cuda.synchronize()
 
+    # ---- the paper's stress workload: random sigma per edge, white noise in a disk -------
+    stress = None
+    if not args.no_stress:
+        Ns, ws_w = 4096, 20
+        Ts = Ns + 2 * ws_w
+        rng_s = np.random.default_rng(91)
+        e_s = np.arange(Ts)
+        layer_s = (e_s <= ws_w - 2) | (e_s >= ws_w + Ns)
+        sig_s = [np.where(layer_s, 2.0 * rng_s.random(Ts), 0.0) for _ in range(2)]
+        s = PMLSolver((Ns, Ns), ws_w, sigma="user", user_sigma=sig_s, precision=32, device=dev)
+        from paper_1804_01390_gb300 import _lib
+        _lib.pml_set_variant(s.ctx, variant)
+        u_s = wk.white_noise_disk((Ts, Ts), (Ts / 2.0, Ts / 2.0), 512.0, 0.25, seed=92,
+                                  window=((ws_w, ws_w), (ws_w + Ns - 1, ws_w + Ns - 1)))
+        s.set_initial(torch.from_numpy(u_s.astype(np.float32)).to(dev))
+        Kst = max(K // 4, 50)
+        ms_s, _ = timed_steps(s, Kst, min(W, 3), ws, profile=False)
+        ms_s = max_over_ranks(ms_s, ws, dev)
+        stress = {"workload": "2D %d^2 interior + %d-cell layer, sigma ~ U[0,2/h) per edge (user path), white noise "
+                              "of variance 1/4 in a disk of radius 512, FP32" % (Ns, ws_w),
+                  "value": Ts * Ts * Kst * ws / (ms_s / 1e3) / 1e9, "unit": UNIT, "steps": Kst,
+                  "ms_per_step": ms_s / Kst}
+        s.close()
+        del s
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -378,7 +403,7 @@ def run_ours(args, ws, rank, local):
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
-            "cfg3": d3, "batched": d4,
+            "cfg3": d3, "batched": d4, "stress": stress,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -456,6 +481,7 @@ def main():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--n3", type=int, default=None, help="3D physical side (default 512)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--n4", type=int, default=None, help="largest side of the batched grids (default 2048)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
