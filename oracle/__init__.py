@@ -19,6 +19,9 @@ function names the part of the paper it follows:
 * ``energy``          -- eq:Energy (Sec. 1.1.5).
 * ``rhs_transpose`` / ``adjoint`` -- transpose of A and the reverse of the RK4
                          stage graph (discrete adjoint of the scheme above).
+* ``misfit_grad_sigma`` -- receiver misfit and its gradient with respect to every edge
+                         damping sigma_a[e], from the reverse stage graph and the sigma
+                         entries of eq:DiscretePML.
 """
 from __future__ import annotations
 
@@ -95,6 +98,9 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
         lib.orc_adjoint.restype = cint
         lib.orc_adjoint.argtypes = [cint, P, dbl, P, P, i64, dbl, i64, cint, P, dbl, dbl, P,
                                     cint, P, P]
+        lib.orc_misfit_grad_sigma.restype = cint
+        lib.orc_misfit_grad_sigma.argtypes = [cint, P, dbl, P, P, i64, dbl, i64, cint, P, P, dbl,
+                                              dbl, cint, P, P, P, P]
         _LIBS[openmp] = lib
         return lib
 
@@ -261,3 +267,26 @@ def adjoint(grid: Grid, yb, nsteps, dt, step_end, sources=None, receivers=None, 
     if rc != 0:
         raise MemoryError("oracle scratch allocation failed")
     return yb, gamp
+
+
+def misfit_grad_sigma(grid: Grid, y0, nsteps, dt, receivers, target, sources=None, step0=0):
+    """J = 1/2 sum_m sum_r (U_m(x_r) - target[m-1, r])^2 of the RK4 run from y0 and dJ/dsigma
+    per axis (list of arrays of length T[a]; zero where sigma is zero).  Keeps every
+    forward state: small problems only."""
+    y0 = _f64(y0).reshape(grid.nfields, grid.n)
+    ns, idx, amp, fp, td, _k1, _k2 = _src_args(sources)
+    ridx = _i64(receivers)
+    nr = int(ridx.shape[0])
+    tgt = _f64(target).reshape(int(nsteps), nr)
+    J = ctypes.c_double(0.0)
+    grad = np.zeros(int(sum(grid.T)), dtype=np.float64)
+    rc = _lib().orc_misfit_grad_sigma(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y0),
+                                      int(nsteps), float(dt), int(step0), ns, _ptr(idx), _ptr(amp), fp,
+                                      td, nr, _ptr(ridx), _ptr(tgt), ctypes.byref(J), _ptr(grad))
+    if rc != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    out, off = [], 0
+    for t in grid.T:
+        out.append(grad[off:off + t].copy())
+        off += t
+    return J.value, out

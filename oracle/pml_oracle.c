@@ -467,3 +467,151 @@ int orc_adjoint(int ndim, const int64_t *T, double h, const double *sig, double 
     free(kb1); free(kb2); free(kb3); free(kb4); free(Yb); free(yb_out);
     return 0;
 }
+
+/*
+ * k^T (dA/dsigma_a[e]) Y for one edge e of axis a (sigma_a[e] != 0), with the supports of
+ * Phi/Psi held fixed.  Written out from the sigma entries of eq:DiscretePML:
+ *   dV/dt(i)     has  sigma_a[i_a] Psi_a(i+e_a)/h  and  -sigma_a[i_a-1] Phi_a(i-e_a)/h
+ *   dPhi_a/dt(i) has -sigma_a[i_a-1] Phi_a(i-e_a)/2 and -sigma_a[i_a] Phi_a(i)/2   (if sigma_a[i_a] != 0)
+ *   dPsi_a/dt(i) has -sigma_a[i_a-1] Psi_a(i)/2     and -sigma_a[i_a] Psi_a(i+e_a)/2 (if sigma_a[i_a-1] != 0)
+ * so the vertices with i_a = e (sigma_a[i_a]) and i_a = e+1 (sigma_a[i_a-1]) contribute.
+ */
+static double dA_contract(const orc_grid *g, int a, int64_t e, const double *kb, const double *Y)
+{
+    const int64_t n = grid_n(g), Ta = g->T[a];
+    const double h = g->h;
+    const double *kV = kb + n, *kPhi = kb + (2 + 2 * a) * n, *kPsi = kb + (3 + 2 * a) * n;
+    const double *Phi = Y + (2 + 2 * a) * n, *Psi = Y + (3 + 2 * a) * n;
+    const int psi_at_e = g->sig[a][(e - 1 + Ta) % Ta] != 0.0;   /* Psi row active at i_a = e   */
+    const int phi_at_e1 = g->sig[a][(e + 1) % Ta] != 0.0;       /* Phi row active at i_a = e+1 */
+    double sum = 0.0;
+    int64_t i;
+    for (i = 0; i < n; i++) {
+        int64_t c[3];
+        to_coords(g, i, c);
+        if (c[a] == e) {
+            const int64_t ip = shifted(g, c, a, +1);
+            sum += kV[i] * Psi[ip] / h;
+            sum += -0.5 * kPhi[i] * Phi[i];
+            if (psi_at_e) sum += -0.5 * kPsi[i] * Psi[ip];
+        } else if (c[a] == (e + 1) % Ta) {
+            const int64_t im = shifted(g, c, a, -1);
+            sum += -kV[i] * Phi[im] / h;
+            if (phi_at_e1) sum += -0.5 * kPhi[i] * Phi[im];
+            sum += -0.5 * kPsi[i] * Psi[i];
+        }
+    }
+    return sum;
+}
+
+/*
+ * Misfit J = 1/2 sum_{m=1..nsteps} sum_r (U_m(x_r) - target[(m-1)*nr + r])^2 of the RK4 run
+ * from y0 (steps step0 .. step0+nsteps, sources as in orc_rk4; y0 is not modified) and its
+ * gradient with respect to every edge damping sigma_a[e] (grad laid out like sig; edges
+ * with sigma_a[e] = 0 get 0: the supports of Phi/Psi are held fixed).  Every forward
+ * state is kept (small problems only).  Per step m, backwards: add the residual of step m
+ * to dJ/dU_m, run the reverse of the stage graph (as in orc_adjoint) and add
+ * sum_i kbar_i^T (dA/dsigma) Y_i, with Y_i the stage inputs of the step from y_{m-1}.
+ * Returns 0, or -1 when scratch cannot be allocated.
+ */
+int orc_misfit_grad_sigma(int ndim, const int64_t *T, double h, const double *sig, const double *y0,
+                          int64_t nsteps, double dt, int64_t step0, int src_ns, const int64_t *src_idx,
+                          const double *src_amp, double f_peak, double t_delay, int nr,
+                          const int64_t *rec_idx, const double *target, double *J, double *grad)
+{
+    orc_grid g;
+    orc_src s;
+    int64_t n, len, k, j, m, tot, off;
+    double *states, *k1, *k2, *k3, *Y2, *Y3, *Y4, *kb1, *kb2, *kb3, *kb4, *Yb, *yb, *yb_out, *res;
+    int a, r;
+    grid_from_args(&g, ndim, T, h, sig);
+    s.ns = src_ns; s.idx = src_idx; s.amp = src_amp; s.f_peak = f_peak; s.t_delay = t_delay;
+    n = grid_n(&g);
+    len = (2 + 2 * (int64_t)ndim) * n;
+    states = (double *)malloc(sizeof(double) * (size_t)(len * (nsteps + 1)));
+    res = (double *)malloc(sizeof(double) * (size_t)(nsteps * (nr > 0 ? nr : 1)));
+    k1 = (double *)malloc(sizeof(double) * (size_t)len);
+    k2 = (double *)malloc(sizeof(double) * (size_t)len);
+    k3 = (double *)malloc(sizeof(double) * (size_t)len);
+    Y2 = (double *)malloc(sizeof(double) * (size_t)len);
+    Y3 = (double *)malloc(sizeof(double) * (size_t)len);
+    Y4 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb1 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb2 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb3 = (double *)malloc(sizeof(double) * (size_t)len);
+    kb4 = (double *)malloc(sizeof(double) * (size_t)len);
+    Yb = (double *)malloc(sizeof(double) * (size_t)len);
+    yb = (double *)malloc(sizeof(double) * (size_t)len);
+    yb_out = (double *)malloc(sizeof(double) * (size_t)len);
+    if (!states || !res || !k1 || !k2 || !k3 || !Y2 || !Y3 || !Y4 || !kb1 || !kb2 || !kb3 || !kb4 || !Yb ||
+        !yb || !yb_out) {
+        free(states); free(res); free(k1); free(k2); free(k3); free(Y2); free(Y3); free(Y4);
+        free(kb1); free(kb2); free(kb3); free(kb4); free(Yb); free(yb); free(yb_out);
+        return -1;
+    }
+    /* forward run, every state kept; residuals of the receivers */
+    memcpy(states, y0, sizeof(double) * (size_t)len);
+    *J = 0.0;
+    for (m = 1; m <= nsteps; m++) {
+        double *y = states + m * len;
+        memcpy(y, states + (m - 1) * len, sizeof(double) * (size_t)len);
+        if (orc_rk4(ndim, T, h, sig, y, 1, dt, step0 + m - 1, src_ns, src_idx, src_amp, f_peak, t_delay, 0,
+                    NULL, NULL) != 0)
+            return -1;
+        for (r = 0; r < nr; r++) {
+            const double d = y[rec_idx[r]] - target[(m - 1) * nr + r];
+            res[(m - 1) * nr + r] = d;
+            *J += 0.5 * d * d;
+        }
+    }
+    tot = 0;
+    for (a = 0; a < ndim; a++) tot += g.T[a];
+    for (j = 0; j < tot; j++) grad[j] = 0.0;
+    for (j = 0; j < len; j++) yb[j] = 0.0;
+    /* backwards */
+    for (m = nsteps; m >= 1; m--) {
+        const double *y = states + (m - 1) * len;
+        const double t = (double)(step0 + m - 1) * dt;
+        const orc_src *sp = src_ns > 0 ? &s : NULL;
+        for (r = 0; r < nr; r++) yb[rec_idx[r]] += res[(m - 1) * nr + r];
+        /* forward stage inputs of the step m-1 -> m */
+        rhs(&g, y, k1, sp, t);
+        for (j = 0; j < len; j++) Y2[j] = y[j] + 0.5 * dt * k1[j];
+        rhs(&g, Y2, k2, sp, t + 0.5 * dt);
+        for (j = 0; j < len; j++) Y3[j] = y[j] + 0.5 * dt * k2[j];
+        rhs(&g, Y3, k3, sp, t + 0.5 * dt);
+        for (j = 0; j < len; j++) Y4[j] = y[j] + dt * k3[j];
+        /* reverse of the stage graph */
+        for (j = 0; j < len; j++) {
+            kb1[j] = dt / 6.0 * yb[j];
+            kb2[j] = dt / 3.0 * yb[j];
+            kb3[j] = dt / 3.0 * yb[j];
+            kb4[j] = dt / 6.0 * yb[j];
+            yb_out[j] = yb[j];
+        }
+        rhs_transpose(&g, kb4, Yb);
+        for (j = 0; j < len; j++) { yb_out[j] += Yb[j]; kb3[j] += dt * Yb[j]; }
+        rhs_transpose(&g, kb3, Yb);
+        for (j = 0; j < len; j++) { yb_out[j] += Yb[j]; kb2[j] += 0.5 * dt * Yb[j]; }
+        rhs_transpose(&g, kb2, Yb);
+        for (j = 0; j < len; j++) { yb_out[j] += Yb[j]; kb1[j] += 0.5 * dt * Yb[j]; }
+        rhs_transpose(&g, kb1, Yb);
+        for (j = 0; j < len; j++) yb_out[j] += Yb[j];
+        /* dJ/dsigma += sum_i kbar_i^T (dA/dsigma) Y_i */
+        off = 0;
+        for (a = 0; a < ndim; a++) {
+            int64_t e;
+            for (e = 0; e < g.T[a]; e++) {
+                if (g.sig[a][e] == 0.0) continue;
+                grad[off + e] += dA_contract(&g, a, e, kb1, y) + dA_contract(&g, a, e, kb2, Y2) +
+                                 dA_contract(&g, a, e, kb3, Y3) + dA_contract(&g, a, e, kb4, Y4);
+            }
+            off += g.T[a];
+        }
+        memcpy(yb, yb_out, sizeof(double) * (size_t)len);
+    }
+    free(states); free(res); free(k1); free(k2); free(k3); free(Y2); free(Y3); free(Y4);
+    free(kb1); free(kb2); free(kb3); free(kb4); free(Yb); free(yb); free(yb_out);
+    (void)k;
+    return 0;
+}

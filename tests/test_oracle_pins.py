@@ -572,3 +572,59 @@ def test_adjoint_gradients_vs_central_differences(orc):
         um[v] -= eps
         fd = (J(up, src["amp"])[0] - J(um, src["amp"])[0]) / (2 * eps)
         assert abs(fd - yb_out[0, v]) < 1e-8 * max(abs(fd), 1e-6), (fd, yb_out[0, v])
+
+
+# ----------------------------------------------------------------------------------
+# Gradient of the receiver misfit with respect to the edge damping sigma_a[e] (the
+# supports of Phi/Psi held fixed): central differences of J(sigma), computed by forward
+# runs only, against the reverse-stage-graph gradient.  J is smooth in every sigma_a[e]
+# that stays nonzero, so the difference quotient agrees up to O(eps^2).
+# ----------------------------------------------------------------------------------
+
+def _grad_sigma_case(orc, N, w, steps, seed):
+    rng = np.random.default_rng(seed)
+    sig = [orc.sigma_profile(n, w, orc.KIND_RANDOM, 2.0, draws=rng.random(n + 2 * w)) for n in N]
+    g = orc.Grid(tuple(n + 2 * w for n in N), 1.0, sig)
+    y = g.zeros_state()
+    y[0] = rng.normal(size=g.n)
+    y[1] = 0.3 * rng.normal(size=g.n)
+    rec = [g.flat(tuple(w + int(rng.integers(0, n)) for n in N)) for _ in range(3)]
+    src = {"idx": [g.flat(tuple(w + n // 2 for n in N))], "amp": [0.7], "f_peak": 0.1, "t_delay": 10.0}
+    tgt = 0.1 * rng.normal(size=(steps, len(rec)))
+    return g, sig, y, rec, src, tgt
+
+
+@pytest.mark.parametrize("N,w,steps", [((10, 9), 3, 25), ((5, 4, 6), 2, 12)])
+def test_grad_sigma_matches_central_differences(orc, N, w, steps):
+    g, sig, y, rec, src, tgt = _grad_sigma_case(orc, N, w, steps, seed=sum(N) + w)
+    J, grad = orc.misfit_grad_sigma(g, y, steps, 0.5, rec, tgt, sources=src)
+    assert J > 0
+
+    def J_of(sigs):
+        return orc.misfit_grad_sigma(orc.Grid(g.T, 1.0, sigs), y, steps, 0.5, rec, tgt, sources=src)[0]
+
+    eps = 1e-5
+    checked = 0
+    for a in range(len(N)):
+        T = g.T[a]
+        for e in (0, 1, w - 2, T - 1, T - 2, T - w):
+            e %= T
+            if sig[a][e] == 0.0:
+                assert grad[a][e] == 0.0
+                continue
+            sp = [s.copy() for s in sig]
+            sm = [s.copy() for s in sig]
+            sp[a][e] += eps
+            sm[a][e] -= eps
+            fd = (J_of(sp) - J_of(sm)) / (2 * eps)
+            assert abs(grad[a][e] - fd) <= 1e-6 * max(abs(fd), 1e-3), (a, e, grad[a][e], fd)
+            checked += 1
+    assert checked >= 4
+
+
+def test_grad_sigma_zero_on_physical_edges(orc):
+    g, sig, y, rec, src, tgt = _grad_sigma_case(orc, (10, 9), 3, 10, seed=3)
+    _, grad = orc.misfit_grad_sigma(g, y, 10, 0.5, rec, tgt, sources=src)
+    for a in range(2):
+        assert np.all(grad[a][sig[a] == 0.0] == 0.0)
+        assert np.any(grad[a] != 0.0)
