@@ -205,6 +205,34 @@ pml_status pml_query_sigma(const pml_ctx *ctx, int axis, double *sigma);
 pml_status pml_adjoint_reset(pml_ctx *ctx);
 pml_status pml_adjoint_step(pml_ctx *ctx, int64_t n, const void *residual, void *grad_u,
                             double *grad_amp);
+/*
+ * Gradient of the receiver misfit with respect to the damping profile (not in the paper:
+ * the derivative of eq:DiscretePML's sigma entries carried through the discrete adjoint
+ * of the RK4 step).  Requires PML_FLAG_ADJOINT.
+ *
+ * From the current forward state (step s0) the call runs n RK4 steps, recording the
+ * receiver traces as pml_step does (the receiver buffer needs n free rows), and forms
+ *   J = 1/2 sum_{m=1..n} sum_r (U_{s0+m}(x_r) - target[(m-1) nr + r])^2
+ * (target: device array [n][nr] of the context precision).  Alternatively `residual`
+ * (same layout) gives dJ/dU_{s0+m}(x_r) directly, for any misfit of the traces; then
+ * *misfit is set to 0.  With receivers exactly one of the two must be given; without
+ * receivers both are ignored and the gradient is 0.
+ * It then runs the adjoint backwards and accumulates, per step, sum over the four RK4
+ * stages of kbar_i^T (dA/dsigma) Y_i, with Y_i the stage inputs of the forward step and
+ * kbar_i the stage cotangents, in FP64.  Forward states are recomputed from checkpoints
+ * taken every `interval` steps (0: ceil(sqrt(n))), so the call holds about
+ * n/interval + interval + 7 states in device memory (cudaMalloc for its duration).
+ *
+ * Outputs: grad_sigma (host FP64, T[0] + T[1] (+ T[2]) values, axis by axis, indexed by
+ * edge): dJ/dsigma_a[e] with the supports of Phi/Psi held fixed; edges with sigma = 0
+ * report 0.  *misfit = J.  grad_amp (optional, host FP64 [ns]): dJ/da_s.  Afterwards the
+ * forward state is the one after step s0 + n (as after pml_step(n)) and the adjoint
+ * state holds dJ/dy at step s0 (pml_adjoint_read_field(PML_FIELD_U) gives dJ/dU_{s0}).
+ * Synchronising.
+ */
+pml_status pml_sigma_gradient(pml_ctx *ctx, int64_t n, const void *target, const void *residual,
+                              int64_t interval, double *grad_sigma, double *misfit, double *grad_amp);
+
 /* Copy field PML_FIELD_* of the adjoint state into a dense T-grid (host or device). */
 pml_status pml_adjoint_read_field(pml_ctx *ctx, int field, void *dst, int on_device);
 

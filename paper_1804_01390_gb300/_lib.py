@@ -46,7 +46,7 @@ EXPORTED = (
     "pml_workspace_bytes", "pml_create", "pml_set_initial", "pml_set_sources",
     "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
-    "pml_adjoint_read_field", "pml_state_bytes", "pml_save_state", "pml_load_state",
+    "pml_adjoint_read_field", "pml_sigma_gradient", "pml_state_bytes", "pml_save_state", "pml_load_state",
     "pml_get_variant", "pml_set_variant", "pml_autotune",
     "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
     "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
@@ -105,6 +105,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_adjoint_reset": [P],
         "pml_adjoint_step": [P, i64, P, P, P],
         "pml_adjoint_read_field": [P, ctypes.c_int, P, ctypes.c_int],
+        "pml_sigma_gradient": [P, i64, P, P, i64, P, P, P],
         "pml_state_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
         "pml_save_state": [P, P, ctypes.c_int],
         "pml_load_state": [P, P, ctypes.c_int],
@@ -224,6 +225,15 @@ def pml_adjoint_step(ctx, n, residual, grad_u, grad_amp):
 
 def pml_adjoint_read_field(ctx, field, dst, on_device):
     _check(load().pml_adjoint_read_field(ctx, int(field), dst, int(on_device)), ctx)
+
+
+def pml_sigma_gradient(ctx, n, target, residual, interval, grad_sigma, grad_amp=None):
+    """Runs n forward steps and the adjoint; fills grad_sigma (numpy float64, sum of T[a])
+    and grad_amp (numpy float64 [ns] or None); returns the misfit J (0 with a residual)."""
+    J = ctypes.c_double(0.0)
+    _check(load().pml_sigma_gradient(ctx, int(n), target, residual, int(interval), grad_sigma.ctypes.data,
+                                     ctypes.byref(J), None if grad_amp is None else grad_amp.ctypes.data), ctx)
+    return float(J.value)
 
 
 def pml_state_bytes(ctx) -> int:

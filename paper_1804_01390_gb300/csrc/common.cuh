@@ -373,6 +373,20 @@ int layer3d_tile_y(int prec);
 cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,
                            void *const *out /*[8]*/, const Layer3DArgs &a, cudaStream_t st);
 
+// Damping gradient (grad_sigma.cu): explicit operator applications over the whole box,
+// stage combinations and the per-edge contraction kbar^T (dA/dsigma_a[e]) Y.
+struct SigmaPtrs {
+    const void *p[3];          // device sigma per axis (context precision)
+};
+cudaError_t launch_apply_op(int prec, bool adjoint, void *const *in, void *const *out, int nf, const Geom &g,
+                            const SigmaPtrs &s, double h, cudaStream_t st);
+cudaError_t launch_axpby(int prec, void *const *x, void *const *y, void *const *out, double alpha, double beta,
+                         int nf, int64_t elems, cudaStream_t st);
+cudaError_t launch_contract(int prec, void *const *kb, void *const *Y, int nf, const Geom &g, const SigmaPtrs &s,
+                            double h, double *acc, cudaStream_t st);
+cudaError_t launch_residual(int prec, const void *trace, const void *target, void *res, int64_t count,
+                            double *misfit, cudaStream_t st);
+
 // Sources and receivers after a forward step; receiver injection and source-amplitude
 // gradients before an adjoint step.
 struct PointArgs {

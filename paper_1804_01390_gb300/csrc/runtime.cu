@@ -1076,6 +1076,141 @@ pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *g
     return PML_OK;
 }
 
+pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const void *residual, int64_t interval,
+                              double *grad_sigma, double *misfit, double *grad_amp)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (!(c->flags & PML_FLAG_ADJOINT)) return fail(c, PML_ESTATE, "context was created without PML_FLAG_ADJOINT");
+    if (n < 1) return fail(c, PML_EINVAL, "n must be >= 1");
+    if (!grad_sigma || !misfit) return fail(c, PML_EINVAL, "grad_sigma and misfit are required");
+    if (c->nr > 0 && !target == !residual)
+        return fail(c, PML_EINVAL, "give exactly one of target and residual when receivers are set");
+    if (c->nr > 0 && c->trace_cap - c->trace_k < n)
+        return fail(c, PML_EINVAL, "the receiver buffer has %lld free rows, %lld needed",
+                    (long long)(c->trace_cap - c->trace_k), (long long)n);
+    const int nf = c->nf;
+    const size_t fb = align_up(size_t(c->g.elems) * c->esz, kAlign);
+    const size_t sb = fb * size_t(nf);   // one state (the fields of one ping-pong half are contiguous)
+    int64_t K = interval;
+    if (K <= 0) {
+        K = int64_t(std::ceil(std::sqrt(double(n))));
+        while (K * K < n) ++K;
+    }
+    if (K > n) K = n;
+    const int64_t nck = (n + K - 1) / K;
+    int64_t tot = 0;
+    for (int a = 0; a < c->nd; ++a) tot += c->T[a];
+    size_t off = 0;
+    const size_t o_ck = off; off += sb * size_t(nck);
+    const size_t o_end = off; off += sb;
+    const size_t o_seg = off; off += sb * size_t(K);
+    const size_t o_stage = off; off += sb * 6;
+    const size_t o_res = off; off += align_up(size_t(n) * size_t(c->nr > 0 ? c->nr : 1) * c->esz, kAlign);
+    const size_t o_acc = off; off += align_up(size_t(tot) * sizeof(double), kAlign);
+    const size_t o_mis = off; off += kAlign;
+    char *mem = nullptr;
+    cudaError_t ce = cudaMalloc(&mem, off);
+    if (ce != cudaSuccess) return fail(c, PML_ENOMEM, "cudaMalloc(%zu) for checkpoints: %s", off, cudaGetErrorString(ce));
+    struct Free {
+        char *p;
+        ~Free() { if (p) cudaFree(p); }
+    } guard{mem};
+    auto state_at = [&](size_t base, void *out[8]) {
+        for (int f = 0; f < nf; ++f) out[f] = mem + base + size_t(f) * fb;
+    };
+    void *K1[8], *Y2[8], *Y3[8], *Y4[8], *KB[8], *YB[8];
+    state_at(o_stage + 0 * sb, K1);
+    state_at(o_stage + 1 * sb, Y2);
+    state_at(o_stage + 2 * sb, Y3);
+    state_at(o_stage + 3 * sb, Y4);
+    state_at(o_stage + 4 * sb, KB);
+    state_at(o_stage + 5 * sb, YB);
+    PML_CU(c, cudaMemsetAsync(mem + o_stage, 0, sb * 6, c->st), "clear stage buffers");
+    double *dacc = reinterpret_cast<double *>(mem + o_acc), *dmis = reinterpret_cast<double *>(mem + o_mis);
+    PML_CU(c, cudaMemsetAsync(dacc, 0, size_t(tot) * sizeof(double), c->st), "clear gradient");
+    PML_CU(c, cudaMemsetAsync(dmis, 0, sizeof(double), c->st), "clear misfit");
+
+    // forward run with a checkpoint every K steps
+    const int64_t s0 = c->step, tk0 = c->trace_k;
+    for (int64_t k = 0; k < n; ++k) {
+        if (k % K == 0)
+            PML_CU(c, cudaMemcpyAsync(mem + o_ck + size_t(k / K) * sb, c->fld[c->cur][0], sb, cudaMemcpyDeviceToDevice,
+                                      c->st), "checkpoint");
+        pml_status s = pml_step(c, 1);
+        if (s != PML_OK) return s;
+    }
+    PML_CU(c, cudaMemcpyAsync(mem + o_end, c->fld[c->cur][0], sb, cudaMemcpyDeviceToDevice, c->st), "final state");
+    if (c->nr > 0 && target)
+        PML_CU(c, launch_residual(c->prec, static_cast<const char *>(c->trace) + size_t(tk0) * size_t(c->nr) * c->esz,
+                                  target, mem + o_res, n * c->nr, dmis, c->st), "residual kernel");
+    else if (c->nr > 0)
+        PML_CU(c, cudaMemcpyAsync(mem + o_res, residual, size_t(n) * size_t(c->nr) * c->esz, cudaMemcpyDeviceToDevice,
+                                  c->st), "residual copy");
+
+    // backwards, one segment of at most K steps at a time
+    pml_status s = pml_adjoint_reset(c);
+    if (s != PML_OK) return s;
+    const SigmaPtrs sp = {{c->dsig[0], c->dsig[1], c->dsig[2]}};
+    const PointArgs pa = point_args(c);
+    const int nr_saved = c->nr;
+    const double dt = c->dt;
+    for (int64_t seg = nck - 1; seg >= 0; --seg) {
+        const int64_t sa = seg * K, se = std::min<int64_t>(n, sa + K);
+        PML_CU(c, cudaMemcpyAsync(c->fld[c->cur][0], mem + o_ck + size_t(seg) * sb, sb, cudaMemcpyDeviceToDevice,
+                                  c->st), "restore checkpoint");
+        c->step = s0 + sa;
+        c->nr = 0;   // recomputation records no traces
+        for (int64_t j = sa; j < se; ++j) {
+            PML_CU(c, cudaMemcpyAsync(mem + o_seg + size_t(j - sa) * sb, c->fld[c->cur][0], sb,
+                                      cudaMemcpyDeviceToDevice, c->st), "segment state");
+            if (j + 1 < se && (s = pml_step(c, 1)) != PML_OK) { c->nr = nr_saved; return s; }
+        }
+        c->nr = nr_saved;
+        for (int64_t m = se; m > sa; --m) {   // adjoint clock s0 + m: the step m-1 -> m
+            const int p = c->acur;
+            const void *row = nr_saved > 0 ? mem + o_res + size_t(m - 1) * size_t(nr_saved) * c->esz : nullptr;
+            if (row || c->ns > 0)
+                PML_CU(c, launch_adjoint_points(c->prec, c->adj[p][0], c->adj[p][1], pa, c->astep, row,
+                                                c->ns > 0 ? c->dgrad : nullptr, c->st), "adjoint point kernel");
+            void *Y1[8];
+            state_at(o_seg + size_t(m - 1 - sa) * sb, Y1);
+            void *const *yb = c->adj[p];
+            // forward stage inputs
+            PML_CU(c, launch_apply_op(c->prec, false, Y1, K1, nf, c->g, sp, c->h, c->st), "stage");
+            PML_CU(c, launch_axpby(c->prec, Y1, K1, Y2, 1.0, 0.5 * dt, nf, c->g.elems, c->st), "stage");
+            PML_CU(c, launch_apply_op(c->prec, false, Y2, K1, nf, c->g, sp, c->h, c->st), "stage");
+            PML_CU(c, launch_axpby(c->prec, Y1, K1, Y3, 1.0, 0.5 * dt, nf, c->g.elems, c->st), "stage");
+            PML_CU(c, launch_apply_op(c->prec, false, Y3, K1, nf, c->g, sp, c->h, c->st), "stage");
+            PML_CU(c, launch_axpby(c->prec, Y1, K1, Y4, 1.0, dt, nf, c->g.elems, c->st), "stage");
+            // stage cotangents, each contracted with its stage input
+            PML_CU(c, launch_axpby(c->prec, yb, yb, KB, dt / 6.0, 0.0, nf, c->g.elems, c->st), "cotangent");
+            PML_CU(c, launch_contract(c->prec, KB, Y4, nf, c->g, sp, c->h, dacc, c->st), "contraction");
+            PML_CU(c, launch_apply_op(c->prec, true, KB, YB, nf, c->g, sp, c->h, c->st), "cotangent");
+            PML_CU(c, launch_axpby(c->prec, yb, YB, KB, dt / 3.0, dt, nf, c->g.elems, c->st), "cotangent");
+            PML_CU(c, launch_contract(c->prec, KB, Y3, nf, c->g, sp, c->h, dacc, c->st), "contraction");
+            PML_CU(c, launch_apply_op(c->prec, true, KB, YB, nf, c->g, sp, c->h, c->st), "cotangent");
+            PML_CU(c, launch_axpby(c->prec, yb, YB, KB, dt / 3.0, 0.5 * dt, nf, c->g.elems, c->st), "cotangent");
+            PML_CU(c, launch_contract(c->prec, KB, Y2, nf, c->g, sp, c->h, dacc, c->st), "contraction");
+            PML_CU(c, launch_apply_op(c->prec, true, KB, YB, nf, c->g, sp, c->h, c->st), "cotangent");
+            PML_CU(c, launch_axpby(c->prec, yb, YB, KB, dt / 6.0, 0.5 * dt, nf, c->g.elems, c->st), "cotangent");
+            PML_CU(c, launch_contract(c->prec, KB, Y1, nf, c->g, sp, c->h, dacc, c->st), "contraction");
+            // the adjoint step itself
+            if ((s = enqueue_step(c, true, p)) != PML_OK) return s;
+            c->acur = 1 - p;
+            c->astep = c->astep - 1;
+        }
+    }
+    PML_CU(c, cudaMemcpyAsync(c->fld[c->cur][0], mem + o_end, sb, cudaMemcpyDeviceToDevice, c->st), "final state");
+    c->step = s0 + n;
+    PML_CU(c, cudaMemcpyAsync(grad_sigma, dacc, size_t(tot) * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+           "gradient copy");
+    PML_CU(c, cudaMemcpyAsync(misfit, dmis, sizeof(double), cudaMemcpyDeviceToHost, c->st), "misfit copy");
+    if (grad_amp && c->ns > 0)
+        PML_CU(c, cudaMemcpyAsync(grad_amp, c->dgrad, size_t(c->ns) * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+               "gradient copy");
+    return check_device_error(c);   // synchronises before the scratch is freed
+}
+
 pml_status pml_adjoint_read_field(pml_ctx *c, int field, void *dst, int on_device)
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");

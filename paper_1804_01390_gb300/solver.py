@@ -185,6 +185,26 @@ class PMLSolver:
         _lib.pml_adjoint_read_field(self.ctx, int(field), out.data_ptr(), True)
         return out
 
+    def sigma_gradient(self, n, target=None, residual=None, interval=0):
+        """Runs n steps from the current state; returns (J, [dJ/dsigma_a per axis],
+        dJ/da or None) for J = 1/2 sum (U_m(x_r) - target[m-1, r])^2, or for the misfit
+        whose trace gradient is `residual` (then J is 0) (pml_sigma_gradient)."""
+        g = np.zeros(int(sum(self.T)), dtype=np.float64)
+        ga = np.zeros(max(self.ns, 1), dtype=np.float64) if self.ns else None
+        args = []
+        for a in (target, residual):   # device copies in the context precision, kept alive
+            if a is not None:
+                a = a.to(device=self.device, dtype=self.dtype).contiguous()
+                assert tuple(a.shape) == (int(n), self.nr)
+            args.append(a)
+        ptr = [None if a is None else a.data_ptr() for a in args]
+        J = _lib.pml_sigma_gradient(self.ctx, int(n), ptr[0], ptr[1], int(interval), g, ga)
+        out, off = [], 0
+        for t in self.T:
+            out.append(g[off:off + t].copy())
+            off += t
+        return J, out, ga
+
     # -- checkpoints -----------------------------------------------------------------
     def state_bytes(self):
         return _lib.pml_state_bytes(self.ctx)

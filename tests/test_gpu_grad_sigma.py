@@ -1,0 +1,142 @@
+"""Gradient of the receiver misfit with respect to the damping profile on the GPU
+(pml_sigma_gradient: checkpointed recomputation plus the adjoint), against the oracle's
+reverse-stage-graph gradient, which is itself pinned by central differences of J(sigma).
+
+FP64 must agree to 1e-9 relative L2 (far inside the 1e-6 asked of gradients), FP32 to
+1e-3; the checkpoint interval only changes where forward states are recomputed, so every
+interval must give the same gradient bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+from ._helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(N, w, steps, seed):
+    rng = np.random.default_rng(seed)
+    T = tuple(n + 2 * w for n in N)
+    draws = [rng.random(t) for t in T]
+    sig = [oracle.sigma_profile(n, w, oracle.KIND_RANDOM, 2.0, draws=d) for n, d in zip(N, draws)]
+    u0 = rng.normal(size=T[::-1])
+    v0 = 0.3 * rng.normal(size=T[::-1])
+    rec = [tuple(int(w + rng.integers(0, n)) for n in N) for _ in range(3)]
+    src = [tuple(w + n // 2 for n in N)]
+    amp = [0.7]
+    tgt = 0.1 * rng.normal(size=(steps, len(rec)))
+    return draws, sig, u0, v0, rec, src, amp, tgt
+
+
+def _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, interval):
+    import torch
+    from paper_1804_01390_gb300.solver import PMLSolver
+    s = PMLSolver(N, w, sigma="random", sigma_max=2.0, draws=draws, precision=prec,
+                  device=torch.device("cuda:0"), adjoint=True)
+    s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
+    s.set_sources(src, amp, 0.1, 10.0)
+    s.set_receivers(rec, steps)
+    J, grad, gamp = s.sigma_gradient(steps, torch.from_numpy(tgt), interval=interval)
+    gu = s.adjoint_read(0).double().cpu().numpy()
+    assert s.step_count == steps
+    s.close()
+    return J, grad, gamp, gu
+
+
+def _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps):
+    T = tuple(n + 2 * w for n in N)
+    g = oracle.Grid(T, 1.0, sig)
+    y = g.zeros_state()
+    y[0] = u0.reshape(-1)
+    y[1] = v0.reshape(-1)
+    ridx = [g.flat(r) for r in rec]
+    srcd = {"idx": [g.flat(p) for p in src], "amp": amp, "f_peak": 0.1, "t_delay": 10.0}
+    J, grad = oracle.misfit_grad_sigma(g, y, steps, 0.5, ridx, tgt, sources=srcd)
+    # dJ/da and dJ/dU0 from the oracle's adjoint with the same residual
+    yT, tr = oracle.rk4(g, y, steps, 0.5, sources=srcd, receivers=ridx)
+    yb, gamp = oracle.adjoint(g, g.zeros_state(), steps, 0.5, steps, sources=srcd, receivers=ridx,
+                              residual=(tr - tgt)[::-1].copy())
+    return J, grad, gamp, g.field(yb, 0)
+
+
+@pytest.mark.parametrize("N,w,steps", [((20, 18), 5, 30), ((8, 7, 9), 3, 12)])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_sigma_gradient_matches_oracle(N, w, steps, prec):
+    draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=sum(N) + w)
+    J, grad, gamp, gu = _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, 0)
+    Jo, grado, gampo, guo = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps)
+    tol = 1e-9 if prec == 64 else 1e-3
+    assert abs(J - Jo) <= tol * Jo, (J, Jo)
+    err = rel_l2(np.concatenate(grad), np.concatenate(grado))
+    assert err <= tol, err
+    for a in range(len(N)):
+        assert np.all(grad[a][sig[a] == 0.0] == 0.0)
+    assert rel_l2(gamp, gampo) <= tol
+    assert rel_l2(gu, guo) <= tol
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    N, w, steps = (24, 20), 6, 21
+    draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=5)
+    ref = None
+    for interval in (1, 4, 0, steps):   # 0: ceil(sqrt(21)) = 5
+        J, grad, gamp, gu = _gpu(N, w, 64, draws, u0, v0, rec, src, amp, tgt, steps, interval)
+        got = (J, np.concatenate(grad), gamp, gu)
+        if ref is None:
+            ref = got
+            continue
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]) and np.array_equal(got[3], ref[3])
+
+
+def test_long_run_with_sqrt_checkpoints():
+    """400 steps with the default sqrt(n) checkpoint spacing (20): the gradient still
+    matches the oracle, which keeps all 401 states."""
+    N, w, steps = (32, 28), 8, 400
+    draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=9)
+    J, grad, _, _ = _gpu(N, w, 64, draws, u0, v0, rec, src, amp, tgt, steps, 0)
+    Jo, grado, _, _ = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps)
+    assert abs(J - Jo) <= 1e-9 * Jo
+    assert rel_l2(np.concatenate(grad), np.concatenate(grado)) <= 1e-9
+
+
+def test_autograd_sigma_matches_oracle_and_differences():
+    """PMLTracesSigma: the damping profile as a differentiable input.  L = 1/2 |traces -
+    target|^2 through torch; dL/dsigma against the oracle and against central differences
+    of L evaluated by the forward pass."""
+    import torch
+    from paper_1804_01390_gb300.autograd import traces_sigma
+    N, w, steps = (18, 16), 5, 24
+    draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=31)
+    v0 = np.zeros_like(v0)   # the Function starts from V = 0
+    dev = torch.device("cuda:0")
+    sig_t = [torch.tensor(s_, dtype=torch.float64, requires_grad=True) for s_ in sig]
+    u0_t = torch.tensor(u0, dtype=torch.float64, device=dev, requires_grad=True)
+    amp_t = torch.tensor(amp, dtype=torch.float64, requires_grad=True)
+    tgt_t = torch.tensor(tgt, dtype=torch.float64, device=dev)
+
+    def loss(sigmas):
+        tr = traces_sigma(N, w, sigmas, u0_t, amp_t, steps, src, rec, 0.1, 10.0, precision=64)
+        return 0.5 * ((tr - tgt_t) ** 2).sum()
+
+    L = loss(sig_t)
+    L.backward()
+    Jo, grado, gampo, guo = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps)
+    assert abs(L.item() - Jo) <= 1e-9 * Jo
+    got = np.concatenate([s_.grad.numpy() for s_ in sig_t])
+    assert rel_l2(got, np.concatenate(grado)) <= 1e-9
+    assert rel_l2(amp_t.grad.numpy(), gampo) <= 1e-9
+    assert rel_l2(u0_t.grad.cpu().numpy(), guo) <= 1e-9
+    eps = 1e-5
+    for a, e in ((0, 1), (1, sig[1].shape[0] - 2)):
+        if sig[a][e] == 0.0:
+            continue
+        with torch.no_grad():
+            sp = [s_.detach().clone() for s_ in sig_t]
+            sm = [s_.detach().clone() for s_ in sig_t]
+            sp[a][e] += eps
+            sm[a][e] -= eps
+            fd = (loss(sp).item() - loss(sm).item()) / (2 * eps)
+        assert abs(sig_t[a].grad[e].item() - fd) <= 1e-6 * max(abs(fd), 1e-3), (a, e, sig_t[a].grad[e].item(), fd)
