@@ -382,6 +382,33 @@ def run_ours(args, ws, rank, local):
         s.close()
         del s
 
+    # ---- damping gradient with sqrt(n) checkpoints (2048^2 + 32 adjoint workload, FP32) --
+    gsig = None
+    if not args.no_grad_sigma:
+        wl5 = wk.cfg5()
+        n5 = max(K // 5, 100)
+        s = PMLSolver(wl5.N, wl5.w, dt=wl5.dt, precision=32, device=dev, adjoint=True)
+        u5 = torch.from_numpy(wk.initial_field(wl5, dtype=np.float32)).to(dev)
+        src5 = wl5.sources
+        s.set_sources(src5["coords"], src5["amp"], src5["f_peak"], src5["t_delay"])
+        tgt5 = torch.zeros((n5, len(wl5.receivers)), dtype=torch.float32, device=dev)
+        for rep in range(2):   # the first call is the warm-up
+            s.set_initial(u5)
+            s.set_receivers(wl5.receivers, n5)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J5, _, _ = s.sigma_gradient(n5, tgt5)
+            t1 = time.perf_counter()
+        pts5 = wl5.points
+        gsig = {"workload": "2D 2048^2 interior + 32-cell quadratic PML, 16 Ricker sources, 64 receivers, FP32: "
+                            "%d forward steps with checkpoints every %d, then the adjoint with the damping "
+                            "gradient" % (n5, int(np.ceil(np.sqrt(n5)))),
+                "steps": n5, "seconds": t1 - t0, "ms_per_step": (t1 - t0) * 1e3 / n5,
+                "value": pts5 * n5 / (t1 - t0) / 1e9, "unit": "GPts/s (forward + adjoint + gradient per step)",
+                "misfit": J5}
+        s.close()
+        del s, u5
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -403,7 +430,7 @@ def run_ours(args, ws, rank, local):
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
-            "cfg3": d3, "batched": d4, "stress": stress,
+            "cfg3": d3, "batched": d4, "stress": stress, "grad_sigma": gsig,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -482,6 +509,7 @@ def main():
     ap.add_argument("--n3", type=int, default=None, help="3D physical side (default 512)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--no-grad-sigma", action="store_true")
     ap.add_argument("--n4", type=int, default=None, help="largest side of the batched grids (default 2048)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")

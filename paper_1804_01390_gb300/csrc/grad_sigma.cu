@@ -37,12 +37,15 @@ template <typename T, bool ADJ>
 __global__ void __launch_bounds__(256) k_apply(const Fld<T> in, const FldW<T> out, const Idx ix, SigmaPtrs s, T ih,
                                                T ih2, T i2h)
 {
-    const int64_t n = ix.T[0] * ix.T[1] * ix.T[2];
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+    // boxes handled here have fewer than 2^31 vertices (checked by the caller): 32-bit index math
+    const uint32_t T0 = uint32_t(ix.T[0]), T1 = uint32_t(ix.T[1]);
+    const uint32_t n = T0 * T1 * uint32_t(ix.T[2]);
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int64_t c[3];
-        c[0] = v % ix.T[0];
-        c[1] = (v / ix.T[0]) % ix.T[1];
-        c[2] = v / (ix.T[0] * ix.T[1]);
+        const uint32_t q = v / T0;
+        c[0] = v - q * T0;
+        c[1] = q % T1;
+        c[2] = q / T1;
         const int64_t o = ix.off(c[0], c[1], c[2]);
         T acc = T(0);   // V row (forward) or U row (transpose)
         const int lapf = ADJ ? 1 : 0;
@@ -195,6 +198,7 @@ template <typename T> FldW<T> fldw(void *const *p, int nf)
 cudaError_t launch_apply_op(int prec, bool adjoint, void *const *in, void *const *out, int nf, const Geom &g,
                             const SigmaPtrs &s, double h, cudaStream_t st)
 {
+    if (g.T[0] * g.T[1] * g.T[2] >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
     const Idx ix = make_idx(g);
     const int grid = grid_for(g.T[0] * g.T[1] * g.T[2]);
     if (prec == 32) {
