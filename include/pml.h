@@ -336,6 +336,29 @@ pml_status pml_batch_profile_read(pml_batch *batch, double ms[2], int64_t launch
 pml_status pml_batch_info(const pml_batch *batch, int64_t info[4]);
 void pml_batch_destroy(pml_batch *batch);
 
+/*
+ * Layer design (host only, no device work).  The amplitude factor of the residual wave a
+ * layer lets back into the physical domain, from the one-edge decay rate rho of
+ * eq:IntroDecayRate (Sec. 1.1.2) multiplied over the edges the wave crosses (Sec. 1.1.4):
+ *   backed = 0: prod_e |rho(s_e, k, w)|            (a layer truncated periodically, as here:
+ *                                                 the wave crosses every layer edge once)
+ *   backed = 1: prod_e |rho(s_e, k, w)| / |rho(s_e, -conj(k), w)|   (a layer backed by a
+ *                                                 reflecting wall, crossed there and back)
+ * pml_residual_factor: sigma_h[e] = sigma * h of the m edges crossed; k h = kh_re + i kh_im
+ * the wave number normal to the layer (traveling waves: kh_im = 0), omega_h = omega * h
+ * (omega from the discrete dispersion relation (omega h)^2 = sum_a 4 sin^2(k_a h / 2)).
+ * pml_design_width: the smallest w in 1..w_max for which the library's profile of `kind`
+ * (PML_SIGMA_CONSTANT or PML_SIGMA_POWER with `order`, peak sigma_max * h = sigma_max_h)
+ * keeps the factor at or below eps for every omega h in (0, omega_h_max] and incidence with
+ * cos(theta) = Re(k)/omega in [cos_min, 1] (grazing waves are not damped at all, Sec. 1.1.4:
+ * they take w / cos(theta) to cross the layer).  *w_out = -1 when none does;
+ * *worst_out = the largest factor of the sweep at the returned (or last) width.
+ */
+pml_status pml_residual_factor(int m, const double *sigma_h, double kh_re, double kh_im, double omega_h,
+                               int backed, double *factor);
+pml_status pml_design_width(int kind, double sigma_max_h, double order, double cos_min, double omega_h_max,
+                            double eps, int backed, int w_max, int *w_out, double *worst_out);
+
 void pml_destroy(pml_ctx *ctx);
 const char *pml_last_error(const pml_ctx *ctx);
 const char *pml_status_string(pml_status s);

@@ -51,7 +51,7 @@ EXPORTED = (
     "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
     "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
     "pml_batch_autotune", "pml_batch_profile_enable", "pml_batch_profile_read", "pml_batch_info",
-    "pml_batch_destroy", "pml_destroy", "pml_last_error", "pml_status_string",
+    "pml_batch_destroy", "pml_residual_factor", "pml_design_width", "pml_destroy", "pml_last_error", "pml_status_string",
 )
 
 
@@ -123,6 +123,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_batch_profile_enable": [P, ctypes.c_int],
         "pml_batch_profile_read": [P, P, P],
         "pml_batch_info": [P, P],
+        "pml_residual_factor": [ctypes.c_int, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, P],
+        "pml_design_width": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -355,6 +358,26 @@ def pml_batch_info(batch):
 
 def pml_batch_destroy(batch):
     load().pml_batch_destroy(batch)
+
+
+def pml_residual_factor(sigma_h, kh, omega_h, backed=False):
+    """Residual-wave amplitude factor of one pass through the edges sigma_h (sigma * h)."""
+    import numpy as np
+    s = np.ascontiguousarray(sigma_h, dtype=np.float64)
+    out = ctypes.c_double(0.0)
+    kh = complex(kh)
+    _check(load().pml_residual_factor(int(s.shape[0]), s.ctypes.data if s.size else None, kh.real, kh.imag,
+                                      float(omega_h), int(bool(backed)), ctypes.byref(out)))
+    return float(out.value)
+
+
+def pml_design_width(kind, sigma_max_h, order, cos_min, omega_h_max, eps, backed=False, w_max=512):
+    """(smallest width meeting eps or -1, largest factor of the sweep at that width)."""
+    w = ctypes.c_int(0)
+    worst = ctypes.c_double(0.0)
+    _check(load().pml_design_width(int(kind), float(sigma_max_h), float(order), float(cos_min), float(omega_h_max),
+                                   float(eps), int(bool(backed)), int(w_max), ctypes.byref(w), ctypes.byref(worst)))
+    return int(w.value), float(worst.value)
 
 
 def pml_destroy(ctx):
