@@ -98,11 +98,20 @@ def _lib(openmp: bool = False) -> ctypes.CDLL:
         lib.orc_adjoint.restype = cint
         lib.orc_adjoint.argtypes = [cint, P, dbl, P, P, i64, dbl, i64, cint, P, dbl, dbl, P,
                                     cint, P, P]
+        lib.orc_set_boundary.restype = None
+        lib.orc_set_boundary.argtypes = [cint]
         lib.orc_misfit_grad_sigma.restype = cint
         lib.orc_misfit_grad_sigma.argtypes = [cint, P, dbl, P, P, i64, dbl, i64, cint, P, P, dbl,
                                               dbl, cint, P, P, P, P]
         _LIBS[openmp] = lib
         return lib
+
+
+def _bc(grid, openmp=False):
+    """The library to call for `grid`, with its boundary (periodic or wall) selected."""
+    lib = _lib(openmp)
+    lib.orc_set_boundary(int(grid.wall))
+    return lib
 
 
 def _ptr(a):
@@ -118,9 +127,11 @@ def _i64(a):
 
 
 class Grid:
-    """A periodic box: shape T (x fastest, length ndim), spacing h, sigma per axis."""
+    """A box of shape T (x fastest, length ndim), spacing h, sigma per axis; periodic, or
+    with wall=True zero beyond both ends of every axis (sigma[T-1] must then be 0)."""
 
-    def __init__(self, T, h, sigmas):
+    def __init__(self, T, h, sigmas, wall=False):
+        self.wall = bool(wall)
         self.T = tuple(int(t) for t in T)
         self.ndim = len(self.T)
         assert 1 <= self.ndim <= 3 and len(sigmas) == self.ndim
@@ -128,6 +139,8 @@ class Grid:
         self.sigmas = [_f64(s) for s in sigmas]
         for t, s in zip(self.T, self.sigmas):
             assert s.shape == (t,)
+        if self.wall:
+            assert all(s_[-1] == 0.0 for s_ in self.sigmas), "a wall leaves no edge T-1 -> 0"
         self._T = _i64(self.T)
         self._sig = _f64(np.concatenate(self.sigmas))
 
@@ -198,7 +211,7 @@ def rhs(grid: Grid, y, sources=None, t=0.0):
     y = _f64(y).reshape(grid.nfields, grid.n)
     out = np.empty_like(y)
     ns, idx, amp, fp, td, _k1, _k2 = _src_args(sources)
-    _lib().orc_rhs(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y), _ptr(out), ns,
+    _bc(grid).orc_rhs(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y), _ptr(out), ns,
                    _ptr(idx), _ptr(amp), fp, td, float(t))
     return out
 
@@ -214,7 +227,7 @@ def rk4(grid: Grid, y, nsteps, dt, step0=0, sources=None, receivers=None, openmp
         ridx = _i64(receivers)
         nr = int(ridx.shape[0])
         trace = np.zeros((int(nsteps), nr), dtype=np.float64)
-    rc = _lib(openmp).orc_rk4(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y),
+    rc = _bc(grid, openmp).orc_rk4(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y),
                               int(nsteps), float(dt), int(step0), ns, _ptr(idx), _ptr(amp), fp,
                               td, nr, _ptr(ridx), _ptr(trace))
     if rc != 0:
@@ -227,7 +240,7 @@ def energy(grid: Grid, y, lo=None, hi=None):
     y = _f64(y).reshape(grid.nfields, grid.n)
     lo = _i64([0] * grid.ndim if lo is None else lo)
     hi = _i64([t - 1 for t in grid.T] if hi is None else hi)
-    return _lib().orc_energy(grid.ndim, _ptr(grid._T), grid.h, _ptr(y), _ptr(lo), _ptr(hi))
+    return _bc(grid).orc_energy(grid.ndim, _ptr(grid._T), grid.h, _ptr(y), _ptr(lo), _ptr(hi))
 
 
 def norms(grid: Grid, U, ref=None, lo=None, hi=None):
@@ -244,7 +257,7 @@ def norms(grid: Grid, U, ref=None, lo=None, hi=None):
 def rhs_transpose(grid: Grid, yb):
     yb = _f64(yb).reshape(grid.nfields, grid.n)
     out = np.empty_like(yb)
-    _lib().orc_rhs_transpose(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(yb),
+    _bc(grid).orc_rhs_transpose(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(yb),
                              _ptr(out))
     return out
 
@@ -261,7 +274,7 @@ def adjoint(grid: Grid, yb, nsteps, dt, step_end, sources=None, receivers=None, 
         ridx = _i64(receivers)
         nr = int(ridx.shape[0])
         res = _f64(residual).reshape(int(nsteps), nr)
-    rc = _lib().orc_adjoint(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(yb),
+    rc = _bc(grid).orc_adjoint(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(yb),
                             int(nsteps), float(dt), int(step_end), ns, _ptr(idx), fp, td,
                             _ptr(gamp), nr, _ptr(ridx), _ptr(res))
     if rc != 0:
@@ -280,7 +293,7 @@ def misfit_grad_sigma(grid: Grid, y0, nsteps, dt, receivers, target, sources=Non
     tgt = _f64(target).reshape(int(nsteps), nr)
     J = ctypes.c_double(0.0)
     grad = np.zeros(int(sum(grid.T)), dtype=np.float64)
-    rc = _lib().orc_misfit_grad_sigma(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y0),
+    rc = _bc(grid).orc_misfit_grad_sigma(grid.ndim, _ptr(grid._T), grid.h, _ptr(grid._sig), _ptr(y0),
                                       int(nsteps), float(dt), int(step0), ns, _ptr(idx), _ptr(amp), fp,
                                       td, nr, _ptr(ridx), _ptr(tgt), ctypes.byref(J), _ptr(grad))
     if rc != 0:

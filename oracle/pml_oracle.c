@@ -41,7 +41,17 @@ typedef struct {
     int64_t T[3];
     double h;
     const double *sig[3];
+    int wall;            /* 0: periodic box; 1: every field is zero beyond both ends of every axis */
 } orc_grid;
+
+/*
+ * Boundary of the box for the calls that follow: 0 periodic (the paper's truncation,
+ * Sec. 1.1.3), 1 a reflecting wall just beyond each end (the layer backed by a reflecting
+ * boundary of Sec. 1.1.4: U, V, Phi, Psi are zero at the vertices -1 and T; the caller's
+ * sigma has sigma[T-1] = 0, there being no edge from T-1 to 0).
+ */
+static int g_wall = 0;
+void orc_set_boundary(int wall) { g_wall = wall ? 1 : 0; }
 
 typedef struct {
     int ns;
@@ -56,6 +66,7 @@ static void grid_from_args(orc_grid *g, int ndim, const int64_t *T, double h, co
     int a;
     g->ndim = ndim;
     g->h = h;
+    g->wall = g_wall;
     for (a = 0; a < 3; a++) g->T[a] = (a < ndim) ? T[a] : 1;
     {
         const double *p = sig_concat;
@@ -80,14 +91,18 @@ static int64_t to_flat(const orc_grid *g, const int64_t c[3])
     return c[0] + g->T[0] * (c[1] + g->T[1] * c[2]);
 }
 
-/* flat index of the vertex c + s*e_a, wrapping periodically along axis a */
+/* flat index of the vertex c + s*e_a, wrapping periodically along axis a; with a wall,
+ * -1 for a vertex beyond the end of the box (read as zero through at()) */
 static int64_t shifted(const orc_grid *g, const int64_t c[3], int a, int s)
 {
     int64_t d[3];
     d[0] = c[0]; d[1] = c[1]; d[2] = c[2];
+    if (g->wall && (d[a] + s < 0 || d[a] + s >= g->T[a])) return -1;
     d[a] = ((d[a] + s) % g->T[a] + g->T[a]) % g->T[a];
     return to_flat(g, d);
 }
+
+static double at(const double *f, int64_t i) { return i < 0 ? 0.0 : f[i]; }
 
 /* Ricker time function g(t) = (1 - 2 pi^2 f^2 (t-t0)^2) exp(-pi^2 f^2 (t-t0)^2). */
 double orc_ricker(double t, double f_peak, double t_delay)
@@ -189,7 +204,7 @@ static void rhs(const orc_grid *g, const double *y, double *out, const orc_src *
         oU[i] = V[i];
         for (a = 0; a < g->ndim; a++) {
             int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
-            lap += (U[ip] - 2.0 * U[i] + U[im]) / (h * h);
+            lap += (at(U, ip) - 2.0 * U[i] + at(U, im)) / (h * h);
         }
         for (a = 0; a < g->ndim; a++) {
             const double *Phi = y + (2 + 2 * a) * n, *Psi = y + (3 + 2 * a) * n;
@@ -198,10 +213,10 @@ static void rhs(const orc_grid *g, const double *y, double *out, const orc_src *
             const double s_i = g->sig[a][c[a]];
             const double s_im = g->sig[a][(c[a] - 1 + Ta) % Ta];
             int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
-            double dU = (U[ip] - U[im]) / (2.0 * h);
-            pml += (s_i * Psi[ip] - s_im * Phi[im]) / h;
-            oPhi[i] = (s_i != 0.0) ? -0.5 * (s_im * Phi[im] + s_i * Phi[i]) - dU : 0.0;
-            oPsi[i] = (s_im != 0.0) ? -0.5 * (s_im * Psi[i] + s_i * Psi[ip]) - dU : 0.0;
+            double dU = (at(U, ip) - at(U, im)) / (2.0 * h);
+            pml += (s_i * at(Psi, ip) - s_im * at(Phi, im)) / h;
+            oPhi[i] = (s_i != 0.0) ? -0.5 * (s_im * at(Phi, im) + s_i * Phi[i]) - dU : 0.0;
+            oPsi[i] = (s_im != 0.0) ? -0.5 * (s_im * Psi[i] + s_i * at(Psi, ip)) - dU : 0.0;
         }
         oV[i] = lap + pml;
     }
@@ -289,7 +304,7 @@ double orc_energy(int ndim, const int64_t *T, double h, const double *y, const i
     orc_grid g;
     int64_t n, i;
     double kin = 0.0, ela = 0.0;
-    g.ndim = ndim; g.h = h;
+    g.ndim = ndim; g.h = h; g.wall = g_wall;
     g.T[0] = T[0]; g.T[1] = ndim > 1 ? T[1] : 1; g.T[2] = ndim > 2 ? T[2] : 1;
     g.sig[0] = g.sig[1] = g.sig[2] = NULL;
     n = grid_n(&g);
@@ -302,7 +317,7 @@ double orc_energy(int ndim, const int64_t *T, double h, const double *y, const i
         if (!inside) continue;
         kin += y[n + i] * y[n + i];
         for (a = 0; a < ndim; a++) {
-            double d = (y[shifted(&g, c, a, +1)] - y[i]) / h;
+            double d = (at(y, shifted(&g, c, a, +1)) - y[i]) / h;
             ela += d * d;
         }
     }
@@ -362,7 +377,7 @@ static void rhs_transpose(const orc_grid *g, const double *yb, double *out)
         out[n + i] = Ub[i];
         for (a = 0; a < g->ndim; a++) {
             int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
-            acc += (Vb[ip] - 2.0 * Vb[i] + Vb[im]) / (h * h);
+            acc += (at(Vb, ip) - 2.0 * Vb[i] + at(Vb, im)) / (h * h);
         }
         for (a = 0; a < g->ndim; a++) {
             const double *Phib = yb + (2 + 2 * a) * n, *Psib = yb + (3 + 2 * a) * n;
@@ -373,15 +388,15 @@ static void rhs_transpose(const orc_grid *g, const double *yb, double *out)
             const double s_i = g->sig[a][ia], s_im = g->sig[a][iam];
             int64_t ip = shifted(g, c, a, +1), im = shifted(g, c, a, -1);
             /* supported adjoint entries (Phi support: sigma[j] != 0; Psi: sigma[j-1] != 0) */
-            double phib_p = (g->sig[a][iap] != 0.0) ? Phib[ip] : 0.0;
-            double phib_m = (g->sig[a][iam] != 0.0) ? Phib[im] : 0.0;
+            double phib_p = (g->sig[a][iap] != 0.0) ? at(Phib, ip) : 0.0;
+            double phib_m = (g->sig[a][iam] != 0.0) ? at(Phib, im) : 0.0;
             double phib_0 = (s_i != 0.0) ? Phib[i] : 0.0;
-            double psib_p = (s_i != 0.0) ? Psib[ip] : 0.0;        /* support of Psi(i+1): sigma[i] */
-            double psib_m = (g->sig[a][iamm] != 0.0) ? Psib[im] : 0.0; /* Psi(i-1): sigma[i-2] */
+            double psib_p = (s_i != 0.0) ? at(Psib, ip) : 0.0;        /* support of Psi(i+1): sigma[i] */
+            double psib_m = (g->sig[a][iamm] != 0.0) ? at(Psib, im) : 0.0; /* Psi(i-1): sigma[i-2] */
             double psib_0 = (s_im != 0.0) ? Psib[i] : 0.0;
             acc += (phib_p - phib_m) / (2.0 * h) + (psib_p - psib_m) / (2.0 * h);
-            oPhi[i] = (s_i != 0.0) ? -s_i * Vb[ip] / h - 0.5 * s_i * (phib_p + phib_0) : 0.0;
-            oPsi[i] = (s_im != 0.0) ? s_im * Vb[im] / h - 0.5 * s_im * (psib_0 + psib_m) : 0.0;
+            oPhi[i] = (s_i != 0.0) ? -s_i * at(Vb, ip) / h - 0.5 * s_i * (phib_p + phib_0) : 0.0;
+            oPsi[i] = (s_im != 0.0) ? s_im * at(Vb, im) / h - 0.5 * s_im * (psib_0 + psib_m) : 0.0;
         }
         out[i] = acc;
     }
@@ -491,13 +506,13 @@ static double dA_contract(const orc_grid *g, int a, int64_t e, const double *kb,
         to_coords(g, i, c);
         if (c[a] == e) {
             const int64_t ip = shifted(g, c, a, +1);
-            sum += kV[i] * Psi[ip] / h;
+            sum += kV[i] * at(Psi, ip) / h;
             sum += -0.5 * kPhi[i] * Phi[i];
-            if (psi_at_e) sum += -0.5 * kPsi[i] * Psi[ip];
+            if (psi_at_e) sum += -0.5 * kPsi[i] * at(Psi, ip);
         } else if (c[a] == (e + 1) % Ta) {
             const int64_t im = shifted(g, c, a, -1);
-            sum += -kV[i] * Phi[im] / h;
-            if (phi_at_e1) sum += -0.5 * kPhi[i] * Phi[im];
+            sum += -kV[i] * at(Phi, im) / h;
+            if (phi_at_e1) sum += -0.5 * kPhi[i] * at(Phi, im);
             sum += -0.5 * kPsi[i] * Psi[i];
         }
     }

@@ -628,3 +628,83 @@ def test_grad_sigma_zero_on_physical_edges(orc):
     for a in range(2):
         assert np.all(grad[a][sig[a] == 0.0] == 0.0)
         assert np.any(grad[a] != 0.0)
+
+
+# ----------------------------------------------------------------------------------
+# Layer backed by a reflecting wall (Sec. 1.1.4): every field is zero just beyond both
+# ends of the box.  The interface still does not reflect, and the wave that comes back
+# from the wall has crossed each layer edge there and back: its amplitude is the
+# product of |rho(s, k)| / |rho(s, -conj k)| over the edges.
+# ----------------------------------------------------------------------------------
+
+def _wall_sigma(orc, n, w, kind, smax):
+    s = orc.sigma_profile(n, w, kind, smax, 2.0)
+    s[-1] = 0.0          # no edge from T-1 back to 0
+    return s
+
+
+def test_wall_layer_interface_does_not_reflect(orc):
+    N, w = 32, 24
+    wl = wk.Workload("t", 2, (N, N), w, gaussians=[wk.Gaussian((w + 7.0, w + 15.5), 3.0, 2.0)])
+    u0 = wk.initial_field(wl)
+    T = (N + 2 * w,) * 2
+    g = orc.Grid(T, 1.0, [_wall_sigma(orc, N, w, orc.KIND_CONSTANT, 2.0) for _ in range(2)], wall=True)
+    y = g.zeros_state()
+    y[0] = u0.reshape(-1)
+    yn, _ = orc.rk4(g, y, 40, 0.5)
+    M = 160
+    gb = orc.Grid((M, M), 1.0, [np.zeros(M), np.zeros(M)])
+    off = (M - N) // 2
+    ub = np.zeros((M, M))
+    ub[off:off + N, off:off + N] = u0[w:w + N, w:w + N]
+    yb = gb.zeros_state()
+    yb[0] = ub.reshape(-1)
+    ybn, _ = orc.rk4(gb, yb, 40, 0.5)
+    a = g.field(yn, 0)[w:w + N, w:w + N]
+    b = gb.field(ybn, 0)[off:off + N, off:off + N]
+    assert np.abs(b).max() > 1e-2
+    assert np.abs(a - b).max() < 1e-14
+
+
+@pytest.mark.parametrize("kind,smax,kh", [(0, 0.04, 0.4), (1, 0.15, 0.7)])
+def test_wall_backed_residual_matches_round_trip_factor(orc, kind, smax, kh):
+    from paper_1804_01390_gb300 import _lib
+    _lib.load()
+    N, w, env = 300, 12, 25.0
+    T = N + 2 * w
+    sig = _wall_sigma(orc, N, w, kind, smax)
+    j = np.arange(T)
+    x0 = w + 0.7 * N
+    G = np.exp(-0.5 * ((j - x0) / env) ** 2)
+    wh = 2.0 * np.sin(kh / 2.0)
+    U = G * np.cos(kh * (j - x0))
+    V = wh * G * np.sin(kh * (j - x0))               # right-travelling, towards the wall
+    steps = int(round(2.0 * (T - x0) / np.cos(kh / 2.0) / 0.5))
+    amp = []
+    for s_ in (sig, np.zeros(T)):
+        g = orc.Grid((T,), 1.0, [s_], wall=True)
+        y = g.zeros_state()
+        y[0] = U
+        y[1] = V
+        yn, _ = orc.rk4(g, y, steps, 0.5)
+        amp.append(np.abs(yn[0][w:w + N]).max())
+    measured = amp[0] / amp[1]
+    right = sig[w + N:T - 1]                          # the layer edges between the domain and the wall
+    pred = _lib.pml_residual_factor(right, kh, wh, backed=True)
+    assert 0.05 < measured < 0.9
+    assert abs(measured - pred) <= 0.03 * pred, (measured, pred)
+
+
+def test_wall_box_energy_decays(orc):
+    N, w = 16, 20
+    g = orc.Grid((N + 2 * w,) * 2, 1.0, [_wall_sigma(orc, N, w, orc.KIND_CONSTANT, 2.0) for _ in range(2)],
+                 wall=True)
+    wl = wk.Workload("t", 2, (N, N), w, gaussians=[wk.Gaussian((w + 8.0, w + 8.0), 2.0, 2.0)])
+    y = g.zeros_state()
+    y[0] = wk.initial_field(wl).reshape(-1)
+    lo, hi = (w, w), (w + N - 1, w + N - 1)
+    E0 = orc.energy(g, y, lo, hi)
+    for _ in range(10):
+        y, _ = orc.rk4(g, y, 250, 0.5)
+    assert np.all(np.isfinite(y))
+    assert orc.energy(g, y, lo, hi) < 1e-8 * E0
