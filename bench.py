@@ -382,6 +382,21 @@ def run_ours(args, ws, rank, local):
         s.close()
         del s
 
+    # ---- layer backed by a reflecting wall (the headline workload with walls, FP32) ------
+    dwall = None
+    if not args.no_wall:
+        from paper_1804_01390_gb300 import _lib
+        s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev, wall=True)
+        _lib.pml_set_variant(s.ctx, variant)
+        s.set_initial(torch.from_numpy(u0).to(dev))
+        Kw = max(K // 4, 50)
+        msw, _ = timed_steps(s, Kw, min(W, 3), ws, profile=False)
+        msw = max_over_ranks(msw, ws, dev)
+        dwall = {"workload": "2D %d^2 interior + 32-cell quadratic PML backed by reflecting walls, FP32" % wl.N[0],
+                 "value": pts * Kw * ws / (msw / 1e3) / 1e9, "unit": UNIT, "steps": Kw, "ms_per_step": msw / Kw}
+        s.close()
+        del s
+
     # ---- damping gradient with sqrt(n) checkpoints (2048^2 + 32 adjoint workload, FP32) --
     gsig = None
     if not args.no_grad_sigma:
@@ -430,7 +445,7 @@ def run_ours(args, ws, rank, local):
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
-            "cfg3": d3, "batched": d4, "stress": stress, "grad_sigma": gsig,
+            "cfg3": d3, "batched": d4, "stress": stress, "grad_sigma": gsig, "wall": dwall,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -510,6 +525,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--no-grad-sigma", action="store_true")
+    ap.add_argument("--no-wall", action="store_true")
     ap.add_argument("--n4", type=int, default=None, help="largest side of the batched grids (default 2048)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")

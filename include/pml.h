@@ -92,7 +92,12 @@ enum { PML_FIELD_U = 0, PML_FIELD_V = 1 };
 
 /* flags of pml_create */
 enum {
-    PML_FLAG_ADJOINT = 1     /* also allocate the adjoint state (pml_adjoint_*) */
+    PML_FLAG_ADJOINT = 1,    /* also allocate the adjoint state (pml_adjoint_*) */
+    PML_FLAG_WALL = 2        /* end every axis with a reflecting wall instead of the periodic
+                                wrap: U, V, Phi, Psi are zero at the vertices -1 and T[a]
+                                (the layer backed by a reflecting boundary, Sec. 1.1.4).
+                                sigma_a[T[a]-1] (the wrap edge) is set to 0.  Not with
+                                pml_sigma_gradient. */
 };
 
 /*

@@ -28,6 +28,7 @@ PML_SIGMA_RANDOM = 2
 PML_SIGMA_USER = 3
 
 PML_FLAG_ADJOINT = 1
+PML_FLAG_WALL = 2
 
 PML_FIELD_U = 0
 PML_FIELD_V = 1

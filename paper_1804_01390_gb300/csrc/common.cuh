@@ -17,6 +17,8 @@ constexpr int G = 4;
 // origin + x + y * P + z * PS.
 struct Geom {
     int ndim;
+    int wall;          // 0: periodic box (ghost ring = periodic images); 1: reflecting wall
+                       // beyond both ends of every axis (ghost ring held at zero)
     int64_t T[3];      // vertices per axis (T[2] = 1 in 2D)
     int64_t P;         // row pitch in elements (multiple of 32)
     int64_t R;         // rows per plane incl. ghosts: T[1] + 2G
@@ -221,6 +223,10 @@ template <typename T>
 __device__ __forceinline__ void store_wrapped(T *base, const Geom &g, int64_t x, int64_t y, int64_t z,
                                               T v)
 {
+    if (g.wall) {   // the ghost ring stays zero
+        base[g.origin + x + y * g.P + z * g.PS] = v;
+        return;
+    }
     int64_t xs[2] = {x, x}, ys[2] = {y, y}, zs[2] = {z, z};
     int nx = 1, ny = 1, nz = 1;
     if (x < G) xs[nx++] = x + g.T[0];

@@ -44,10 +44,11 @@ struct Plan {
     size_t total = 0;
 };
 
-Geom make_geom(int nd, const int64_t T[3])
+Geom make_geom(int nd, const int64_t T[3], bool wall = false)
 {
     Geom g{};
     g.ndim = nd;
+    g.wall = wall ? 1 : 0;
     for (int a = 0; a < 3; ++a) g.T[a] = a < nd ? T[a] : 1;
     g.P = round_up(g.T[0] + 2 * G, 32);
     g.R = g.T[1] + 2 * G;
@@ -82,7 +83,7 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
         if (p->T[a] < 2 * G) { *why = "every axis needs n + 2w >= 8 vertices"; return false; }
         if (p->T[a] > (int64_t(1) << 30)) { *why = "axis too long"; return false; }
     }
-    p->g = make_geom(p->nd, p->T);
+    p->g = make_geom(p->nd, p->T, (flags & PML_FLAG_WALL) != 0);
     size_t off = 0;
     const size_t fb = align_up(size_t(p->g.elems) * p->esz, kAlign);
     for (int s = 0; s < 2; ++s)
@@ -225,6 +226,7 @@ pml_status build_sigma(pml_ctx *c, const pml_sigma_profile *pr)
             }
             s[size_t(e)] = v;
         }
+        if (c->flags & PML_FLAG_WALL) s[size_t(T - 1)] = 0.0;   // a wall leaves no edge T-1 -> 0
     }
     return PML_OK;
 }
@@ -266,6 +268,11 @@ void build_layout(pml_ctx *c)
         const int64_t centre = c->w + c->N[a] / 2;
         c->ir[a] = layer_free_run(s, centre, -2, 1);
         c->ir_adj[a] = layer_free_run(s, centre, -3, 2);
+        if (c->flags & PML_FLAG_WALL)   // the closed form needs real vertices on both sides
+            for (Range *r : {&c->ir[a], &c->ir_adj[a]}) {
+                r->lo = std::max<int64_t>(r->lo, 1);
+                r->hi = std::min<int64_t>(r->hi, T - 2);
+            }
         for (int64_t i = c->ir[a].lo; i <= c->ir[a].hi; ++i) c->inner[a][size_t(i)] = 1;
     }
     for (int a = c->nd; a < 3; ++a) c->ir[a] = c->ir_adj[a] = {0, 0};
@@ -303,7 +310,7 @@ std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
     Rect rest = full;
     for (int a = c->nd - 1; a >= 0; --a) {
         const bool lo_gap = ir[a].lo > 0, hi_gap = ir[a].hi < c->T[a] - 1;
-        if (a == 2 && (lo_gap || hi_gap)) {
+        if (a == 2 && !c->g.wall && (lo_gap || hi_gap)) {
             Rect r = rest; r.lo[a] = ir[a].hi + 1; r.hi[a] = c->T[a] + ir[a].lo - 1; out.push_back(r);
         } else {
             if (lo_gap) { Rect r = rest; r.lo[a] = 0; r.hi[a] = ir[a].lo - 1; out.push_back(r); }
@@ -353,6 +360,11 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
         const int64_t T0 = c->T[0], T1 = c->T[1];
         if (range_empty(ir[0]) || range_empty(ir[1])) {
             add(0, T0 - 1, 0, T1 - 1, kLayer2BandRows);
+        } else if (c->g.wall) {   // no seam to cross: two bands
+            if (ir[1].lo > 0) add(0, T0 - 1, 0, ir[1].lo - 1, kLayer2BandRows);
+            if (ir[1].hi < T1 - 1) add(0, T0 - 1, ir[1].hi + 1, T1 - 1, kLayer2BandRows);
+            if (ir[0].lo > 0) add(0, ir[0].lo - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
+            if (ir[0].hi < T0 - 1) add(ir[0].hi + 1, T0 - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
         } else {
             const int64_t band = T1 - (ir[1].hi - ir[1].lo + 1);
             if (band > 0) add(0, T0 - 1, ir[1].hi + 1, ir[1].hi + band, kLayer2BandRows);
@@ -886,8 +898,10 @@ pml_status pml_set_initial(pml_ctx *c, const void *u0, const void *v0, int on_de
         pml_status s = copy_dense(c, c->fld[0][1], v0, on_device != 0, true);
         if (s != PML_OK) return s;
     }
-    PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][0], c->g, c->st), "ghost fill");
-    PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][1], c->g, c->st), "ghost fill");
+    if (!c->g.wall) {   // with a wall the ghost ring stays zero
+        PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][0], c->g, c->st), "ghost fill");
+        PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][1], c->g, c->st), "ghost fill");
+    }
     c->step = 0;
     c->trace_k = 0;
     return PML_OK;
@@ -1081,6 +1095,7 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (!(c->flags & PML_FLAG_ADJOINT)) return fail(c, PML_ESTATE, "context was created without PML_FLAG_ADJOINT");
+    if (c->g.wall) return fail(c, PML_EINVAL, "pml_sigma_gradient supports periodic boxes only");
     if (n < 1) return fail(c, PML_EINVAL, "n must be >= 1");
     if (!grad_sigma || !misfit) return fail(c, PML_EINVAL, "grad_sigma and misfit are required");
     if (c->nr > 0 && !target == !residual)

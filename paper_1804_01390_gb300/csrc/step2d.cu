@@ -407,8 +407,8 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     const int32_t tx = tile.x0 - 4 + G;
     auto box_y = [&](int c) -> int32_t {          // box row of box c (rows stay in -4 .. T1 + 3)
         int y = tile.ylo - 4 + c * CH;
-        if (y > T1) y -= T1;
-        return int32_t(y + G);
+        if (!g.wall && y > T1) y -= T1;            // with a wall, items never cross the seam and
+        return int32_t(y + G);                     // rows beyond the ghost ring load as zeros
     };
     auto issue = [&](int c) {
         const uint32_t k = use + uint32_t(c);
@@ -473,6 +473,21 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     const LayerConstT<T> &lk = lconst_of<T>(a.k);
     const V ih = O::bc(lk.ih), ih2 = O::bc(lk.ih2), i2h = O::bc(lk.i2h), c4 = O::bc(lk.c4), c3 = O::bc(lk.c3),
             c2 = O::bc(lk.c2), c1 = O::bc(lk.c1);
+    // with a wall every stage value beyond the ends of the box is zero: the lane's columns
+    // and a row's validity as masks for the level values
+    V xmask = O::bc(T(1));
+    if (g.wall) {
+        T m[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) m[k] = (gx0 + k >= 0 && gx0 + k < g.T[0]) ? T(1) : T(0);
+        if constexpr (W == 1) xmask = m[0];
+        else xmask = make_float2(m[0], m[W - 1]);
+    }
+    auto wall_mask = [&](V v, int q) -> V {        // level value at input row q
+        if (!g.wall) return v;
+        const int y = tile.ylo - 4 + q;
+        return (y >= 0 && y < T1) ? O::sel(xmask, v) : O::bc(T(0));
+    };
     const int qmax = nch * CH - 1;                 // last row the boxes brought in
     const uint32_t rbase = uint32_t(CH) * use;
     // the lane's values of input row q (clamped into the rows brought in), field f at + f RR COLS
@@ -534,7 +549,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
             };
             apply_A2<O, ADJ, MASK>(N, sig_at(p - 1), ih, ih2, i2h, r);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) n4[f] = O::fma(c4, r[f], cen[f]);
+            for (int f = 0; f < NF; ++f) n4[f] = wall_mask(O::fma(c4, r[f], cen[f]), p - 1);
         }
         // level 3 at row p-3 (z4 rows p-4, p-3, p-2)
         {
@@ -555,7 +570,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
             };
             apply_A2<O, ADJ, MASK>(N, sig_at(p - 3), ih, ih2, i2h, r);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) n3[f] = O::fma(c3, r[f], O::ld(y3 + f * FS));
+            for (int f = 0; f < NF; ++f) n3[f] = wall_mask(O::fma(c3, r[f], O::ld(y3 + f * FS)), p - 3);
         }
         // level 2 at row p-5 (z3 rows p-6, p-5, p-4)
         {
@@ -576,7 +591,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
             };
             apply_A2<O, ADJ, MASK>(N, sig_at(p - 5), ih, ih2, i2h, r);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) n2[f] = O::fma(c2, r[f], O::ld(y5 + f * FS));
+            for (int f = 0; f < NF; ++f) n2[f] = wall_mask(O::fma(c2, r[f], O::ld(y5 + f * FS)), p - 5);
         }
         // level 1 at row p-7 (z2 rows p-8, p-7, p-6): output row p-11 of the item
         {

@@ -460,7 +460,7 @@ __device__ __forceinline__ void issue_plane3(T *stage_base, const Maps8 &maps, c
     using F = Fields<MASK>;
     constexpr int PL = L3<T>::PL, PLS = L3<T>::PLS;
     int64_t z = zin;
-    z += z < 0 ? g.T[2] : (z >= g.T[2] ? -g.T[2] : 0);
+    if (!g.wall) z += z < 0 ? g.T[2] : (z >= g.T[2] ? -g.T[2] : 0);   // a wall keeps the zero ghost planes
     mbar_arrive_expect_tx(bar, uint32_t(F::NF * PL * sizeof(T)));
 #pragma unroll
     for (int f = 0; f < F::NF; ++f)
@@ -533,6 +533,9 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
     const bool v1 = cx >= 4 && cx <= RX - 5 && cy >= 4 && cy <= RY - 5;
     const int64_t gx = int64_t(tile.x0) - 4 + cx, gy = int64_t(tile.y0) - 4 + cy;
     const bool in_rect = v1 && gx >= tile.xlo && gx <= tile.xhi && gy >= tile.ylo && gy <= tile.yhi;
+    // with a wall every stage value beyond the ends of the box is zero
+    const bool in_xy = !g.wall || (gx >= 0 && gx < g.T[0] && gy >= 0 && gy < g.T[1]);
+    auto keep = [&](int q) { return in_xy && (!g.wall || (zin0 + q >= 0 && zin0 + q < g.T[2])); };
 
     bool ok = true;
     int pfail = nin;   // first plane whose wait gave up
@@ -564,9 +567,10 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         T r[NF];
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
                         T *zb = Zb + ((0 * 2 + (q & 1)) * NF) * PLS;
+                        const bool kq = keep(q);
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Pc[f * PLS + tid] + c4 * r[f];
+                            const T val = kq ? Pc[f * PLS + tid] + c4 * r[f] : T(0);
                             z4r[(PH + 2) % 3][f] = val;
                             zb[f * PLS + tid] = val;
                         }
@@ -591,9 +595,10 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
                         const T *Y = stage + (q % S) * NF * PLS;
                         T *zo = Zb + ((1 * 2 + (q & 1)) * NF) * PLS;
+                        const bool kq = keep(q);
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Y[f * PLS + tid] + c3 * r[f];
+                            const T val = kq ? Y[f * PLS + tid] + c3 * r[f] : T(0);
                             z3r[(PH + 1) % 3][f] = val;
                             zo[f * PLS + tid] = val;
                         }
@@ -618,9 +623,10 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
                         apply_A3<T, ADJ, MASK>(N, sg, ih, ih2, i2h, r);
                         const T *Y = stage + (q % S) * NF * PLS;
                         T *zo = Zb + ((2 * 2 + (q & 1)) * NF) * PLS;
+                        const bool kq = keep(q);
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const T val = Y[f * PLS + tid] + c2 * r[f];
+                            const T val = kq ? Y[f * PLS + tid] + c2 * r[f] : T(0);
                             z2r[PH][f] = val;
                             zo[f * PLS + tid] = val;
                         }

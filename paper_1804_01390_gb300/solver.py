@@ -30,11 +30,12 @@ class PMLSolver:
     layer width ``w``, spacing ``h``, step ``dt``, damping profile ``sigma`` (one of
     "constant", "quadratic"/"power", "random", "user"), ``precision`` 32 or 64.
     ``draws`` (random) or ``user_sigma`` (user) are per-axis host arrays of length T.
+    ``wall=True`` ends every axis with a reflecting wall instead of the periodic wrap.
     """
 
     def __init__(self, N, w, h=1.0, dt=0.5, sigma="quadratic", sigma_max=2.0, order=2.0,
                  draws=None, user_sigma=None, precision=32, device=None, stream=None,
-                 adjoint=False):
+                 adjoint=False, wall=False):
         self.N = tuple(int(n) for n in N)
         self.ndim = len(self.N)
         self.w = int(w)
@@ -60,7 +61,8 @@ class PMLSolver:
                 assert arr.shape == (self.T[a],)
                 self._keep.append(arr)
                 user.append(_host_ptr(arr))
-        flags = _lib.PML_FLAG_ADJOINT if adjoint else 0
+        flags = (_lib.PML_FLAG_ADJOINT if adjoint else 0) | (_lib.PML_FLAG_WALL if wall else 0)
+        self.wall = bool(wall)
         nbytes = _lib.pml_workspace_bytes(self.ndim, self.N, self.w, self.precision, flags)
         with torch.cuda.device(self.device):
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
