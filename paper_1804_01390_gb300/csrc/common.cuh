@@ -20,6 +20,8 @@ struct Geom {
     int wall;          // 0: periodic box (ghost ring = periodic images); 1: reflecting wall
                        // beyond both ends of every axis (ghost ring held at zero)
     int64_t T[3];      // vertices per axis (T[2] = 1 in 2D)
+    int64_t wrap[3];   // offset of a vertex's ghost image: T[a] (periodic) or 0 (wall: the
+                       // image store lands on the vertex itself and the ghosts stay zero)
     int64_t P;         // row pitch in elements (multiple of 32)
     int64_t R;         // rows per plane incl. ghosts: T[1] + 2G
     int64_t PS;        // plane stride = P * R
@@ -223,19 +225,15 @@ template <typename T>
 __device__ __forceinline__ void store_wrapped(T *base, const Geom &g, int64_t x, int64_t y, int64_t z,
                                               T v)
 {
-    if (g.wall) {   // the ghost ring stays zero
-        base[g.origin + x + y * g.P + z * g.PS] = v;
-        return;
-    }
     int64_t xs[2] = {x, x}, ys[2] = {y, y}, zs[2] = {z, z};
     int nx = 1, ny = 1, nz = 1;
-    if (x < G) xs[nx++] = x + g.T[0];
-    else if (x >= g.T[0] - G) xs[nx++] = x - g.T[0];
-    if (y < G) ys[ny++] = y + g.T[1];
-    else if (y >= g.T[1] - G) ys[ny++] = y - g.T[1];
+    if (x < G) xs[nx++] = x + g.wrap[0];
+    else if (x >= g.T[0] - G) xs[nx++] = x - g.wrap[0];
+    if (y < G) ys[ny++] = y + g.wrap[1];
+    else if (y >= g.T[1] - G) ys[ny++] = y - g.wrap[1];
     if (g.ndim == 3) {
-        if (z < G) zs[nz++] = z + g.T[2];
-        else if (z >= g.T[2] - G) zs[nz++] = z - g.T[2];
+        if (z < G) zs[nz++] = z + g.wrap[2];
+        else if (z >= g.T[2] - G) zs[nz++] = z - g.wrap[2];
     }
     for (int c = 0; c < nz; ++c)
         for (int b = 0; b < ny; ++b)
@@ -340,7 +338,7 @@ int batch2d_strip_cols(int prec, int v);   // output columns per interior work i
 int batch2d_interior_blocks_per_sm(int prec, int v);
 cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st,
                                     bool overlap_previous);
-cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, bool wall, cudaStream_t st);
 
 // 3D counterparts.
 struct Interior3DArgs {
@@ -378,6 +376,28 @@ int layer3d_tile_y(int prec);
 // outputs are disjoint), the first one after all earlier work of the stream.
 cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,
                            void *const *out /*[8]*/, const Layer3DArgs &a, cudaStream_t st);
+cudaError_t launch_layer3d_wall(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,
+                                void *const *out /*[8]*/, const Layer3DArgs &a, cudaStream_t st);
+
+// Launch with programmatic stream serialization when overlap_previous: the kernel may
+// start while the previous kernel of the stream still runs (their outputs must be
+// disjoint); the kernel calls wait_prerequisite_grid() before it finishes.
+template <typename K, typename... Args>
+inline cudaError_t launch_pdl(K kernel, int grid, int threads, size_t smem, cudaStream_t st, bool overlap_previous,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap_previous ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // Damping gradient (grad_sigma.cu): explicit operator applications over the whole box,
 // stage combinations and the per-edge contraction kbar^T (dA/dsigma_a[e]) Y.

@@ -50,6 +50,7 @@ Geom make_geom(int nd, const int64_t T[3], bool wall = false)
     g.ndim = nd;
     g.wall = wall ? 1 : 0;
     for (int a = 0; a < 3; ++a) g.T[a] = a < nd ? T[a] : 1;
+    for (int a = 0; a < 3; ++a) g.wrap[a] = wall ? 0 : g.T[a];
     g.P = round_up(g.T[0] + 2 * G, 32);
     g.R = g.T[1] + 2 * G;
     g.PS = g.P * g.R;
@@ -1419,7 +1420,7 @@ pml_status batch_enqueue(pml_batch *b, int p, cudaStream_t st, bool timed)
     a.queue = b->dqueue;
     a.parity = p;
     long pi = timed ? bprof_begin(b, 1, st) : -1;
-    cudaError_t e = launch_batch2d_layer(b->prec, a, layer2d_grid(b->prec, b->ntiles, b->sm_count), st);
+    cudaError_t e = launch_batch2d_layer(b->prec, a, layer2d_grid(b->prec, b->ntiles, b->sm_count), b->ctx[0]->g.wall != 0, st);
     bprof_end(b, pi, st);
     if (e != cudaSuccess) return bfail(PML_ECUDA, "batched layer kernel: %s", cudaGetErrorString(e));
     pi = timed ? bprof_begin(b, 0, st) : -1;
@@ -1472,6 +1473,7 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
         if (c->nd != 2) return bfail(PML_EINVAL, "pml_batch_create: context %d is not 2D", i);
         if (c->prec != ctxs[0]->prec) return bfail(PML_EINVAL, "pml_batch_create: contexts mix precisions");
         if (c->st != ctxs[0]->st) return bfail(PML_EINVAL, "pml_batch_create: contexts use different streams");
+        if (c->g.wall != ctxs[0]->g.wall) return bfail(PML_EINVAL, "pml_batch_create: contexts mix walls and periodic boxes");
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return bfail(PML_EINVAL, "pml_batch_create: context %d appears twice", i);
     }

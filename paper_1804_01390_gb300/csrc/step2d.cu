@@ -390,7 +390,7 @@ __device__ __forceinline__ void issue_rows2(T *ring, const Maps6 &maps, int32_t 
 // box coordinates wrap by T1.  One loop iteration handles one input row p; the register
 // rings hold three rows of each level and rotate by one row per iteration (a compact loop
 // body keeps the instruction stream in cache).
-template <typename T, bool ADJ, int MASK>
+template <typename T, bool ADJ, int MASK, bool WALL>
 __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out, const Layer2DArgs &a,
                                              const LayerTile &tile, T *ring, T *sy, uint64_t *bars, int lane,
                                              uint32_t &use)
@@ -407,7 +407,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     const int32_t tx = tile.x0 - 4 + G;
     auto box_y = [&](int c) -> int32_t {          // box row of box c (rows stay in -4 .. T1 + 3)
         int y = tile.ylo - 4 + c * CH;
-        if (!g.wall && y > T1) y -= T1;            // with a wall, items never cross the seam and
+        if (!WALL && y > T1) y -= T1;              // with a wall, items never cross the seam and
         return int32_t(y + G);                     // rows beyond the ghost ring load as zeros
     };
     auto issue = [&](int c) {
@@ -476,7 +476,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     // with a wall every stage value beyond the ends of the box is zero: the lane's columns
     // and a row's validity as masks for the level values
     V xmask = O::bc(T(1));
-    if (g.wall) {
+    if (WALL) {
         T m[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) m[k] = (gx0 + k >= 0 && gx0 + k < g.T[0]) ? T(1) : T(0);
@@ -484,7 +484,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
         else xmask = make_float2(m[0], m[W - 1]);
     }
     auto wall_mask = [&](V v, int q) -> V {        // level value at input row q
-        if (!g.wall) return v;
+        if (!WALL) return v;
         const int y = tile.ylo - 4 + q;
         return (y >= 0 && y < T1) ? O::sel(xmask, v) : O::bc(T(0));
     };
@@ -855,7 +855,7 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 
 // Each warp takes items from a work queue (atomic counter) until the list is done; tiles
 // are sorted by class, so warps run the same class at the same time.
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, bool WALL>
 __global__ void __launch_bounds__(128, L2Cfg<T>::MINB)
     k_layer2d(const __grid_constant__ Maps6 maps, const Out6 out, const Layer2DArgs a)
 {
@@ -882,10 +882,10 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB)
         const LayerTile tile = a.tiles[item];
         bool ok;
         switch (tile.flags & 3) {
-        case 0: ok = layer2d_item<T, ADJ, 0>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
-        case 1: ok = layer2d_item<T, ADJ, 1>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
-        case 2: ok = layer2d_item<T, ADJ, 2>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
-        default: ok = layer2d_item<T, ADJ, 3>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 0: ok = layer2d_item<T, ADJ, 0, WALL>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 1: ok = layer2d_item<T, ADJ, 1, WALL>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 2: ok = layer2d_item<T, ADJ, 2, WALL>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        default: ok = layer2d_item<T, ADJ, 3, WALL>(maps, out, a, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
         }
         if (!ok) break;
     }
@@ -897,18 +897,25 @@ int layer2d_box_rows() { return kL2CH; }
 int layer2d_box_cols(int prec) { return prec == 32 ? L2Cfg<float>::COLS : L2Cfg<double>::COLS; }
 int layer2d_tile_cols(int prec) { return prec == 32 ? L2Cfg<float>::OUT : L2Cfg<double>::OUT; }
 
-template <typename T, bool ADJ>
-static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st)
+template <typename T, bool ADJ, bool WALL>
+static cudaError_t launch_l2w(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st)
 {
     static bool done = false;
     const size_t sm = layer2d_smem<T>();
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_layer2d<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        cudaError_t e =
+            cudaFuncSetAttribute(k_layer2d<T, ADJ, WALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
         done = true;
     }
-    k_layer2d<T, ADJ><<<grid, 128, sm, st>>>(m, o, a);
+    k_layer2d<T, ADJ, WALL><<<grid, 128, sm, st>>>(m, o, a);
     return cudaGetLastError();
+}
+
+template <typename T, bool ADJ>
+static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st)
+{
+    return a.g.wall ? launch_l2w<T, ADJ, true>(m, o, a, grid, st) : launch_l2w<T, ADJ, false>(m, o, a, grid, st);
 }
 
 int layer2d_grid(int prec, int ntiles, int sm_count)
@@ -1153,7 +1160,7 @@ __global__ void __launch_bounds__(128, MINB) k_interior2d_batch(const Batch2DArg
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, bool WALL>
 __global__ void __launch_bounds__(128, L2Cfg<T>::MINB) k_layer2d_batch(const Batch2DArgs b)
 {
     constexpr int S = L2Cfg<T>::S, WE = L2Cfg<T>::WE;
@@ -1184,10 +1191,10 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB) k_layer2d_batch(const Bat
         const Layer2DArgs la = d.lay;   // local copies: stores to the fields cannot alias them
         bool ok;
         switch (tile.flags & 3) {
-        case 0: ok = layer2d_item<T, ADJ, 0>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
-        case 1: ok = layer2d_item<T, ADJ, 1>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
-        case 2: ok = layer2d_item<T, ADJ, 2>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
-        default: ok = layer2d_item<T, ADJ, 3>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 0: ok = layer2d_item<T, ADJ, 0, WALL>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 1: ok = layer2d_item<T, ADJ, 1, WALL>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        case 2: ok = layer2d_item<T, ADJ, 2, WALL>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
+        default: ok = layer2d_item<T, ADJ, 3, WALL>(maps, out, la, tile, ring, sig_sh[warp], bars[warp], lane, use); break;
         }
         if (!ok) break;
     }
@@ -1202,7 +1209,10 @@ template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct BKernel 
         if (done) return cudaSuccess;
         cudaError_t e = cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_layer2d_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_layer2d_batch<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(layer2d_smem<T>()));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_layer2d_batch<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(layer2d_smem<T>()));
         if (e == cudaSuccess) done = true;
         return e;
@@ -1262,13 +1272,18 @@ cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int g
     return with_b2(prec, v, [&](auto k) { return decltype(k)::launch(a, grid, st, overlap_previous); });
 }
 
-cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, cudaStream_t st)
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, bool wall, cudaStream_t st)
 {
     if (a.ntiles <= 0 || grid <= 0) return cudaSuccess;
     cudaError_t e = with_b2(prec, 0, [](auto k) { return decltype(k)::prep(); });
     if (e != cudaSuccess) return e;
-    if (prec == 32) k_layer2d_batch<float, false><<<grid, 128, layer2d_smem<float>(), st>>>(a);
-    else k_layer2d_batch<double, false><<<grid, 128, layer2d_smem<double>(), st>>>(a);
+    if (prec == 32) {
+        if (wall) k_layer2d_batch<float, false, true><<<grid, 128, layer2d_smem<float>(), st>>>(a);
+        else k_layer2d_batch<float, false, false><<<grid, 128, layer2d_smem<float>(), st>>>(a);
+    } else {
+        if (wall) k_layer2d_batch<double, false, true><<<grid, 128, layer2d_smem<double>(), st>>>(a);
+        else k_layer2d_batch<double, false, false><<<grid, 128, layer2d_smem<double>(), st>>>(a);
+    }
     return cudaGetLastError();
 }
 
