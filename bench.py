@@ -178,6 +178,9 @@ def run_ours(args, ws, rank, local):
     u_dev = torch.from_numpy(u0).to(dev)
     s.set_initial(u_dev)
     variant, tune_table = autotune.tune(s, steps=20, use_cache=not args.retune)
+    one_step = s.one_step_variant
+    from paper_1804_01390_gb300 import _lib as _l
+    tb = _l.pml_get_time_block(s.ctx)
     s.set_initial(u_dev)
     clk = ClockSampler(local)
     clk.start()
@@ -190,10 +193,14 @@ def run_ours(args, ws, rank, local):
     value = pts * K * ws / (ms_max / 1e3) / 1e9
     ms_prof, prof = timed_steps(s, K, 0, ws, profile=True)
     (ms_k, n_k) = prof
-    interior_pts = int(np.prod([n - 2 for n in wl.N]))
-    bytes_per_launch = interior_pts * 4 * 4               # U, V read + written, FP32
+    # vertices one interior launch advances: the layer-free run (n - 2 per axis), shrunk
+    # by 2 at both ends for the two-step kernel, which advances them two steps per launch
+    interior_pts = int(np.prod([n - 2 - (4 if tb == 2 else 0) for n in wl.N]))
+    bytes_per_launch = interior_pts * 4 * 4               # U, V read + written once per launch, FP32
     avg_launch_s = ms_k[0] / max(n_k[0], 1) / 1e3
     achieved = bytes_per_launch / avg_launch_s / 1e9
+    # the same launch counted per point-update at the one-step figure (16 B per update)
+    effective = bytes_per_launch * tb / avg_launch_s / 1e9
     launches = int(n_k.sum())
     layer_share = float(ms_k[1] / max(ms_k.sum(), 1e-30))
 
@@ -205,7 +212,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_e2e:
         from paper_1804_01390_gb300 import _lib
         s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev)
-        _lib.pml_set_variant(s.ctx, variant)
+        autotune.select(s.ctx, variant, one_step)
         u_host = torch.from_numpy(u0).pin_memory()
         out_host = torch.empty_like(u_host).pin_memory()
         s.set_initial(u_host)
@@ -238,7 +245,7 @@ def run_ours(args, ws, rank, local):
         v64 = pts * K64 * ws / (ms64 / 1e3) / 1e9
         m64, n64 = prof64
         t_int = m64[0] / max(n64[0], 1) / 1e3
-        tflops = interior_pts * FP64_FLOP_PER_POINT / t_int / 1e12
+        tflops = int(np.prod([n - 2 for n in wl.N])) * FP64_FLOP_PER_POINT / t_int / 1e12
         fp64 = {"value": v64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
                 "roofline": {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS,
                              "unit": "TFLOP/s", "frac": tflops / NOMINAL_FP64_TFLOPS,
@@ -252,7 +259,7 @@ def run_ours(args, ws, rank, local):
         import torch as _t
         from paper_1804_01390_gb300 import _lib
         s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev, adjoint=True)
-        _lib.pml_set_variant(s.ctx, variant)
+        autotune.select(s.ctx, variant, one_step)
         s.set_initial(_t.from_numpy(u0).to(dev))
         s.adjoint_reset()
         Ka = max(K // 2, 10)
@@ -435,12 +442,16 @@ def run_ours(args, ws, rank, local):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "2D %d^2 interior + 32-cell quadratic PML (T = %d^2), 16 seeded "
                                    "Gaussian pulses, RK4 dt = 0.5h" % (wl.N[0], wl.T[0]), "grid": list(wl.T),
-                       "pml_width": wl.w, "interior_variant": variant, "autotune_ms_per_step": tune_table,
+                       "pml_width": wl.w, "interior_variant": variant, "steps_per_pass": tb,
+                       "autotune_ms_per_step": tune_table,
                        "l2": "inputs larger than L2 (U and V are 272 MB each; 1.09 GB state read + written "
-                             "per step)", "parallelism": "replicas" if ws > 1 else "single GPU"},
+                             "per pass, one pass per %d step%s)" % (tb, "s" if tb > 1 else ""), "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_interior2d<float>", "bytes_per_launch": bytes_per_launch,
+                         "kernel": "k_interior2d_tb2<float>" if tb == 2 else "k_interior2d<float>",
+                         "steps_per_launch": tb, "bytes_per_launch": bytes_per_launch,
+                         "bytes_rule": "16 B per vertex per launch (U, V read and written once)",
+                         "effective_gbs_per_update": effective,
                          "avg_launch_ms": avg_launch_s * 1e3, "layer_time_share": layer_share,
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},

@@ -153,7 +153,13 @@ pml_status pml_set_sources(pml_ctx *ctx, int ns, const int64_t *coords, const do
 pml_status pml_set_receivers(pml_ctx *ctx, int nr, const int64_t *coords, void *trace_buf,
                              int64_t capacity);
 
-/* Advance n RK4 steps (asynchronous). */
+/*
+ * Advance n RK4 steps (asynchronous).  With a two-step kernel variant selected (see
+ * pml_set_variant; 2D FP32 contexts), consecutive steps with no sources and no receiver
+ * row to record advance two per pass (temporal blocking depth 2); the state after each
+ * pair equals that of two single steps up to rounding (the first step's values near the
+ * layer are then formed by the layer's operator form instead of the closed form).
+ */
 pml_status pml_step(pml_ctx *ctx, int64_t n);
 
 /* Copy field PML_FIELD_* of the current state into a dense T-grid (host or device). */
@@ -262,16 +268,21 @@ pml_status pml_profile_read(pml_ctx *ctx, double ms[3], int64_t launches[3]);
 /*
  * Kernel variants and autotuning.  The layer-free (interior) kernel of a 2D context
  * exists in several shapes (columns per lane, rows per TMA box, pipeline depth,
- * resident CTAs per SM); 3D contexts have one.  pml_get_variant reports the current
- * one and how many exist; pml_set_variant selects one (synchronising).
+ * resident CTAs per SM); 3D contexts have one.  Variants 0 .. n1-1 advance one step per
+ * pass; 2D FP32 contexts add variants n1 .. count-1 that advance two steps per pass
+ * (temporal blocking depth 2, see pml_step), selecting one of those keeps the one-step
+ * variant last selected for single steps and the adjoint.  pml_get_variant reports the
+ * current one and how many exist; pml_set_variant selects one (synchronising);
+ * pml_get_time_block reports the steps per pass of the current variant (1 or 2).
  * pml_autotune times every variant for `steps` steps on the current state (sources and
  * receivers are suspended while it runs; the state advances by
- * (steps + 2) * count steps, so tune before pml_set_initial), keeps the fastest, writes
- * its index to *chosen and, if times_ms is not NULL, each variant's milliseconds per step
- * to times_ms[0..count-1].
+ * (steps + 2) * count steps, so tune before pml_set_initial), keeps the fastest (and the
+ * fastest one-step variant for single steps), writes its index to *chosen and, if
+ * times_ms is not NULL, each variant's milliseconds per step to times_ms[0..count-1].
  */
 pml_status pml_get_variant(const pml_ctx *ctx, int *variant, int *count);
 pml_status pml_set_variant(pml_ctx *ctx, int variant);
+pml_status pml_get_time_block(const pml_ctx *ctx, int *depth);
 pml_status pml_autotune(pml_ctx *ctx, int steps, double *times_ms, int *chosen);
 
 /*

@@ -48,7 +48,7 @@ EXPORTED = (
     "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
     "pml_adjoint_read_field", "pml_sigma_gradient", "pml_state_bytes", "pml_save_state", "pml_load_state",
-    "pml_get_variant", "pml_set_variant", "pml_autotune",
+    "pml_get_variant", "pml_set_variant", "pml_get_time_block", "pml_autotune",
     "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
     "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
     "pml_batch_autotune", "pml_batch_profile_enable", "pml_batch_profile_read", "pml_batch_info",
@@ -113,6 +113,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_profile_enable": [P, ctypes.c_int],
         "pml_get_variant": [P, P, P],
         "pml_set_variant": [P, ctypes.c_int],
+        "pml_get_time_block": [P, P],
         "pml_autotune": [P, ctypes.c_int, P, P],
         "pml_norms_dense_static": [ctypes.c_int, P, ctypes.c_int, P, P, P, P, ctypes.c_double, P, P, P],
         "pml_profile_read": [P, P, P],
@@ -264,6 +265,13 @@ def pml_get_variant(ctx):
 
 def pml_set_variant(ctx, variant):
     _check(load().pml_set_variant(ctx, int(variant)), ctx)
+
+
+def pml_get_time_block(ctx):
+    """Steps per pass of the current variant (1, or 2 for a two-step variant)."""
+    d = ctypes.c_int(0)
+    _check(load().pml_get_time_block(ctx, ctypes.byref(d)), ctx)
+    return int(d.value)
 
 
 def pml_autotune(ctx, steps):

@@ -287,6 +287,15 @@ int interior2d_max_blocks_per_sm(int prec, bool adjoint, int v);
 cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *tmU, const CUtensorMap *tmV,
                               void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
                               bool overlap_previous);
+// Two forward steps per pass (temporal blocking depth 2) over the run given in a.xr, a.yr
+// (the layer-free run shrunk by 2 where a layer bounds it); FP32 only (variants() = 0 for
+// FP64).  Its TMA box is 128 columns x interior2d_tb2_box_rows(prec, v) rows.
+int interior2d_tb2_variants(int prec);
+int interior2d_tb2_box_rows(int prec, int v);
+int interior2d_tb2_max_blocks_per_sm(int prec, int v);
+cudaError_t launch_interior2d_tb2(int prec, int v, const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo,
+                                  void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
+                                  bool overlap_previous);
 
 // Layer step of 2D strips (Horner form of the RK4 polynomial with the full operator).
 struct Layer2DArgs {
@@ -307,8 +316,12 @@ int layer2d_grid(int prec, int ntiles, int sm_count);   // CTAs of one layer lau
 int layer2d_box_rows();               // rows of the layer kernel's TMA box
 int layer2d_box_cols(int prec);       // columns of the layer kernel's TMA box (one strip)
 int layer2d_tile_cols(int prec);      // output columns of one layer strip (box minus the halo)
+// overlap_previous: the launch may start while the previous kernel of the stream runs; the
+// kernel waits for that kernel to complete before it reads anything (its inputs may be
+// that kernel's outputs), but the kernel after it may start early
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U,V,Px,Qx,Py,Qy*/,
-                           void *const *out /*[6]*/, const Layer2DArgs &a, int grid, cudaStream_t st);
+                           void *const *out /*[6]*/, const Layer2DArgs &a, int grid, cudaStream_t st,
+                           bool overlap_previous = false);
 
 // Batched 2D step over many independent grids: one interior launch and one layer launch
 // per step for the whole batch.  Per-grid descriptors (tensor maps included) live in device

@@ -37,8 +37,10 @@ struct Plan {
     Geom g{};
     size_t fields[2][8] = {};
     size_t adj[2][8] = {};
+    size_t mid[8] = {};          // two-step blocks (2D FP32): first-step values of the widened frame
+    bool tb2 = false;
     size_t sig[3] = {};
-    size_t tiles = 0, tiles_adj = 0, max_tiles = 0;
+    size_t tiles = 0, tiles_adj = 0, max_tiles = 0, tiles_l1 = 0, tiles_l2 = 0;
     size_t partials = 0, normout = 0, err = 0, queue = 0;
     size_t src_off = 0, src_xyz = 0, src_amp = 0, grad = 0, rec_off = 0;
     size_t total = 0;
@@ -92,10 +94,17 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
     if (flags & PML_FLAG_ADJOINT)
         for (int s = 0; s < 2; ++s)
             for (int f = 0; f < p->nf; ++f) { p->adj[s][f] = off; off += fb; }
+    p->tb2 = p->nd == 2 && interior2d_tb2_variants(prec) > 0;
+    if (p->tb2)
+        for (int f = 0; f < p->nf; ++f) { p->mid[f] = off; off += fb; }
     for (int a = 0; a < p->nd; ++a) { p->sig[a] = off; off += align_up(size_t(p->T[a]) * p->esz, kAlign); }
     p->max_tiles = tile_bound(p->nd, prec, p->T);
     p->tiles = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
     p->tiles_adj = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+    if (p->tb2) {
+        p->tiles_l1 = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+        p->tiles_l2 = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+    }
     p->partials = off; off += align_up(size_t(kNormBlocks) * kNormVals * sizeof(double), kAlign);
     p->normout = off; off += kAlign;
     p->err = off; off += kAlign;
@@ -133,8 +142,9 @@ struct pml_ctx {
     int class_off[9] = {}, class_off_adj[9] = {};
     double *dpart = nullptr, *dnorm = nullptr, *dgrad = nullptr;
     DeviceError *derr = nullptr;
-    int *dqueue = nullptr;              // work counters: interior fwd 0/1, adj 2/3; 2D layer fwd 4/5, adj 6/7
-    int64_t launches_fwd = 0, launches_adj = 0, launches_layer_fwd = 0, launches_layer_adj = 0;
+    int *dqueue = nullptr;              // work counters: interior fwd 0/1, adj 2/3; 2D layer fwd 4/5, adj 6/7,
+                                        // second layer pass of a two-step block 8/9
+    int64_t launches_fwd = 0, launches_adj = 0, launches_layer_fwd = 0, launches_layer_adj = 0, launches_layer2 = 0;
     int ns = 0, nr = 0;
     int64_t *dsrc_off = nullptr, *drec_off = nullptr;
     int32_t *dsrc_xyz = nullptr;
@@ -146,7 +156,16 @@ struct pml_ctx {
     bool adj_ready = false;
     CUtensorMap tm_int[2][2], tm_lay[2][8], tm_int_adj[2][2], tm_lay_adj[2][8];
     int grid_int = 0, grid_int_adj = 0, sm_count = 0;
-    int ivar = 0;                       // interior kernel variant (2D)
+    int ivar = 0;                       // interior kernel variant (2D, one step per pass)
+    // temporal blocking depth 2 (2D FP32): forward steps without sources or receiver rows
+    // advance two at a time (layer pass 1 on the frame widened by 6 into mid, layer pass 2
+    // on the frame widened by 2, two-step interior kernel on the run shrunk by 2)
+    int tb = 1, tbvar = 0, grid_tb = 0;
+    void *mid[8] = {};
+    CUtensorMap tm_mid[8], tm_tb[2][2];
+    LayerTile *dtiles_l1 = nullptr, *dtiles_l2 = nullptr;
+    int ntiles_l1 = 0, ntiles_l2 = 0;
+    Range ir_tb[3];
     // kernel timing (pml_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs
@@ -252,6 +271,14 @@ Range layer_free_run(const std::vector<double> &s, int64_t centre, int lo_off, i
     while (lo - 1 >= 0 && ok(lo - 1)) --lo;
     while (hi + 1 <= T - 1 && ok(hi + 1)) ++hi;
     return {lo, hi};
+}
+
+// The run shrunk by k vertices at both ends; a run that is the whole periodic axis (no
+// layer on it) has no ends and stays whole.
+Range shrink_run(const Range &r, int64_t T, int64_t k)
+{
+    if (r.lo == 0 && r.hi == T - 1) return r;
+    return {r.lo + k, r.hi - k};
 }
 
 void build_layout(pml_ctx *c)
@@ -584,6 +611,55 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
     return PML_OK;
 }
 
+// Two forward steps from buffers `p` to buffers `1 - p` (temporal blocking depth 2, 2D):
+//   layer pass 1: step n+1 on the frame of the run shrunk by 6, fld[p] -> mid;
+//   layer pass 2: step n+2 on the frame of the run shrunk by 2, mid -> fld[1-p]; launched
+//                 early, it waits for pass 1 before reading;
+//   interior:     steps n+1, n+2 in one pass on the run shrunk by 2, fld[p] -> fld[1-p];
+//                 launched while pass 2 runs, it completes only after pass 2.
+pml_status enqueue_double_step(pml_ctx *c, int p)
+{
+    const int q = 1 - p;
+    StepCoef k;
+    step_coef(c, false, &k);
+    Layer2DArgs l{};
+    l.g = c->g; l.k = layer_const(c);
+    l.sig[0] = c->dsig[0]; l.sig[1] = c->dsig[1];
+    l.err = c->derr;
+    l.tiles = c->dtiles_l1; l.ntiles = c->ntiles_l1;
+    l.queue = c->dqueue + 4;
+    l.parity = int(c->launches_layer_fwd & 1);
+    if (l.ntiles > 0) ++c->launches_layer_fwd;
+    long pi = prof_begin(c, 1);
+    cudaError_t e = launch_layer2d(c->prec, false, c->tm_lay[p], c->mid, l, layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st);
+    prof_end(c, pi);
+    if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel (pass 1)");
+    const bool pass1 = l.ntiles > 0;
+    l.tiles = c->dtiles_l2; l.ntiles = c->ntiles_l2;
+    l.queue = c->dqueue + 8;
+    l.parity = int(c->launches_layer2 & 1);
+    if (l.ntiles > 0) ++c->launches_layer2;
+    pi = prof_begin(c, 1);
+    e = launch_layer2d(c->prec, false, c->tm_mid, c->fld[q], l, layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st,
+                       pass1 && !c->prof_on);
+    prof_end(c, pi);
+    if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel (pass 2)");
+    Interior2DArgs a{};
+    a.g = c->g; a.xr = c->ir_tb[0]; a.yr = c->ir_tb[1]; a.c = k; a.err = c->derr;
+    a.queue = c->dqueue + 0;
+    a.parity = int(c->launches_fwd & 1);
+    pi = prof_begin(c, 0);
+    e = launch_interior2d_tb2(c->prec, c->tbvar, &c->tm_tb[p][0], &c->tm_tb[p][1], c->fld[q][0], c->fld[q][1], a,
+                              c->grid_tb, c->st, (pass1 || l.ntiles > 0) && !c->prof_on);
+    prof_end(c, pi);
+    if (e != cudaSuccess) return cuda_fail(c, e, "interior 2D kernel (two steps)");
+    if (!range_empty(a.xr) && !range_empty(a.yr)) ++c->launches_fwd;
+    return PML_OK;
+}
+
+int one_step_variants(const pml_ctx *c) { return c->nd == 2 ? interior2d_variants(c->prec) : 1; }
+int two_step_variants(const pml_ctx *c) { return c->plan.tb2 ? interior2d_tb2_variants(c->prec) : 0; }
+
 // Grid sizes of the interior kernels for the current variant: all resident CTAs.
 pml_status interior_grids(pml_ctx *c)
 {
@@ -595,6 +671,24 @@ pml_status interior_grids(pml_ctx *c)
         return fail(c, PML_ECUDA, "interior kernel cannot be resident (shared memory / registers)");
     c->grid_int = bps * c->sm_count;
     c->grid_int_adj = bpa * c->sm_count;
+    if (c->plan.tb2) {
+        const int bt = interior2d_tb2_max_blocks_per_sm(c->prec, c->tbvar);
+        if (bt <= 0) return fail(c, PML_ECUDA, "two-step interior kernel cannot be resident (shared memory / registers)");
+        c->grid_tb = bt * c->sm_count;
+    }
+    return PML_OK;
+}
+
+// Tensor maps of the two-step interior kernel (U, V of both ping-pong halves) for its
+// current variant's box.
+pml_status encode_tb_maps(pml_ctx *c)
+{
+    if (!c->plan.tb2) return PML_OK;
+    uint32_t box[3] = {128u, uint32_t(interior2d_tb2_box_rows(c->prec, c->tbvar)), 1};
+    pml_status s;
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 2; ++f)
+            if ((s = encode_map(c, &c->tm_tb[p][f], c->fld[p][f], box)) != PML_OK) return s;
     return PML_OK;
 }
 
@@ -708,6 +802,11 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             c->fld[p][f] = c->ws + plan.fields[p][f];
             if (flags & PML_FLAG_ADJOINT) c->adj[p][f] = c->ws + plan.adj[p][f];
         }
+    if (plan.tb2) {
+        for (int f = 0; f < c->nf; ++f) c->mid[f] = c->ws + plan.mid[f];
+        c->dtiles_l1 = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l1);
+        c->dtiles_l2 = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l2);
+    }
     for (int a = 0; a < c->nd; ++a) c->dsig[a] = c->ws + plan.sig[a];
     c->dtiles = reinterpret_cast<LayerTile *>(c->ws + plan.tiles);
     c->dtiles_adj = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_adj);
@@ -725,7 +824,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     {
         cudaError_t e = cudaMemsetAsync(c->ws, 0, plan.sig[0], c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(DeviceError), c->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->dqueue, 0, 8 * sizeof(int), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->dqueue, 0, 16 * sizeof(int), c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->dgrad, 0, kMaxSources * sizeof(double), c->st);
         if (e != cudaSuccess) { cuda_fail(c, e, "clear workspace"); return bail(PML_ECUDA); }
     }
@@ -753,6 +852,29 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         if (!tf.empty()) e = cudaMemcpy(c->dtiles, tf.data(), tf.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !ta.empty() && (flags & PML_FLAG_ADJOINT))
             e = cudaMemcpy(c->dtiles_adj, ta.data(), ta.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cuda_fail(c, e, "upload tiles"); return bail(PML_ECUDA); }
+    }
+    // two-step blocks: the second pass writes the frame of the run shrunk by 2, from first-
+    // step values the first pass writes on the frame of the run shrunk by 6 (4 more: the
+    // reach of one layer step)
+    if (plan.tb2) {
+        Range r6[3], r2[3];
+        for (int a = 0; a < 3; ++a) {
+            r6[a] = shrink_run(c->ir[a], c->T[a], 6);
+            r2[a] = c->ir_tb[a] = shrink_run(c->ir[a], c->T[a], 2);
+        }
+        int dummy[9];
+        std::vector<LayerTile> t1 = build_tiles(c, r6, dummy), t2 = build_tiles(c, r2, dummy);
+        if (t1.size() > plan.max_tiles || t2.size() > plan.max_tiles) {
+            fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
+            return bail(PML_ENOMEM);
+        }
+        c->ntiles_l1 = int(t1.size());
+        c->ntiles_l2 = int(t2.size());
+        cudaError_t e = cudaSuccess;
+        if (!t1.empty()) e = cudaMemcpy(c->dtiles_l1, t1.data(), t1.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !t2.empty())
+            e = cudaMemcpy(c->dtiles_l2, t2.data(), t2.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cuda_fail(c, e, "upload tiles"); return bail(PML_ECUDA); }
     }
     // tensor maps
@@ -783,6 +905,12 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             }
             for (int f = c->nf; f < 8; ++f) { c->tm_lay[p][f] = c->tm_lay[p][0]; c->tm_lay_adj[p][f] = c->tm_lay_adj[p][0]; }
         }
+        if (plan.tb2) {
+            for (int f = 0; f < c->nf; ++f)
+                if ((s = encode_map(c, &c->tm_mid[f], c->mid[f], box_lay)) != PML_OK) return bail(s);
+            for (int f = c->nf; f < 8; ++f) c->tm_mid[f] = c->tm_mid[0];
+            if ((s = encode_tb_maps(c)) != PML_OK) return bail(s);
+        }
     }
     if ((s = interior_grids(c)) != PML_OK) return bail(s);
     cudaError_t e = cudaStreamSynchronize(c->st);
@@ -794,16 +922,26 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
 pml_status pml_set_variant(pml_ctx *c, int variant)
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
-    const int n = c->nd == 2 ? interior2d_variants(c->prec) : 1;
+    const int n1 = one_step_variants(c), n = n1 + two_step_variants(c);
     if (variant < 0 || variant >= n) return fail(c, PML_EINVAL, "variant %d not in [0, %d)", variant, n);
     PML_CU(c, cudaStreamSynchronize(c->st), "stream synchronize");
-    const int old = c->ivar;
-    c->ivar = variant;
+    const int old_ivar = c->ivar, old_tb = c->tb, old_tbvar = c->tbvar;
+    if (variant < n1) {
+        c->ivar = variant;
+        c->tb = 1;
+    } else {   // the one-step variant stays as it is: it serves single steps and the adjoint
+        c->tb = 2;
+        c->tbvar = variant - n1;
+    }
     pml_status s = encode_interior_maps(c);
+    if (s == PML_OK) s = encode_tb_maps(c);
     if (s == PML_OK) s = interior_grids(c);
     if (s != PML_OK) {
-        c->ivar = old;
+        c->ivar = old_ivar;
+        c->tb = old_tb;
+        c->tbvar = old_tbvar;
         encode_interior_maps(c);
+        encode_tb_maps(c);
         interior_grids(c);
     }
     return s;
@@ -812,8 +950,16 @@ pml_status pml_set_variant(pml_ctx *c, int variant)
 pml_status pml_get_variant(const pml_ctx *c, int *variant, int *count)
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
-    if (variant) *variant = c->ivar;
-    if (count) *count = c->nd == 2 ? interior2d_variants(c->prec) : 1;
+    if (variant) *variant = c->tb == 2 ? one_step_variants(c) + c->tbvar : c->ivar;
+    if (count) *count = one_step_variants(c) + two_step_variants(c);
+    return PML_OK;
+}
+
+pml_status pml_get_time_block(const pml_ctx *c, int *depth)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (!depth) return fail(const_cast<pml_ctx *>(c), PML_EINVAL, "depth is NULL");
+    *depth = c->tb;
     return PML_OK;
 }
 
@@ -821,12 +967,12 @@ pml_status pml_autotune(pml_ctx *c, int steps, double *times_ms, int *chosen)
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (steps < 1) return fail(c, PML_EINVAL, "steps must be >= 1");
-    const int n = c->nd == 2 ? interior2d_variants(c->prec) : 1;
+    const int n1 = one_step_variants(c), n = n1 + two_step_variants(c);
     cudaEvent_t e0, e1;
     PML_CU(c, cudaEventCreate(&e0), "event");
     PML_CU(c, cudaEventCreate(&e1), "event");
-    int best = c->ivar;
-    double best_ms = 1e300;
+    int best = c->tb == 2 ? n1 + c->tbvar : c->ivar, best1 = c->ivar;
+    double best_ms = 1e300, best1_ms = 1e300;
     pml_status st = PML_OK;
     const int ns = c->ns, nr = c->nr;
     c->ns = 0;   // time the step alone: no sources, no receiver rows consumed
@@ -843,6 +989,8 @@ pml_status pml_autotune(pml_ctx *c, int steps, double *times_ms, int *chosen)
         const double per = double(ms) / steps;
         if (times_ms) times_ms[v] = per;
         if (per < best_ms) { best_ms = per; best = v; }
+        if (v < n1 && per < best1_ms) { best1_ms = per; best1 = v; }
+        if (v == n1 - 1 && (st = pml_set_variant(c, best1)) != PML_OK) break;   // kept for single steps
     }
     c->ns = ns;
     c->nr = nr;
@@ -974,6 +1122,15 @@ pml_status pml_step(pml_ctx *c, int64_t n)
     const PointArgs pa = point_args(c);
     for (int64_t k = 0; k < n; ++k) {
         const int p = c->cur, q = 1 - p;
+        // two steps per pass where nothing has to happen between the two
+        if (c->tb == 2 && n - k >= 2 && c->ns == 0 && !(c->nr > 0 && c->trace_k < c->trace_cap)) {
+            pml_status s = enqueue_double_step(c, p);
+            if (s != PML_OK) return s;
+            c->cur = q;
+            c->step += 2;
+            ++k;
+            continue;
+        }
         pml_status s = enqueue_step(c, false, p);
         if (s != PML_OK) return s;
         void *row = nullptr;

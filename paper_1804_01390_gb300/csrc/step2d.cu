@@ -244,6 +244,195 @@ __device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUt
 }
 
 // ------------------------------------------------------------------------------------
+// Temporal blocking, depth 2: two forward RK4 steps in one pass over HBM.
+//
+// The layer-free run shrunk by 2 vertices per side is advanced by two closed-form steps:
+// the first step's values are needed two vertices beyond the outputs, and the closed form
+// holds there (the first step only reads the run itself plus its halo).  One warp streams
+// its 128-column strip as before, but the rows of the first step (two rows behind the
+// input) feed a second copy of the one-step pipeline, whose rows (two more behind) are the
+// outputs.  Lanes 0 and 31 carry exactly the 4-column halo of the two steps, so a strip
+// still has 120 outputs; each output row needs 4 input rows above and below.  Every
+// vertex is read and written once per two steps.
+// ------------------------------------------------------------------------------------
+
+// Three consecutive rows of U, V and of their 5-point differences, for one step.
+template <typename T, int NH> struct StepRing {
+    typename Pair<T>::P u[3][NH], v[3][NH], du[3][NH], dv[3][NH];
+    T ul[3], ur[3], vl[3], vr[3], dul[3], dur[3], dvl[3], dvr[3];
+};
+
+template <typename T> struct FwdCoefP {
+    typename Pair<T>::P A1, A2, A3, A4, B2, B3, B4, B5;
+};
+
+// Row q of one step's input sits in R.u[j % 3], R.v[j % 3] (j = q mod 3 after unrolling):
+// its edge columns go to the neighbouring lanes; with d1 the differences of row q-1
+// follow, with d2 the step's new values of row q-2 are returned in uo, vo.  Same
+// arithmetic, in the same order, as the forward case of interior2d_seg.
+template <typename T, int NH>
+__device__ __forceinline__ void ring_push(StepRing<T, NH> &R, const FwdCoefP<T> &k, int j, bool d1, bool d2,
+                                          typename Pair<T>::P (&uo)[NH], typename Pair<T>::P (&vo)[NH])
+{
+    using M = Pair<T>;
+    using PT = typename M::P;
+    const int J0 = j % 3, J1 = (j + 2) % 3, J2 = (j + 1) % 3;   // rows q, q-1, q-2
+    R.ul[J0] = __shfl_up_sync(0xffffffffu, R.u[J0][NH - 1].y, 1);
+    R.ur[J0] = __shfl_down_sync(0xffffffffu, R.u[J0][0].x, 1);
+    R.vl[J0] = __shfl_up_sync(0xffffffffu, R.v[J0][NH - 1].y, 1);
+    R.vr[J0] = __shfl_down_sync(0xffffffffu, R.v[J0][0].x, 1);
+    if (d1) {
+        diff5p<T, NH>(R.u[J1], R.ul[J1], R.ur[J1], R.u[J2], R.u[J0], R.du[J1]);
+        diff5p<T, NH>(R.v[J1], R.vl[J1], R.vr[J1], R.v[J2], R.v[J0], R.dv[J1]);
+        R.dul[J1] = __shfl_up_sync(0xffffffffu, R.du[J1][NH - 1].y, 1);
+        R.dur[J1] = __shfl_down_sync(0xffffffffu, R.du[J1][0].x, 1);
+        R.dvl[J1] = __shfl_up_sync(0xffffffffu, R.dv[J1][NH - 1].y, 1);
+        R.dvr[J1] = __shfl_down_sync(0xffffffffu, R.dv[J1][0].x, 1);
+    }
+    if (d2) {
+        PT d2u[NH], d2v[NH];
+        diff5p<T, NH>(R.du[J2], R.dul[J2], R.dur[J2], R.du[J0], R.du[J1], d2u);
+        diff5p<T, NH>(R.dv[J2], R.dvl[J2], R.dvr[J2], R.dv[J0], R.dv[J1], d2v);
+#pragma unroll
+        for (int c = 0; c < NH; ++c) {
+            const PT uc = R.u[J2][c], vc = R.v[J2][c], duc = R.du[J2][c], dvc = R.dv[J2][c];
+            uo[c] = M::add(uc, M::fma(k.A1, vc, M::fma(k.A2, duc, M::fma(k.A3, dvc, M::mul(k.A4, d2u[c])))));
+            vo[c] = M::add(vc, M::fma(k.B2, duc, M::fma(k.B3, dvc, M::fma(k.B4, d2u[c], M::mul(k.B5, d2v[c])))));
+        }
+    }
+}
+
+// One work item of the two-step kernel: output rows y0 .. y0+cnt-1 of the strip starting
+// at column xs (ring and barrier conventions as in interior2d_seg).
+template <typename T, int NC, int CH, int S>
+__device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CUtensorMap *tmV, T *__restrict__ Uo,
+                                                T *__restrict__ Vo, const Interior2DArgs &a, int64_t xs, int64_t y0,
+                                                int cnt, unsigned char *wbase, uint64_t *bars, int lane,
+                                                uint32_t &use)
+{
+    using M = Pair<T>;
+    using PT = typename M::P;
+    constexpr int NH = NC / 2;
+    constexpr int ROW = 32 * NC;
+    constexpr uint32_t FIELD_BYTES = CH * ROW * sizeof(T);
+    constexpr uint32_t STAGE_BYTES = 2 * FIELD_BYTES;
+    static_assert(NC == 4 && CH % 3 == 0, "4 columns per lane; ring positions repeat every 3 rows");
+    const Geom &g = a.g;
+    const StepCoefT<T> &kc = coef_of<T>(a.c);
+    const FwdCoefP<T> k{M::mk(kc.a1, kc.a1), M::mk(kc.a2, kc.a2), M::mk(kc.a3, kc.a3), M::mk(kc.a4, kc.a4),
+                        M::mk(kc.b2, kc.b2), M::mk(kc.b3, kc.b3), M::mk(kc.b4, kc.b4), M::mk(kc.b5, kc.b5)};
+    const int n_in = cnt + 8;
+    const int nch = (n_in + CH - 1) / CH;
+    const int32_t tx = int32_t(xs - NC + G);
+    const int32_t ty = int32_t(y0 - 4 + G);
+
+    if (lane == 0) {
+        fence_proxy_async();   // earlier generic reads of the ring before async writes
+        const int npro = nch < S ? nch : S;
+        for (int c = 0; c < npro; ++c) {
+            const int slot = (use + c) % S;
+            unsigned char *dst = wbase + slot * STAGE_BYTES;
+            mbar_arrive_expect_tx(&bars[slot], STAGE_BYTES);
+            tma_load_2d(dst, tmU, tx, ty + c * CH, &bars[slot]);
+            tma_load_2d(dst + FIELD_BYTES, tmV, tx, ty + c * CH, &bars[slot]);
+        }
+    }
+    __syncwarp();
+
+    const int64_t x0 = xs - NC + NC * lane;
+    const bool out_lane = lane >= 1 && lane <= 30;
+    const bool seg_vec = out_lane && x0 >= a.xr.lo && x0 + NC - 1 <= a.xr.hi && x0 >= G &&
+                         x0 + NC - 1 < g.T[0] - G && y0 >= G && y0 + cnt <= g.T[1] - G;
+    T *const pU = Uo + g.origin + (y0 - 8) * g.P + x0;   // output row of input row q: pU + q P
+    T *const pV = Vo + g.origin + (y0 - 8) * g.P + x0;
+    StepRing<T, NH> RA, RB;
+
+    // input row q at ring position j; `guard`: the first boxes (stages start at rows 2, 4,
+    // 6, 8) and the last (rows past the input)
+    auto row = [&](const T *sU, const T *sV, int j, int q, bool guard) {
+        if (guard && q >= n_in) return;
+        const int J0 = j % 3;
+#pragma unroll
+        for (int c = 0; c < NH; c += 2) {
+            const V4<T> tu = lds4(sU + 2 * c), tv = lds4(sV + 2 * c);
+            RA.u[J0][c] = M::mk(tu.x, tu.y);
+            RA.u[J0][c + 1] = M::mk(tu.z, tu.w);
+            RA.v[J0][c] = M::mk(tv.x, tv.y);
+            RA.v[J0][c + 1] = M::mk(tv.z, tv.w);
+        }
+        PT u1[NH], v1[NH];
+        const bool a2 = !guard || q >= 4;
+        ring_push<T, NH>(RA, k, j, !guard || q >= 2, a2, u1, v1);
+        if (!a2) return;
+        const int jb = j + 2;   // first-step row q-2 is row q-4 of the second step's input
+#pragma unroll
+        for (int c = 0; c < NH; ++c) {
+            RB.u[jb % 3][c] = u1[c];
+            RB.v[jb % 3][c] = v1[c];
+        }
+        PT uo[NH], vo[NH];
+        const bool b2 = !guard || q >= 8;
+        ring_push<T, NH>(RB, k, jb, !guard || q >= 6, b2, uo, vo);
+        if (!b2) return;
+        if (seg_vec) {
+            T *ru = pU + int64_t(q) * g.P, *rv = pV + int64_t(q) * g.P;
+#pragma unroll
+            for (int c = 0; c < NH; c += 2) {
+                stg4(ru + 2 * c, V4<T>{uo[c].x, uo[c].y, uo[c + 1].x, uo[c + 1].y});
+                stg4(rv + 2 * c, V4<T>{vo[c].x, vo[c].y, vo[c + 1].x, vo[c + 1].y});
+            }
+        } else if (out_lane) {
+            const int64_t r = y0 + q - 8;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int64_t x = x0 + c;
+                if (x >= a.xr.lo && x <= a.xr.hi) {
+                    const T vu = (c & 1) ? uo[c >> 1].y : uo[c >> 1].x;
+                    const T vv = (c & 1) ? vo[c >> 1].y : vo[c >> 1].x;
+                    if (x >= G && x < g.T[0] - G && r >= G && r < g.T[1] - G) {
+                        Uo[g.origin + r * g.P + x] = vu;
+                        Vo[g.origin + r * g.P + x] = vv;
+                    } else {
+                        store_wrapped(Uo, g, x, r, 0, vu);
+                        store_wrapped(Vo, g, x, r, 0, vv);
+                    }
+                }
+            }
+        }
+    };
+
+    for (int c = 0; c < nch; ++c) {
+        const uint32_t uu = use + c;
+        const int slot = uu % S;
+        if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 6)) {
+            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2)
+                mbar_wait(&bars[(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0, kDrainLimitNs);
+            return false;
+        }
+        const T *sU = reinterpret_cast<const T *>(wbase + slot * STAGE_BYTES) + NC * lane;
+        const T *sV = sU + CH * ROW;
+        if (c * CH < 8 || c == nch - 1) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) row(sU + j * ROW, sV + j * ROW, j, c * CH + j, true);
+        } else {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) row(sU + j * ROW, sV + j * ROW, j, c * CH + j, false);
+        }
+        __syncwarp();
+        if (lane == 0 && c + S < nch) {
+            fence_proxy_async();
+            unsigned char *dst = wbase + slot * STAGE_BYTES;
+            mbar_arrive_expect_tx(&bars[slot], STAGE_BYTES);
+            tma_load_2d(dst, tmU, tx, ty + (c + S) * CH, &bars[slot]);
+            tma_load_2d(dst + FIELD_BYTES, tmV, tx, ty + (c + S) * CH, &bars[slot]);
+        }
+    }
+    __syncwarp();
+    use += uint32_t(nch);
+    return true;
+}
+
+// ------------------------------------------------------------------------------------
 // Layer frame: Horner form with the full operator of Eq. 3 (or its transpose), streamed
 // down the rows by independent warps.
 //
@@ -870,6 +1059,9 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB)
         for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
         fence_mbar_init();
     }
+    // launched early (second layer pass of a two-step block): the inputs are the previous
+    // kernel's outputs; a no-op for a launch without programmatic overlap
+    wait_prerequisite_grid();
     __syncwarp();
     T *ring = smem + warp * WE;
     uint32_t use = 0;
@@ -898,7 +1090,8 @@ int layer2d_box_cols(int prec) { return prec == 32 ? L2Cfg<float>::COLS : L2Cfg<
 int layer2d_tile_cols(int prec) { return prec == 32 ? L2Cfg<float>::OUT : L2Cfg<double>::OUT; }
 
 template <typename T, bool ADJ, bool WALL>
-static cudaError_t launch_l2w(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st)
+static cudaError_t launch_l2w(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st,
+                              bool overlap)
 {
     static bool done = false;
     const size_t sm = layer2d_smem<T>();
@@ -908,14 +1101,19 @@ static cudaError_t launch_l2w(const Maps6 &m, const Out6 &o, const Layer2DArgs &
         if (e != cudaSuccess) return e;
         done = true;
     }
-    k_layer2d<T, ADJ, WALL><<<grid, 128, sm, st>>>(m, o, a);
-    return cudaGetLastError();
+    if (!overlap) {
+        k_layer2d<T, ADJ, WALL><<<grid, 128, sm, st>>>(m, o, a);
+        return cudaGetLastError();
+    }
+    return launch_pdl(k_layer2d<T, ADJ, WALL>, grid, 128, sm, st, true, m, o, a);
 }
 
 template <typename T, bool ADJ>
-static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st)
+static cudaError_t launch_l2(const Maps6 &m, const Out6 &o, const Layer2DArgs &a, int grid, cudaStream_t st,
+                             bool overlap)
 {
-    return a.g.wall ? launch_l2w<T, ADJ, true>(m, o, a, grid, st) : launch_l2w<T, ADJ, false>(m, o, a, grid, st);
+    return a.g.wall ? launch_l2w<T, ADJ, true>(m, o, a, grid, st, overlap)
+                    : launch_l2w<T, ADJ, false>(m, o, a, grid, st, overlap);
 }
 
 int layer2d_grid(int prec, int ntiles, int sm_count)
@@ -926,7 +1124,7 @@ int layer2d_grid(int prec, int ntiles, int sm_count)
 }
 
 cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *const *outp, const Layer2DArgs &a,
-                           int grid, cudaStream_t st)
+                           int grid, cudaStream_t st, bool overlap_previous)
 {
     if (a.ntiles <= 0 || grid <= 0) return cudaSuccess;
     Maps6 m;
@@ -935,8 +1133,10 @@ cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm, void *
         m.m[f] = tm[f];
         o.p[f] = outp[f];
     }
-    if (prec == 32) return adjoint ? launch_l2<float, true>(m, o, a, grid, st) : launch_l2<float, false>(m, o, a, grid, st);
-    return adjoint ? launch_l2<double, true>(m, o, a, grid, st) : launch_l2<double, false>(m, o, a, grid, st);
+    const bool ov = overlap_previous;
+    if (prec == 32)
+        return adjoint ? launch_l2<float, true>(m, o, a, grid, st, ov) : launch_l2<float, false>(m, o, a, grid, st, ov);
+    return adjoint ? launch_l2<double, true>(m, o, a, grid, st, ov) : launch_l2<double, false>(m, o, a, grid, st, ov);
 }
 
 template <typename T, bool ADJ, int NC, int CH, int S, int MINB>
@@ -1096,6 +1296,123 @@ cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *
     return adjoint ? with_i2<true>(prec, v, go) : with_i2<false>(prec, v, go);
 }
 
+// Two-step interior kernel: persistent CTAs of 4 warps take ROWS-row strip segments of
+// the shrunk run from the work queue, as k_interior2d does.
+template <typename T, int NC, int CH, int S, int MINB, int ROWS>
+__global__ void __launch_bounds__(128, MINB)
+    k_interior2d_tb2(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
+                     T *__restrict__ Uo, T *__restrict__ Vo, const Interior2DArgs a)
+{
+    constexpr size_t WB = size_t(S) * 2 * CH * 32 * NC * sizeof(T);
+    __shared__ __align__(8) uint64_t bars[4][S];
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem + warp * WB;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.queue[1 - a.parity] = 0;
+    if (lane == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmV);
+        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t use = 0;
+    const int64_t xs0 = a.xr.lo & ~int64_t(3);
+    const int64_t nrows = a.yr.hi - a.yr.lo + 1;
+    const int rblocks = int((nrows + ROWS - 1) / ROWS);
+    const int nstrips = int((a.xr.hi - xs0) / (30 * NC) + 1);
+    const int n_items = nstrips * rblocks;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&a.queue[a.parity], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int st = item / rblocks, rb = item - st * rblocks;
+        const int64_t y0 = a.yr.lo + int64_t(rb) * ROWS;
+        const int64_t rem = a.yr.hi - y0 + 1;
+        if (!interior2d_seg2<T, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(30 * NC) * st, y0,
+                                           int(rem < ROWS ? rem : ROWS), wbase, bars[warp], lane, use))
+            break;
+    }
+    // finish only after the layer kernels of the same two steps (launched before this one)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct I2TKernel {
+    static constexpr size_t smem() { return size_t(4) * S * 2 * CH * 32 * NC * sizeof(T) + 128; }
+    static cudaError_t prep()
+    {
+        static bool done = false;
+        if (done) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(k_interior2d_tb2<T, NC, CH, S, MINB, ROWS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e == cudaSuccess) done = true;
+        return e;
+    }
+    static int occupancy()
+    {
+        if (prep() != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d_tb2<T, NC, CH, S, MINB, ROWS>, 128,
+                                                          smem()) != cudaSuccess)
+            return 0;
+        return n;
+    }
+    static cudaError_t launch(const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo, void *Vo,
+                              const Interior2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+    {
+        cudaError_t e = prep();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = overlap_previous ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, k_interior2d_tb2<T, NC, CH, S, MINB, ROWS>, *tmU, *tmV, (T *)Uo, (T *)Vo, a);
+    }
+};
+
+// Two-step variants (FP32 only: FP64 is bound by its arithmetic, not by HBM, so a second
+// step per pass gains nothing there): rows per TMA box, ring stages, resident CTAs per
+// SM, rows per work item.
+struct I2TVar {
+    int ch, s, minb, rows;
+};
+constexpr I2TVar kI2TVars32[] = {{6, 4, 2, 128}, {6, 3, 2, 128}, {3, 6, 2, 128}};
+constexpr int kNI2TVars32 = sizeof(kI2TVars32) / sizeof(I2TVar);
+
+template <typename F> static auto with_i2t(int v, F &&f)
+{
+    switch (v) {
+    case 0: return f(I2TKernel<float, 4, 6, 4, 2, 128>{});
+    case 1: return f(I2TKernel<float, 4, 6, 3, 2, 128>{});
+    default: return f(I2TKernel<float, 4, 3, 6, 2, 128>{});
+    }
+}
+
+int interior2d_tb2_variants(int prec) { return prec == 32 ? kNI2TVars32 : 0; }
+int interior2d_tb2_box_rows(int prec, int v) { return prec == 32 ? kI2TVars32[v].ch : 0; }
+int interior2d_tb2_max_blocks_per_sm(int prec, int v)
+{
+    if (prec != 32) return 0;
+    return with_i2t(v, [](auto k) { return decltype(k)::occupancy(); });
+}
+
+cudaError_t launch_interior2d_tb2(int prec, int v, const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo, void *Vo,
+                                  const Interior2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+{
+    if (prec != 32 || v < 0 || v >= kNI2TVars32) return cudaErrorInvalidValue;
+    if (a.xr.lo > a.xr.hi || a.yr.lo > a.yr.hi || grid <= 0) return cudaSuccess;
+    return with_i2t(v, [&](auto k) { return decltype(k)::launch(tmU, tmV, Uo, Vo, a, grid, st, overlap_previous); });
+}
+
 // ------------------------------------------------------------------------------------
 // Batched 2D step: the per-item code above, with the grid of each work item read from a
 // descriptor table in device memory.  Interior items of all grids form one queue (the
@@ -1174,6 +1491,9 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB) k_layer2d_batch(const Bat
         for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
         fence_mbar_init();
     }
+    // launched early (second layer pass of a two-step block): the inputs are the previous
+    // kernel's outputs; a no-op for a launch without programmatic overlap
+    wait_prerequisite_grid();
     __syncwarp();
     T *ring = smem + warp * WE;
     uint32_t use = 0;
