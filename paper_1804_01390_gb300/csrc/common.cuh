@@ -289,9 +289,10 @@ cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *
                               bool overlap_previous);
 // Two forward steps per pass (temporal blocking depth 2) over the run given in a.xr, a.yr
 // (the layer-free run shrunk by 2 where a layer bounds it); FP32 only (variants() = 0 for
-// FP64).  Its TMA box is 128 columns x interior2d_tb2_box_rows(prec, v) rows.
+// FP64).  Its TMA box is interior2d_tb2_box_cols(prec, v) x interior2d_tb2_box_rows(prec, v).
 int interior2d_tb2_variants(int prec);
 int interior2d_tb2_box_rows(int prec, int v);
+int interior2d_tb2_box_cols(int prec, int v);
 int interior2d_tb2_max_blocks_per_sm(int prec, int v);
 cudaError_t launch_interior2d_tb2(int prec, int v, const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo,
                                   void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
@@ -312,6 +313,8 @@ struct Layer2DArgs {
 // 4 columns per side) by a run of rows, taken by the warps from a work queue
 constexpr int kLayer2BandRows = 64;  // most output rows of one item of the y band
 constexpr int kLayer2SlabRows = 32;  // most output rows of one item of an x slab
+constexpr int kLayer2BandRowsTB = 32;  // the same for the frames of two-step blocks
+constexpr int kLayer2SlabRowsTB = 24;
 int layer2d_grid(int prec, int ntiles, int sm_count);   // CTAs of one layer launch (warps loop over items)
 int layer2d_box_rows();               // rows of the layer kernel's TMA box
 int layer2d_box_cols(int prec);       // columns of the layer kernel's TMA box (one strip)

@@ -66,7 +66,7 @@ Geom make_geom(int nd, const int64_t T[3], bool wall = false)
 size_t tile_bound(int nd, int prec, const int64_t T[3])
 {
     if (nd == 2)
-        return size_t(3) * size_t(T[0] / layer2d_tile_cols(prec) + 3) * size_t(T[1] / kLayer2SlabRows + 2);
+        return size_t(3) * size_t(T[0] / layer2d_tile_cols(prec) + 3) * size_t(T[1] / kLayer2SlabRowsTB + 2);
     const int TX = prec == 32 ? kLayer3TXf : kLayer3TXd, TY = prec == 32 ? kLayer3TYf : kLayer3TYd;
     return size_t(5) * size_t(T[0] / TX + 2) * size_t(T[1] / TY + 2) * size_t(T[2] / kLayer3LZ + 2);
 }
@@ -359,7 +359,8 @@ std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
 //      are cut into runs of at most kLayer2SlabRows rows.
 //  3D: (x, y) column tiles streamed over z segments of at most kLayer3LZ planes (zlo..zhi,
 //      unwrapped).
-std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_off[9])
+std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_off[9],
+                                   int64_t band_rows = kLayer2BandRows, int64_t slab_rows = kLayer2SlabRows)
 {
     std::vector<LayerTile> t;
     if (c->nd == 2) {
@@ -387,17 +388,17 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
         };
         const int64_t T0 = c->T[0], T1 = c->T[1];
         if (range_empty(ir[0]) || range_empty(ir[1])) {
-            add(0, T0 - 1, 0, T1 - 1, kLayer2BandRows);
+            add(0, T0 - 1, 0, T1 - 1, band_rows);
         } else if (c->g.wall) {   // no seam to cross: two bands
-            if (ir[1].lo > 0) add(0, T0 - 1, 0, ir[1].lo - 1, kLayer2BandRows);
-            if (ir[1].hi < T1 - 1) add(0, T0 - 1, ir[1].hi + 1, T1 - 1, kLayer2BandRows);
-            if (ir[0].lo > 0) add(0, ir[0].lo - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
-            if (ir[0].hi < T0 - 1) add(ir[0].hi + 1, T0 - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
+            if (ir[1].lo > 0) add(0, T0 - 1, 0, ir[1].lo - 1, band_rows);
+            if (ir[1].hi < T1 - 1) add(0, T0 - 1, ir[1].hi + 1, T1 - 1, band_rows);
+            if (ir[0].lo > 0) add(0, ir[0].lo - 1, ir[1].lo, ir[1].hi, slab_rows);
+            if (ir[0].hi < T0 - 1) add(ir[0].hi + 1, T0 - 1, ir[1].lo, ir[1].hi, slab_rows);
         } else {
             const int64_t band = T1 - (ir[1].hi - ir[1].lo + 1);
-            if (band > 0) add(0, T0 - 1, ir[1].hi + 1, ir[1].hi + band, kLayer2BandRows);
-            if (ir[0].lo > 0) add(0, ir[0].lo - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
-            if (ir[0].hi < T0 - 1) add(ir[0].hi + 1, T0 - 1, ir[1].lo, ir[1].hi, kLayer2SlabRows);
+            if (band > 0) add(0, T0 - 1, ir[1].hi + 1, ir[1].hi + band, band_rows);
+            if (ir[0].lo > 0) add(0, ir[0].lo - 1, ir[1].lo, ir[1].hi, slab_rows);
+            if (ir[0].hi < T0 - 1) add(ir[0].hi + 1, T0 - 1, ir[1].lo, ir[1].hi, slab_rows);
         }
     } else {
         const int TX = layer3d_tile_x(c->prec), TY = layer3d_tile_y(c->prec), TZ = kLayer3LZ;
@@ -684,7 +685,8 @@ pml_status interior_grids(pml_ctx *c)
 pml_status encode_tb_maps(pml_ctx *c)
 {
     if (!c->plan.tb2) return PML_OK;
-    uint32_t box[3] = {128u, uint32_t(interior2d_tb2_box_rows(c->prec, c->tbvar)), 1};
+    uint32_t box[3] = {uint32_t(interior2d_tb2_box_cols(c->prec, c->tbvar)),
+                       uint32_t(interior2d_tb2_box_rows(c->prec, c->tbvar)), 1};
     pml_status s;
     for (int p = 0; p < 2; ++p)
         for (int f = 0; f < 2; ++f)
@@ -863,8 +865,12 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             r6[a] = shrink_run(c->ir[a], c->T[a], 6);
             r2[a] = c->ir_tb[a] = shrink_run(c->ir[a], c->T[a], 2);
         }
+        // shorter items than the one-step frame's: these passes run alone or beside the
+        // interior kernel, so a pass lasts as long as its longest item; about one short item
+        // per warp of a full launch
         int dummy[9];
-        std::vector<LayerTile> t1 = build_tiles(c, r6, dummy), t2 = build_tiles(c, r2, dummy);
+        std::vector<LayerTile> t1 = build_tiles(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
+                               t2 = build_tiles(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
         if (t1.size() > plan.max_tiles || t2.size() > plan.max_tiles) {
             fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
             return bail(PML_ENOMEM);

@@ -251,8 +251,10 @@ __device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUt
 // holds there (the first step only reads the run itself plus its halo).  One warp streams
 // its 128-column strip as before, but the rows of the first step (two rows behind the
 // input) feed a second copy of the one-step pipeline, whose rows (two more behind) are the
-// outputs.  Lanes 0 and 31 carry exactly the 4-column halo of the two steps, so a strip
-// still has 120 outputs; each output row needs 4 input rows above and below.  Every
+// outputs.  The two steps reach 4 columns to each side: with 4 columns per lane, lanes 0
+// and 31 carry exactly that halo and a 128-column strip still has 120 outputs; with 2
+// columns per lane (half the registers, more warps per SM) lanes 0-1 and 30-31 do and a
+// 64-column strip has 56.  Each output row needs 4 input rows above and below.  Every
 // vertex is read and written once per two steps.
 // ------------------------------------------------------------------------------------
 
@@ -302,8 +304,37 @@ __device__ __forceinline__ void ring_push(StepRing<T, NH> &R, const FwdCoefP<T> 
     }
 }
 
+// NH pairs of one lane's row from shared memory / to global memory (16-byte accesses for
+// two pairs, 8-byte for one).
+template <typename T, int NH>
+__device__ __forceinline__ void lds_pairs(const T *p, typename Pair<T>::P (&o)[NH])
+{
+    if constexpr (NH == 1) {
+        o[0] = *reinterpret_cast<const typename Pair<T>::P *>(p);
+    } else {
+#pragma unroll
+        for (int c = 0; c < NH; c += 2) {
+            const V4<T> t = lds4(p + 2 * c);
+            o[c] = Pair<T>::mk(t.x, t.y);
+            o[c + 1] = Pair<T>::mk(t.z, t.w);
+        }
+    }
+}
+template <typename T, int NH>
+__device__ __forceinline__ void stg_pairs(T *p, const typename Pair<T>::P (&v)[NH])
+{
+    if constexpr (NH == 1) {
+        *reinterpret_cast<typename Pair<T>::P *>(p) = v[0];
+    } else {
+#pragma unroll
+        for (int c = 0; c < NH; c += 2) stg4(p + 2 * c, V4<T>{v[c].x, v[c].y, v[c + 1].x, v[c + 1].y});
+    }
+}
+
 // One work item of the two-step kernel: output rows y0 .. y0+cnt-1 of the strip starting
-// at column xs (ring and barrier conventions as in interior2d_seg).
+// at column xs (ring and barrier conventions as in interior2d_seg).  NC = 4 columns per
+// lane (lanes 0 and 31 carry the 4-column halo, 120 outputs) or NC = 2 (lanes 0-1 and
+// 30-31, 56 outputs).
 template <typename T, int NC, int CH, int S>
 __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CUtensorMap *tmV, T *__restrict__ Uo,
                                                 T *__restrict__ Vo, const Interior2DArgs &a, int64_t xs, int64_t y0,
@@ -316,14 +347,15 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
     constexpr int ROW = 32 * NC;
     constexpr uint32_t FIELD_BYTES = CH * ROW * sizeof(T);
     constexpr uint32_t STAGE_BYTES = 2 * FIELD_BYTES;
-    static_assert(NC == 4 && CH % 3 == 0, "4 columns per lane; ring positions repeat every 3 rows");
+    static_assert((NC == 4 || NC == 2) && CH % 3 == 0, "2 or 4 columns per lane; ring positions repeat every 3 rows");
+    constexpr int HL = 4 / NC;   // halo lanes per side
     const Geom &g = a.g;
     const StepCoefT<T> &kc = coef_of<T>(a.c);
     const FwdCoefP<T> k{M::mk(kc.a1, kc.a1), M::mk(kc.a2, kc.a2), M::mk(kc.a3, kc.a3), M::mk(kc.a4, kc.a4),
                         M::mk(kc.b2, kc.b2), M::mk(kc.b3, kc.b3), M::mk(kc.b4, kc.b4), M::mk(kc.b5, kc.b5)};
     const int n_in = cnt + 8;
     const int nch = (n_in + CH - 1) / CH;
-    const int32_t tx = int32_t(xs - NC + G);
+    const int32_t tx = int32_t(xs - 4 + G);
     const int32_t ty = int32_t(y0 - 4 + G);
 
     if (lane == 0) {
@@ -339,27 +371,24 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
     }
     __syncwarp();
 
-    const int64_t x0 = xs - NC + NC * lane;
-    const bool out_lane = lane >= 1 && lane <= 30;
+    const int64_t x0 = xs - 4 + NC * lane;
+    const bool out_lane = lane >= HL && lane <= 31 - HL;
     const bool seg_vec = out_lane && x0 >= a.xr.lo && x0 + NC - 1 <= a.xr.hi && x0 >= G &&
                          x0 + NC - 1 < g.T[0] - G && y0 >= G && y0 + cnt <= g.T[1] - G;
     T *const pU = Uo + g.origin + (y0 - 8) * g.P + x0;   // output row of input row q: pU + q P
     T *const pV = Vo + g.origin + (y0 - 8) * g.P + x0;
     StepRing<T, NH> RA, RB;
 
+    // every output lane of this item can use vector stores (the common case): the steady
+    // rows then store without a branch, so the unrolled box stays one basic block
+    const bool fast = __all_sync(0xffffffffu, !out_lane || seg_vec);
     // input row q at ring position j; `guard`: the first boxes (stages start at rows 2, 4,
-    // 6, 8) and the last (rows past the input)
+    // 6, 8), the last (rows past the input) and items at the edges of the run or the box
     auto row = [&](const T *sU, const T *sV, int j, int q, bool guard) {
         if (guard && q >= n_in) return;
         const int J0 = j % 3;
-#pragma unroll
-        for (int c = 0; c < NH; c += 2) {
-            const V4<T> tu = lds4(sU + 2 * c), tv = lds4(sV + 2 * c);
-            RA.u[J0][c] = M::mk(tu.x, tu.y);
-            RA.u[J0][c + 1] = M::mk(tu.z, tu.w);
-            RA.v[J0][c] = M::mk(tv.x, tv.y);
-            RA.v[J0][c + 1] = M::mk(tv.z, tv.w);
-        }
+        lds_pairs<T, NH>(sU, RA.u[J0]);
+        lds_pairs<T, NH>(sV, RA.v[J0]);
         PT u1[NH], v1[NH];
         const bool a2 = !guard || q >= 4;
         ring_push<T, NH>(RA, k, j, !guard || q >= 2, a2, u1, v1);
@@ -374,13 +403,14 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
         const bool b2 = !guard || q >= 8;
         ring_push<T, NH>(RB, k, jb, !guard || q >= 6, b2, uo, vo);
         if (!b2) return;
-        if (seg_vec) {
-            T *ru = pU + int64_t(q) * g.P, *rv = pV + int64_t(q) * g.P;
-#pragma unroll
-            for (int c = 0; c < NH; c += 2) {
-                stg4(ru + 2 * c, V4<T>{uo[c].x, uo[c].y, uo[c + 1].x, uo[c + 1].y});
-                stg4(rv + 2 * c, V4<T>{vo[c].x, vo[c].y, vo[c + 1].x, vo[c + 1].y});
+        if (!guard) {   // fast item: predicated vector stores
+            if (out_lane) {
+                stg_pairs<T, NH>(pU + int64_t(q) * g.P, uo);
+                stg_pairs<T, NH>(pV + int64_t(q) * g.P, vo);
             }
+        } else if (seg_vec) {
+            stg_pairs<T, NH>(pU + int64_t(q) * g.P, uo);
+            stg_pairs<T, NH>(pV + int64_t(q) * g.P, vo);
         } else if (out_lane) {
             const int64_t r = y0 + q - 8;
 #pragma unroll
@@ -411,7 +441,7 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
         }
         const T *sU = reinterpret_cast<const T *>(wbase + slot * STAGE_BYTES) + NC * lane;
         const T *sV = sU + CH * ROW;
-        if (c * CH < 8 || c == nch - 1) {
+        if (c * CH < 8 || c == nch - 1 || !fast) {
 #pragma unroll
             for (int j = 0; j < CH; ++j) row(sU + j * ROW, sV + j * ROW, j, c * CH + j, true);
         } else {
@@ -1321,19 +1351,39 @@ __global__ void __launch_bounds__(128, MINB)
     uint32_t use = 0;
     const int64_t xs0 = a.xr.lo & ~int64_t(3);
     const int64_t nrows = a.yr.hi - a.yr.lo + 1;
-    const int rblocks = int((nrows + ROWS - 1) / ROWS);
-    const int nstrips = int((a.xr.hi - xs0) / (30 * NC) + 1);
-    const int n_items = nstrips * rblocks;
+    constexpr int OUT = (32 - 2 * (4 / NC)) * NC;   // output columns per strip
+    const int nstrips = int((a.xr.hi - xs0) / OUT + 1);
+    // Items: every strip's first rows in ROWS-row segments, then its last rows in
+    // SR-row segments, queued after all the long ones, so that the launch ends with about
+    // two rounds of short items over all warps instead of a ragged round of long ones.
+    constexpr int SR = ROWS / 4;
+    const int64_t nwarps = int64_t(gridDim.x) * 4;
+    int64_t small = int64_t(SR) * ((2 * nwarps + nstrips - 1) / nstrips);
+    small = small < nrows ? small : nrows;
+    const int64_t big = nrows - small;
+    const int nbig = int((big + ROWS - 1) / ROWS), nsmall = int((small + SR - 1) / SR);
+    const int items_big = nstrips * nbig, n_items = items_big + nstrips * nsmall;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&a.queue[a.parity], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        const int st = item / rblocks, rb = item - st * rblocks;
-        const int64_t y0 = a.yr.lo + int64_t(rb) * ROWS;
-        const int64_t rem = a.yr.hi - y0 + 1;
-        if (!interior2d_seg2<T, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(30 * NC) * st, y0,
-                                           int(rem < ROWS ? rem : ROWS), wbase, bars[warp], lane, use))
+        int st;
+        int64_t y0, cnt;
+        if (item < items_big) {
+            st = item / nbig;
+            const int rb = item - st * nbig;
+            y0 = int64_t(rb) * ROWS;
+            cnt = big - y0 < ROWS ? big - y0 : ROWS;
+        } else {
+            const int i = item - items_big;
+            st = i / nsmall;
+            const int sb = i - st * nsmall;
+            y0 = big + int64_t(sb) * SR;
+            cnt = nrows - y0 < SR ? nrows - y0 : SR;
+        }
+        if (!interior2d_seg2<T, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(OUT) * st, a.yr.lo + y0,
+                                           int(cnt), wbase, bars[warp], lane, use))
             break;
     }
     // finish only after the layer kernels of the same two steps (launched before this one)
@@ -1383,22 +1433,23 @@ template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct I2TKerne
 // step per pass gains nothing there): rows per TMA box, ring stages, resident CTAs per
 // SM, rows per work item.
 struct I2TVar {
-    int ch, s, minb, rows;
+    int nc, ch, s, minb, rows;
 };
-constexpr I2TVar kI2TVars32[] = {{6, 4, 2, 128}, {6, 3, 2, 128}, {3, 6, 2, 128}};
+constexpr I2TVar kI2TVars32[] = {{4, 6, 4, 2, 128}, {4, 3, 6, 2, 128}, {2, 3, 6, 3, 128}};
 constexpr int kNI2TVars32 = sizeof(kI2TVars32) / sizeof(I2TVar);
 
 template <typename F> static auto with_i2t(int v, F &&f)
 {
     switch (v) {
     case 0: return f(I2TKernel<float, 4, 6, 4, 2, 128>{});
-    case 1: return f(I2TKernel<float, 4, 6, 3, 2, 128>{});
-    default: return f(I2TKernel<float, 4, 3, 6, 2, 128>{});
+    case 1: return f(I2TKernel<float, 4, 3, 6, 2, 128>{});
+    default: return f(I2TKernel<float, 2, 3, 6, 3, 128>{});
     }
 }
 
 int interior2d_tb2_variants(int prec) { return prec == 32 ? kNI2TVars32 : 0; }
 int interior2d_tb2_box_rows(int prec, int v) { return prec == 32 ? kI2TVars32[v].ch : 0; }
+int interior2d_tb2_box_cols(int prec, int v) { return prec == 32 ? 32 * kI2TVars32[v].nc : 0; }
 int interior2d_tb2_max_blocks_per_sm(int prec, int v)
 {
     if (prec != 32) return 0;
