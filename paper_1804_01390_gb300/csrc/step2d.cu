@@ -82,9 +82,11 @@ __device__ __forceinline__ void diff5p(const typename Pair<T>::P (&c)[NH], T l, 
     const typename M::P m4 = M::mk(T(-4), T(-4));
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
-        const typename M::P left = M::mk(k == 0 ? l : c[k - 1].y, c[k].x);
-        const typename M::P right = M::mk(c[k].y, k == NH - 1 ? r : c[k + 1].x);
-        o[k] = M::fma(m4, c[k], M::add(M::add(left, right), M::add(up[k], dn[k])));
+        // x-neighbour sums of the pair's two columns as two scalar additions (the packed
+        // form would first assemble the straddling pairs (x-1) and (x+1) with moves)
+        const T lv = k == 0 ? l : c[k - 1].y, rv = k == NH - 1 ? r : c[k + 1].x;
+        const typename M::P xs = M::mk(lv + c[k].y, c[k].x + rv);
+        o[k] = M::fma(m4, c[k], M::add(xs, M::add(up[k], dn[k])));
     }
 }
 
