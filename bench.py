@@ -177,8 +177,12 @@ def run_ours(args, ws, rank, local):
     s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=32, device=dev)
     u_dev = torch.from_numpy(u0).to(dev)
     s.set_initial(u_dev)
-    variant, tune_table = autotune.tune(s, steps=20, use_cache=not args.retune)
-    one_step = s.one_step_variant
+    if args.variant is None:
+        variant, tune_table = autotune.tune(s, steps=20, use_cache=not args.retune)
+        one_step = s.one_step_variant
+    else:   # a fixed variant (profiling): no tuning launches
+        variant, tune_table, one_step = args.variant, None, None
+        autotune.select(s.ctx, variant)
     from paper_1804_01390_gb300 import _lib as _l
     tb = _l.pml_get_time_block(s.ctx)
     s.set_initial(u_dev)
@@ -540,6 +544,8 @@ def main():
     ap.add_argument("--n4", type=int, default=None, help="largest side of the batched grids (default 2048)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="use this 2D FP32 kernel variant instead of the autotuned one (profiling)")
     ap.add_argument("--n", type=int, default=None,
                     help="physical domain side (default 8192); smaller values are for profiling runs")
     args = ap.parse_args()
