@@ -333,7 +333,11 @@ pml_status pml_norms_dense_static(int ndim, const int64_t *T, int precision, con
  * pml_batch_get_variant / pml_batch_set_variant / pml_batch_autotune: as for a single
  *   context, over the batched interior kernel's variants (columns per lane, rows per TMA
  *   box, pipeline depth, resident CTAs per SM, rows per work item); autotuning advances
- *   every grid by (steps + 2) * count steps.
+ *   every grid by (steps + 2) * count steps.  FP32 batches add two-step variants (two
+ *   steps per pass, as for a single context: a layer pass into each context's mid buffer,
+ *   a second one from it, and the two-step interior kernel, all grids per launch; the graph
+ *   then replays 16 pairs); an odd last step uses the one-step variant last selected.
+ *   pml_batch_get_time_block reports the steps per pass of the current variant.
  * pml_batch_profile_enable / pml_batch_profile_read: event timing of every launch
  *   (kinds 0 interior, 1 layer); while enabled, steps are launched one by one without the
  *   graph and without overlap.
@@ -346,6 +350,7 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out);
 pml_status pml_batch_step(pml_batch *batch, int64_t n);
 pml_status pml_batch_get_variant(const pml_batch *batch, int *variant, int *count);
 pml_status pml_batch_set_variant(pml_batch *batch, int variant);
+pml_status pml_batch_get_time_block(const pml_batch *batch, int *depth);
 pml_status pml_batch_autotune(pml_batch *batch, int steps, double *times_ms, int *chosen);
 pml_status pml_batch_profile_enable(pml_batch *batch, int enable);
 pml_status pml_batch_profile_read(pml_batch *batch, double ms[2], int64_t launches[2]);

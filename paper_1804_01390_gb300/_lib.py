@@ -51,6 +51,7 @@ EXPORTED = (
     "pml_get_variant", "pml_set_variant", "pml_get_time_block", "pml_autotune",
     "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
     "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
+    "pml_batch_get_time_block",
     "pml_batch_autotune", "pml_batch_profile_enable", "pml_batch_profile_read", "pml_batch_info",
     "pml_batch_destroy", "pml_residual_factor", "pml_design_width", "pml_destroy", "pml_last_error", "pml_status_string",
 )
@@ -121,6 +122,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_batch_step": [P, i64],
         "pml_batch_get_variant": [P, P, P],
         "pml_batch_set_variant": [P, ctypes.c_int],
+        "pml_batch_get_time_block": [P, P],
         "pml_batch_autotune": [P, ctypes.c_int, P, P],
         "pml_batch_profile_enable": [P, ctypes.c_int],
         "pml_batch_profile_read": [P, P, P],
@@ -332,6 +334,13 @@ def pml_batch_get_variant(batch):
 
 def pml_batch_set_variant(batch, variant):
     _check(load().pml_batch_set_variant(batch, int(variant)))
+
+
+def pml_batch_get_time_block(b):
+    """Steps per pass of the batch's current variant (1 or 2)."""
+    d = ctypes.c_int(0)
+    _check(load().pml_batch_get_time_block(b, ctypes.byref(d)))
+    return int(d.value)
 
 
 def pml_batch_autotune(batch, steps):

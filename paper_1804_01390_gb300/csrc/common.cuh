@@ -332,19 +332,27 @@ cudaError_t launch_layer2d(int prec, bool adjoint, const CUtensorMap *tm /*[6] U
 struct GridDesc2 {   // aligned as CUtensorMap
     CUtensorMap tm_int[2][2];  // [input parity][U, V], interior box of the batch's variant
     CUtensorMap tm_lay[2][6];  // [input parity][field], layer box
+    CUtensorMap tm_tb[2][2];   // [input parity][U, V], box of the two-step interior shape
+    CUtensorMap tm_mid[6];     // first-step values of a two-step block, layer box
     void *out[2][6];           // output buffers when the input parity is p
+    void *mid[6];              // first-step values of a two-step block
     Interior2DArgs in;         // geometry, layer-free ranges, coefficients
+    Interior2DArgs in2;        // the same with the run shrunk by 2 (two-step interior)
     Layer2DArgs lay;           // geometry, constants, sigma (tiles: the batch list)
     int rblocks, nstrips;      // interior work items of this grid: nstrips x rblocks
+    int rblocks2, nstrips2;    // two-step interior work items of this grid
 };
 struct Batch2DArgs {
     const GridDesc2 *desc;
-    const int *item_off;       // [ngrid + 1] first interior item of each grid
-    const LayerTile *tiles;    // layer tiles of all grids
+    const int *item_off;       // [ngrid + 1] first interior item of each grid (of this launch's kind)
+    const LayerTile *tiles;    // layer tiles of all grids (of this launch's frame)
     const int *tile_grid;      // grid of each tile
     int ngrid, n_items, ntiles;
-    int *queue;                // interior work counters [2], then layer work counters [2]
+    int *queue;                // work counters: interior [2], layer [2], second layer pass [2]
     int parity;                // input parity of every grid; a launch counts on counter [parity]
+    int pass;                  // layer launch: 0 one step (fields -> fields), 1 first pass of a
+                               // two-step block (fields -> mid), 2 second pass (mid -> fields)
+    int qparity;               // counter parity of a second pass (its own launch count)
 };
 int batch2d_variants(int prec);
 int batch2d_box_cols(int prec, int v);     // interior tensor-map box of variant v
@@ -354,7 +362,17 @@ int batch2d_strip_cols(int prec, int v);   // output columns per interior work i
 int batch2d_interior_blocks_per_sm(int prec, int v);
 cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st,
                                     bool overlap_previous);
-cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, bool wall, cudaStream_t st);
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, bool wall, cudaStream_t st,
+                                 bool overlap_previous = false);
+// Two-step (temporally blocked) batched interior shapes (FP32 only).
+int batch2d_tb2_variants(int prec);
+int batch2d_tb2_box_cols(int prec, int v);
+int batch2d_tb2_box_rows(int prec, int v);
+int batch2d_tb2_item_rows(int prec, int v);
+int batch2d_tb2_strip_cols(int prec, int v);
+int batch2d_tb2_blocks_per_sm(int prec, int v);
+cudaError_t launch_batch2d_tb2(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st,
+                               bool overlap_previous);
 
 // 3D counterparts.
 struct Interior3DArgs {

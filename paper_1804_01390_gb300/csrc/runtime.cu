@@ -1465,6 +1465,14 @@ struct pml_batch {
     LayerTile *dtiles = nullptr;
     int n_items = 0, ntiles = 0, grid_int = 0;
     int64_t launches = 0;         // interior launches so far; its parity is the queue's
+    // two steps per pass (FP32 batches whose contexts all have the two-step buffers):
+    // `var` stays the one-step shape (odd steps), `var2` is the two-step shape when tb == 2
+    bool tb_ok = false;
+    int tb = 1, var2 = 0;
+    int *ditem_off2 = nullptr, *dtile_grid1 = nullptr, *dtile_grid2 = nullptr;
+    LayerTile *dtiles1 = nullptr, *dtiles2 = nullptr;
+    int n_items2 = 0, ntiles1 = 0, ntiles2 = 0, grid_tb = 0;
+    int64_t launches2 = 0;        // second layer passes so far; their counter parity
     cudaGraphExec_t exec = nullptr;
     bool pdl = true;              // interior launches overlap the layer launch
     bool prof_on = false;
@@ -1500,8 +1508,8 @@ pml_status batch_upload(pml_batch *b)
     const uint32_t box[3] = {uint32_t(batch2d_box_cols(b->prec, b->var)), uint32_t(batch2d_box_rows(b->prec, b->var)), 1};
     const int rows = batch2d_item_rows(b->prec, b->var), cols = batch2d_strip_cols(b->prec, b->var);
     std::vector<GridDesc2> desc(static_cast<size_t>(ng));
-    std::vector<int> off(static_cast<size_t>(ng) + 1, 0);
-    int64_t items = 0;
+    std::vector<int> off(static_cast<size_t>(ng) + 1, 0), off2(static_cast<size_t>(ng) + 1, 0);
+    int64_t items = 0, items2 = 0;
     for (int i = 0; i < ng; ++i) {
         pml_ctx *c = b->ctx[size_t(i)];
         GridDesc2 &d = desc[size_t(i)];
@@ -1525,6 +1533,31 @@ pml_status batch_upload(pml_batch *b)
         d.lay.sig[0] = c->dsig[0];
         d.lay.sig[1] = c->dsig[1];
         d.lay.err = c->derr;
+        if (b->tb_ok) {
+            const uint32_t box2[3] = {uint32_t(batch2d_tb2_box_cols(b->prec, b->var2)),
+                                      uint32_t(batch2d_tb2_box_rows(b->prec, b->var2)), 1};
+            for (int p = 0; p < 2; ++p)
+                for (int f = 0; f < 2; ++f)
+                    if (encode_map(c, &d.tm_tb[p][f], c->fld[p][f], box2) != PML_OK)
+                        return bfail(PML_ECUDA, "grid %d: %s", i, c->err.c_str());
+            for (int f = 0; f < 6; ++f) {
+                d.tm_mid[f] = c->tm_mid[f];
+                d.mid[f] = c->mid[f];
+            }
+            d.in2 = d.in;
+            d.in2.xr = c->ir_tb[0];
+            d.in2.yr = c->ir_tb[1];
+            int64_t n2 = 0;
+            if (!range_empty(c->ir_tb[0]) && !range_empty(c->ir_tb[1])) {
+                const int rows2 = batch2d_tb2_item_rows(b->prec, b->var2), cols2 = batch2d_tb2_strip_cols(b->prec, b->var2);
+                d.rblocks2 = int((c->ir_tb[1].hi - c->ir_tb[1].lo + 1 + rows2 - 1) / rows2);
+                d.nstrips2 = int((c->ir_tb[0].hi - (c->ir_tb[0].lo & ~int64_t(3))) / cols2 + 1);
+                n2 = int64_t(d.rblocks2) * d.nstrips2;
+            }
+            off2[size_t(i)] = int(items2);
+            items2 += n2;
+            if (items2 > (int64_t(1) << 30)) return bfail(PML_EINVAL, "batch has too many interior work items");
+        }
         int64_t n = 0;
         if (!range_empty(c->ir[0]) && !range_empty(c->ir[1])) {
             d.rblocks = int((c->ir[1].hi - c->ir[1].lo + 1 + rows - 1) / rows);
@@ -1536,9 +1569,18 @@ pml_status batch_upload(pml_batch *b)
         if (items > (int64_t(1) << 30)) return bfail(PML_EINVAL, "batch has too many interior work items");
     }
     off[size_t(ng)] = int(items);
+    off2[size_t(ng)] = int(items2);
     b->n_items = int(items);
+    b->n_items2 = int(items2);
     PML_BCU(cudaMemcpy(b->ddesc, desc.data(), desc.size() * sizeof(GridDesc2), cudaMemcpyHostToDevice), "upload batch descriptors");
     PML_BCU(cudaMemcpy(b->ditem_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "upload batch offsets");
+    if (b->tb_ok) {
+        PML_BCU(cudaMemcpy(b->ditem_off2, off2.data(), off2.size() * sizeof(int), cudaMemcpyHostToDevice),
+                "upload batch offsets");
+        const int bt = batch2d_tb2_blocks_per_sm(b->prec, b->var2);
+        if (bt <= 0) return bfail(PML_ECUDA, "batched two-step interior kernel cannot be resident");
+        b->grid_tb = bt * b->sm_count;
+    }
     // (also sets the kernels' shared-memory limits, which must not happen during capture)
     const int bps = batch2d_interior_blocks_per_sm(b->prec, b->var);
     if (bps <= 0 || batch2d_interior_blocks_per_sm(b->prec, 0) <= 0)
@@ -1593,6 +1635,44 @@ pml_status batch_enqueue(pml_batch *b, int p, cudaStream_t st, bool timed)
     return PML_OK;
 }
 
+// Two steps of every grid from input parity p: layer pass 1 (fields -> mid), layer pass 2
+// (mid -> fields; launched early, waits for pass 1; counters of parity qp), two-step interior.
+pml_status batch_enqueue_pair(pml_batch *b, int p, int qp, cudaStream_t st, bool timed)
+{
+    Batch2DArgs a{};
+    a.desc = b->ddesc;
+    a.ngrid = int(b->ctx.size());
+    a.queue = b->dqueue;
+    a.parity = p;
+    a.qparity = qp;
+    const bool wall = b->ctx[0]->g.wall != 0;
+    a.tiles = b->dtiles1;
+    a.tile_grid = b->dtile_grid1;
+    a.ntiles = b->ntiles1;
+    a.pass = 1;
+    long pi = timed ? bprof_begin(b, 1, st) : -1;
+    cudaError_t e = launch_batch2d_layer(b->prec, a, layer2d_grid(b->prec, a.ntiles, b->sm_count), wall, st, false);
+    bprof_end(b, pi, st);
+    if (e != cudaSuccess) return bfail(PML_ECUDA, "batched layer kernel (pass 1): %s", cudaGetErrorString(e));
+    a.tiles = b->dtiles2;
+    a.tile_grid = b->dtile_grid2;
+    a.ntiles = b->ntiles2;
+    a.pass = 2;
+    pi = timed ? bprof_begin(b, 1, st) : -1;
+    e = launch_batch2d_layer(b->prec, a, layer2d_grid(b->prec, a.ntiles, b->sm_count), wall, st,
+                             b->pdl && !timed && b->ntiles1 > 0);
+    bprof_end(b, pi, st);
+    if (e != cudaSuccess) return bfail(PML_ECUDA, "batched layer kernel (pass 2): %s", cudaGetErrorString(e));
+    a.pass = 0;
+    a.item_off = b->ditem_off2;
+    a.n_items = b->n_items2;
+    pi = timed ? bprof_begin(b, 0, st) : -1;
+    e = launch_batch2d_tb2(b->prec, b->var2, a, b->grid_tb, st, b->pdl && !timed && (b->ntiles1 + b->ntiles2) > 0);
+    bprof_end(b, pi, st);
+    if (e != cudaSuccess) return bfail(PML_ECUDA, "batched two-step interior kernel: %s", cudaGetErrorString(e));
+    return PML_OK;
+}
+
 void batch_drop_graph(pml_batch *b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1608,7 +1688,10 @@ pml_status batch_capture(pml_batch *b)
         cudaGraph_t g = nullptr;
         PML_BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin graph capture");
         pml_status s = PML_OK;
-        for (int k = 0; k < kBatchGraphSteps && s == PML_OK; ++k) s = batch_enqueue(b, k & 1, b->cap, false);
+        if (b->tb == 2)   // pairs from counter parity 0 (the caller aligns the second-pass counters)
+            for (int k = 0; k < kBatchGraphSteps / 2 && s == PML_OK; ++k) s = batch_enqueue_pair(b, k & 1, k & 1, b->cap, false);
+        else
+            for (int k = 0; k < kBatchGraphSteps && s == PML_OK; ++k) s = batch_enqueue(b, k & 1, b->cap, false);
         cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (s == PML_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
         if (g) cudaGraphDestroy(g);
@@ -1660,28 +1743,58 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
         tiles.insert(tiles.end(), t.begin(), t.end());
         tile_grid.insert(tile_grid.end(), t.size(), i);
     }
-    {   // one class after another across all grids (warps that run the same class share code)
-        std::vector<size_t> order(tiles.size());
+    // one class after another across all grids (warps that run the same class share code)
+    auto by_class = [](std::vector<LayerTile> &tl, std::vector<int> &tg) {
+        std::vector<size_t> order(tl.size());
         for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](size_t a, size_t b) { return tiles[a].flags < tiles[b].flags; });
-        std::vector<LayerTile> t2(tiles.size());
-        std::vector<int> g2(tiles.size());
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return tl[a].flags < tl[b].flags; });
+        std::vector<LayerTile> t2(tl.size());
+        std::vector<int> g2(tl.size());
         for (size_t k = 0; k < order.size(); ++k) {
-            t2[k] = tiles[order[k]];
-            g2[k] = tile_grid[order[k]];
+            t2[k] = tl[order[k]];
+            g2[k] = tg[order[k]];
         }
-        tiles.swap(t2);
-        tile_grid.swap(g2);
+        tl.swap(t2);
+        tg.swap(g2);
+    };
+    by_class(tiles, tile_grid);
+    // frames of the two layer passes of a two-step block (FP32 contexts with the buffers)
+    b->tb_ok = batch2d_tb2_variants(b->prec) > 0;
+    for (int i = 0; i < count; ++i) b->tb_ok = b->tb_ok && b->ctx[size_t(i)]->plan.tb2;
+    std::vector<LayerTile> tiles1, tiles2;
+    std::vector<int> grid1, grid2;
+    if (b->tb_ok) {
+        for (int i = 0; i < count; ++i) {
+            pml_ctx *c = b->ctx[size_t(i)];
+            Range r6[3];
+            for (int a = 0; a < 3; ++a) r6[a] = shrink_run(c->ir[a], c->T[a], 6);
+            int co[9];
+            std::vector<LayerTile> t1 = build_tiles(c, r6, co, kLayer2BandRowsTB, kLayer2SlabRowsTB),
+                                   t2 = build_tiles(c, c->ir_tb, co, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+            tiles1.insert(tiles1.end(), t1.begin(), t1.end());
+            grid1.insert(grid1.end(), t1.size(), i);
+            tiles2.insert(tiles2.end(), t2.begin(), t2.end());
+            grid2.insert(grid2.end(), t2.size(), i);
+        }
+        by_class(tiles1, grid1);
+        by_class(tiles2, grid2);
     }
-    if (tiles.size() > size_t(1) << 30) return bail(bfail(PML_EINVAL, "batch has too many layer tiles"));
+    if (tiles.size() > size_t(1) << 30 || tiles1.size() > size_t(1) << 30 || tiles2.size() > size_t(1) << 30)
+        return bail(bfail(PML_EINVAL, "batch has too many layer tiles"));
     b->ntiles = int(tiles.size());
+    b->ntiles1 = int(tiles1.size());
+    b->ntiles2 = int(tiles2.size());
     size_t off = 0;
     const size_t o_desc = off; off += align_up(size_t(count) * sizeof(GridDesc2), kAlign);
     const size_t o_item = off; off += align_up((size_t(count) + 1) * sizeof(int), kAlign);
     const size_t o_tile = off; off += align_up(std::max<size_t>(tiles.size(), 1) * sizeof(LayerTile), kAlign);
     const size_t o_tg = off; off += align_up(std::max<size_t>(tiles.size(), 1) * sizeof(int), kAlign);
     const size_t o_q = off; off += kAlign;
+    const size_t o_item2 = off; off += align_up((size_t(count) + 1) * sizeof(int), kAlign);
+    const size_t o_tile1 = off; off += align_up(std::max<size_t>(tiles1.size(), 1) * sizeof(LayerTile), kAlign);
+    const size_t o_tg1 = off; off += align_up(std::max<size_t>(tiles1.size(), 1) * sizeof(int), kAlign);
+    const size_t o_tile2 = off; off += align_up(std::max<size_t>(tiles2.size(), 1) * sizeof(LayerTile), kAlign);
+    const size_t o_tg2 = off; off += align_up(std::max<size_t>(tiles2.size(), 1) * sizeof(int), kAlign);
     cudaError_t e = cudaMalloc(&b->mem, off);
     if (e != cudaSuccess) { b->mem = nullptr; return bail(bfail(PML_ENOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e))); }
     b->ddesc = reinterpret_cast<GridDesc2 *>(b->mem + o_desc);
@@ -1689,12 +1802,25 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
     b->dtiles = reinterpret_cast<LayerTile *>(b->mem + o_tile);
     b->dtile_grid = reinterpret_cast<int *>(b->mem + o_tg);
     b->dqueue = reinterpret_cast<int *>(b->mem + o_q);
+    b->ditem_off2 = reinterpret_cast<int *>(b->mem + o_item2);
+    b->dtiles1 = reinterpret_cast<LayerTile *>(b->mem + o_tile1);
+    b->dtile_grid1 = reinterpret_cast<int *>(b->mem + o_tg1);
+    b->dtiles2 = reinterpret_cast<LayerTile *>(b->mem + o_tile2);
+    b->dtile_grid2 = reinterpret_cast<int *>(b->mem + o_tg2);
     if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess) return bail(bfail(PML_ECUDA, "stream synchronize: %s", cudaGetErrorString(e)));
     if (!tiles.empty()) {
         e = cudaMemcpy(b->dtiles, tiles.data(), tiles.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(b->dtile_grid, tile_grid.data(), tile_grid.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemset(b->dqueue, 0, 4 * sizeof(int));
+    if (e == cudaSuccess && !tiles1.empty()) {
+        e = cudaMemcpy(b->dtiles1, tiles1.data(), tiles1.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->dtile_grid1, grid1.data(), grid1.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && !tiles2.empty()) {
+        e = cudaMemcpy(b->dtiles2, tiles2.data(), tiles2.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->dtile_grid2, grid2.data(), grid2.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(b->dqueue, 0, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(bfail(PML_ECUDA, "batch tables: %s", cudaGetErrorString(e)));
     pml_status s = batch_upload(b);
@@ -1723,7 +1849,31 @@ pml_status pml_batch_step(pml_batch *b, int64_t n)
     }
     int64_t left = n;
     while (left > 0) {
-        if (p == 0 && left >= kBatchGraphSteps && !b->prof_on) {
+        if (b->tb == 2 && left >= 2) {   // two steps per pass
+            if (p == 0 && left >= kBatchGraphSteps && !b->prof_on) {
+                if (b->launches2 & 1) {   // the graph's second passes start on counter parity 0
+                    PML_BCU(cudaMemsetAsync(b->dqueue + 4, 0, 2 * sizeof(int), b->st), "reset batch queues");
+                    b->launches2 = 0;
+                }
+                if (!b->exec) {
+                    pml_status s = batch_capture(b);
+                    if (s != PML_OK) return s;
+                }
+                PML_BCU(cudaGraphLaunch(b->exec, b->st), "graph launch");
+                left -= kBatchGraphSteps;
+                b->launches += kBatchGraphSteps / 2;
+                b->launches2 += kBatchGraphSteps / 2;
+                continue;
+            }
+            pml_status s = batch_enqueue_pair(b, p, int(b->launches2 & 1), b->st, b->prof_on);
+            if (s != PML_OK) return s;
+            p ^= 1;
+            left -= 2;
+            ++b->launches;
+            ++b->launches2;
+            continue;
+        }
+        if (b->tb == 1 && p == 0 && left >= kBatchGraphSteps && !b->prof_on) {
             if (!b->exec) {
                 pml_status s = batch_capture(b);
                 if (s != PML_OK) return s;
@@ -1749,23 +1899,39 @@ pml_status pml_batch_step(pml_batch *b, int64_t n)
 pml_status pml_batch_get_variant(const pml_batch *b, int *variant, int *count)
 {
     if (!b) return bfail(PML_EINVAL, "pml_batch_get_variant: batch is NULL");
-    if (variant) *variant = b->var;
-    if (count) *count = batch2d_variants(b->prec);
+    const int n1 = batch2d_variants(b->prec);
+    if (variant) *variant = b->tb == 2 ? n1 + b->var2 : b->var;
+    if (count) *count = n1 + (b->tb_ok ? batch2d_tb2_variants(b->prec) : 0);
+    return PML_OK;
+}
+
+pml_status pml_batch_get_time_block(const pml_batch *b, int *depth)
+{
+    if (!b || !depth) return bfail(PML_EINVAL, "pml_batch_get_time_block: NULL argument");
+    *depth = b->tb;
     return PML_OK;
 }
 
 pml_status pml_batch_set_variant(pml_batch *b, int variant)
 {
     if (!b) return bfail(PML_EINVAL, "pml_batch_set_variant: batch is NULL");
-    const int n = batch2d_variants(b->prec);
+    const int n1 = batch2d_variants(b->prec), n = n1 + (b->tb_ok ? batch2d_tb2_variants(b->prec) : 0);
     if (variant < 0 || variant >= n) return bfail(PML_EINVAL, "pml_batch_set_variant: variant %d not in [0, %d)", variant, n);
     PML_BCU(cudaStreamSynchronize(b->st), "stream synchronize");
     batch_drop_graph(b);
-    const int old = b->var;
-    b->var = variant;
+    const int old = b->var, old_tb = b->tb, old2 = b->var2;
+    if (variant < n1) {
+        b->var = variant;
+        b->tb = 1;
+    } else {   // the one-step shape stays: it serves odd steps
+        b->var2 = variant - n1;
+        b->tb = 2;
+    }
     pml_status s = batch_upload(b);
     if (s != PML_OK) {
         b->var = old;
+        b->tb = old_tb;
+        b->var2 = old2;
         batch_upload(b);
     }
     return s;
@@ -1775,12 +1941,12 @@ pml_status pml_batch_autotune(pml_batch *b, int steps, double *times_ms, int *ch
 {
     if (!b) return bfail(PML_EINVAL, "pml_batch_autotune: batch is NULL");
     if (steps < 1) return bfail(PML_EINVAL, "pml_batch_autotune: steps must be >= 1");
-    const int n = batch2d_variants(b->prec);
+    const int n1 = batch2d_variants(b->prec), n = n1 + (b->tb_ok ? batch2d_tb2_variants(b->prec) : 0);
     cudaEvent_t e0, e1;
     PML_BCU(cudaEventCreate(&e0), "event");
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return bfail(PML_ECUDA, "event"); }
-    int best = b->var;
-    double best_ms = 1e300;
+    int best = b->tb == 2 ? n1 + b->var2 : b->var, best1 = b->var;
+    double best_ms = 1e300, best1_ms = 1e300;
     pml_status s = PML_OK;
     for (int v = 0; v < n && s == PML_OK; ++v) {
         if ((s = pml_batch_set_variant(b, v)) != PML_OK) break;
@@ -1794,6 +1960,8 @@ pml_status pml_batch_autotune(pml_batch *b, int steps, double *times_ms, int *ch
         const double per = double(ms) / steps;
         if (times_ms) times_ms[v] = per;
         if (per < best_ms) { best_ms = per; best = v; }
+        if (v < n1 && per < best1_ms) { best1_ms = per; best1 = v; }
+        if (v == n1 - 1 && (s = pml_batch_set_variant(b, best1)) != PML_OK) break;   // kept for odd steps
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1828,9 +1996,9 @@ pml_status pml_batch_info(const pml_batch *b, int64_t info[4])
 {
     if (!b || !info) return bfail(PML_EINVAL, "pml_batch_info: NULL argument");
     info[0] = int64_t(b->ctx.size());
-    info[1] = b->n_items;
-    info[2] = b->ntiles;
-    info[3] = b->grid_int;
+    info[1] = b->tb == 2 ? b->n_items2 : b->n_items;
+    info[2] = b->tb == 2 ? b->ntiles1 + b->ntiles2 : b->ntiles;
+    info[3] = b->tb == 2 ? b->grid_tb : b->grid_int;
     return PML_OK;
 }
 

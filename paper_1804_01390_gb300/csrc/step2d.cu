@@ -1550,17 +1550,20 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB) k_layer2d_batch(const Bat
     __syncwarp();
     T *ring = smem + warp * WE;
     uint32_t use = 0;
-    int *const lq = b.queue + 2;
-    if (blockIdx.x == 0 && threadIdx.x == 0) lq[1 - b.parity] = 0;
+    // the second pass of a two-step block has its own counters (it starts before the first
+    // pass has finished with its own)
+    int *const lq = b.queue + (b.pass == 2 ? 4 : 2);
+    const int qp = b.pass == 2 ? b.qparity : b.parity;
+    if (blockIdx.x == 0 && threadIdx.x == 0) lq[1 - qp] = 0;
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(&lq[b.parity], 1);
+        if (lane == 0) item = atomicAdd(&lq[qp], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= b.ntiles) break;
         const LayerTile tile = b.tiles[item];
         const GridDesc2 &d = b.desc[b.tile_grid[item]];
-        const Maps6 &maps = *reinterpret_cast<const Maps6 *>(&d.tm_lay[b.parity][0]);
-        const Out6 out = *reinterpret_cast<const Out6 *>(&d.out[b.parity][0]);
+        const Maps6 &maps = *reinterpret_cast<const Maps6 *>(b.pass == 2 ? &d.tm_mid[0] : &d.tm_lay[b.parity][0]);
+        const Out6 out = *reinterpret_cast<const Out6 *>(b.pass == 1 ? &d.mid[0] : &d.out[b.parity][0]);
         const Layer2DArgs la = d.lay;   // local copies: stores to the fields cannot alias them
         bool ok;
         switch (tile.flags & 3) {
@@ -1645,19 +1648,125 @@ cudaError_t launch_batch2d_interior(int prec, int v, const Batch2DArgs &a, int g
     return with_b2(prec, v, [&](auto k) { return decltype(k)::launch(a, grid, st, overlap_previous); });
 }
 
-cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, bool wall, cudaStream_t st)
+cudaError_t launch_batch2d_layer(int prec, const Batch2DArgs &a, int grid, bool wall, cudaStream_t st,
+                                 bool overlap_previous)
 {
     if (a.ntiles <= 0 || grid <= 0) return cudaSuccess;
     cudaError_t e = with_b2(prec, 0, [](auto k) { return decltype(k)::prep(); });
     if (e != cudaSuccess) return e;
+    const bool ov = overlap_previous;
     if (prec == 32) {
-        if (wall) k_layer2d_batch<float, false, true><<<grid, 128, layer2d_smem<float>(), st>>>(a);
-        else k_layer2d_batch<float, false, false><<<grid, 128, layer2d_smem<float>(), st>>>(a);
-    } else {
-        if (wall) k_layer2d_batch<double, false, true><<<grid, 128, layer2d_smem<double>(), st>>>(a);
-        else k_layer2d_batch<double, false, false><<<grid, 128, layer2d_smem<double>(), st>>>(a);
+        if (wall) return launch_pdl(k_layer2d_batch<float, false, true>, grid, 128, layer2d_smem<float>(), st, ov, a);
+        return launch_pdl(k_layer2d_batch<float, false, false>, grid, 128, layer2d_smem<float>(), st, ov, a);
     }
-    return cudaGetLastError();
+    if (wall) return launch_pdl(k_layer2d_batch<double, false, true>, grid, 128, layer2d_smem<double>(), st, ov, a);
+    return launch_pdl(k_layer2d_batch<double, false, false>, grid, 128, layer2d_smem<double>(), st, ov, a);
+}
+
+// ------------------------------------------------------------------------------------
+// Batched two-step interior kernel: interior2d_seg2 over the shrunk runs of all grids, one
+// queue of ROWS-row strip segments (owning grid by binary search over item_off).
+// ------------------------------------------------------------------------------------
+template <typename T, int NC, int CH, int S, int MINB, int ROWS>
+__global__ void __launch_bounds__(128, MINB) k_interior2d_tb2_batch(const Batch2DArgs b)
+{
+    constexpr size_t WB = size_t(S) * 2 * CH * 32 * NC * sizeof(T);
+    constexpr int OUT = (32 - 2 * (4 / NC)) * NC;
+    __shared__ __align__(8) uint64_t bars[4][S];
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem + warp * WB;
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.queue[1 - b.parity] = 0;
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[warp][s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t use = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&b.queue[b.parity], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= b.n_items) break;
+        int lo = 0, hi = b.ngrid - 1;   // last grid whose first item is <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.item_off[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const GridDesc2 &d = b.desc[lo];
+        const Interior2DArgs a = d.in2;   // a local copy: stores to the fields cannot alias it
+        const int k = item - b.item_off[lo];
+        const int st = k / d.rblocks2, rb = k - st * d.rblocks2;
+        const int64_t y0 = a.yr.lo + int64_t(rb) * ROWS;
+        const int64_t rem = a.yr.hi - y0 + 1;
+        const int64_t xs = (a.xr.lo & ~int64_t(3)) + int64_t(OUT) * st;
+        if (!interior2d_seg2<T, NC, CH, S>(&d.tm_tb[b.parity][0], &d.tm_tb[b.parity][1],
+                                           static_cast<T *>(d.out[b.parity][0]), static_cast<T *>(d.out[b.parity][1]),
+                                           a, xs, y0, int(rem < ROWS ? rem : ROWS), wbase, bars[warp], lane, use))
+            break;
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct BTKernel {
+    static constexpr size_t smem() { return size_t(4) * S * 2 * CH * 32 * NC * sizeof(T) + 128; }
+    static auto fn() { return k_interior2d_tb2_batch<T, NC, CH, S, MINB, ROWS>; }
+    static cudaError_t prep()
+    {
+        static bool done = false;
+        if (done) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e == cudaSuccess) done = true;
+        return e;
+    }
+    static int occupancy()
+    {
+        if (prep() != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn(), 128, smem()) != cudaSuccess) return 0;
+        return n;
+    }
+    static cudaError_t launch(const Batch2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+    {
+        cudaError_t e = prep();
+        if (e != cudaSuccess) return e;
+        return launch_pdl(fn(), grid, 128, smem(), st, overlap_previous, a);
+    }
+};
+
+struct BTVar {
+    int nc, ch, s, minb, rows;
+};
+constexpr BTVar kBT32[] = {{4, 3, 6, 2, 64}, {4, 3, 6, 2, 128}};
+constexpr int kNBT32 = sizeof(kBT32) / sizeof(BTVar);
+
+template <typename F> static auto with_bt2(int v, F &&f)
+{
+    switch (v) {
+    case 0: return f(BTKernel<float, 4, 3, 6, 2, 64>{});
+    default: return f(BTKernel<float, 4, 3, 6, 2, 128>{});
+    }
+}
+
+int batch2d_tb2_variants(int prec) { return prec == 32 ? kNBT32 : 0; }
+int batch2d_tb2_box_cols(int prec, int v) { return prec == 32 ? 32 * kBT32[v].nc : 0; }
+int batch2d_tb2_box_rows(int prec, int v) { return prec == 32 ? kBT32[v].ch : 0; }
+int batch2d_tb2_item_rows(int prec, int v) { return prec == 32 ? kBT32[v].rows : 0; }
+int batch2d_tb2_strip_cols(int prec, int v) { return prec == 32 ? (32 - 2 * (4 / kBT32[v].nc)) * kBT32[v].nc : 0; }
+int batch2d_tb2_blocks_per_sm(int prec, int v)
+{
+    if (prec != 32) return 0;
+    return with_bt2(v, [](auto k) { return decltype(k)::occupancy(); });
+}
+
+cudaError_t launch_batch2d_tb2(int prec, int v, const Batch2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+{
+    if (prec != 32 || v < 0 || v >= kNBT32) return cudaErrorInvalidValue;
+    if (a.n_items <= 0 || grid <= 0) return cudaSuccess;
+    return with_bt2(v, [&](auto k) { return decltype(k)::launch(a, grid, st, overlap_previous); });
 }
 
 }  // namespace pml

@@ -255,6 +255,10 @@ class PMLBatch:
     def variant_count(self):
         return _lib.pml_batch_get_variant(self.handle)[1]
 
+    def time_block(self):
+        """Steps per pass of the current variant (1, or 2 for a two-step shape)."""
+        return _lib.pml_batch_get_time_block(self.handle)
+
     def set_variant(self, v):
         _lib.pml_batch_set_variant(self.handle, int(v))
 

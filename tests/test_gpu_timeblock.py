@@ -212,3 +212,80 @@ def test_full_size_cfg2_two_step_sampled(variant_pos):
         want += [wu, wv]
     err = rel_l2(got, want)
     assert err <= TOL[32], err
+
+
+# ------------------------------------------------------------------------------------
+# batched mode
+# ------------------------------------------------------------------------------------
+BGRIDS = [((150, 90), 12), ((40, 33), 0), ((2, 2), 4), ((64, 201), 6), ((23, 47), 5), ((300, 70), 9)]
+
+
+def _batch_make(grids=BGRIDS, seed0=300):
+    import torch
+    solvers, inits = [], []
+    for k, (N, w) in enumerate(grids):
+        s = make_solver(N, w, 32)
+        T = tuple(n + 2 * w for n in N)
+        rng = np.random.default_rng(seed0 + k)
+        u0 = gaussian_u0(N, w, seed0 + k) + rng.normal(scale=0.3, size=T[::-1])
+        v0 = rng.normal(scale=0.3, size=T[::-1])
+        s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
+        solvers.append(s)
+        inits.append((u0, v0))
+    return solvers, inits
+
+
+def _batch_two_step_variants(b):
+    out = []
+    for v in range(b.variant_count):
+        b.set_variant(v)
+        if b.time_block() == 2:
+            out.append(v)
+    return out
+
+
+def test_batch_two_step_odd_parities_match_oracle():
+    """Two-step batch variants from the odd ping-pong half, with a second-pass counter parity
+    that must be realigned before the graph replay (1 + 2 + 35 + 5 steps)."""
+    from paper_1804_01390_gb300.solver import PMLBatch
+    probe, _ = _batch_make(BGRIDS[:1])
+    vs = _batch_two_step_variants(PMLBatch(probe))
+    assert vs
+    for v in vs:
+        solvers, inits = _batch_make()
+        b = PMLBatch(solvers)
+        b.set_variant(v)
+        assert b.time_block() == 2
+        for n in (1, 2, 35, 5):
+            b.step(n)
+        for k, ((N, w), s, (u0, v0)) in enumerate(zip(BGRIDS, solvers, inits)):
+            want = _oracle_run(N, w, "quadratic", None, u0, v0, 43)
+            assert s.step_count == 43
+            for f in range(6):
+                got = s.read(f).double().cpu().numpy()
+                err = rel_l2(got, want[f].reshape(got.shape))
+                assert err <= TOL[32], (v, k, f, err)
+        b.close()
+        for s in solvers:
+            s.close()
+
+
+def test_batch_two_step_equals_single_context_two_step():
+    """Same arithmetic per vertex (4 columns per lane, the same frame tables): the batched
+    two-step launches reproduce the per-context two-step launches bit for bit."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    from paper_1804_01390_gb300.solver import PMLBatch
+    a, _ = _batch_make()
+    c, _ = _batch_make()
+    for s in a:
+        vs = _two_step_variants(s)
+        _lib.pml_set_variant(s.ctx, vs[1])   # 4 columns per lane, 3-row boxes
+        s.step(40)
+    batch = PMLBatch(c)
+    bv = _batch_two_step_variants(batch)
+    batch.set_variant(bv[0])
+    batch.step(40)
+    for x, y in zip(a, c):
+        for f in range(6):
+            assert torch.equal(x.read(f), y.read(f)), f
