@@ -171,6 +171,15 @@ def run_ours(args, ws, rank, local):
     u0 = wk.initial_field(wl, dtype=np.float32)
     K, W = args.steps, args.warmup
     hbm_peak, peak_kind = _peaks()
+    # bytes one point-update must move (each step reads and writes U, V once, plus
+    # Phi_a, Psi_a on their 2w - 1 active cells per axis): 4 + 4 sum_a (2w - 1) / T_a words
+    words_per_update = 4.0 + 4.0 * sum((2 * wl.w - 1) / t for t in wl.T)
+
+    def step_roofline(gpts, esz):
+        b = words_per_update * esz
+        return {"bytes_per_update": b, "achieved_gbs": gpts * b, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gpts * b / hbm_peak, "peak_kind": peak_kind,
+                "definition": "point-updates/s x algorithmic bytes per point-update / measured copy bandwidth"}
 
     # ---- FP32 headline: inputs resident in HBM ------------------------------------
     from paper_1804_01390_gb300 import autotune
@@ -251,6 +260,7 @@ def run_ours(args, ws, rank, local):
         t_int = m64[0] / max(n64[0], 1) / 1e3
         tflops = int(np.prod([n - 2 for n in wl.N])) * FP64_FLOP_PER_POINT / t_int / 1e12
         fp64 = {"value": v64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
+                "hbm_roofline": step_roofline(v64 / ws, 8),
                 "roofline": {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS,
                              "unit": "TFLOP/s", "frac": tflops / NOMINAL_FP64_TFLOPS,
                              "peak_kind": "nominal GB300 FP64", "flop_per_point": FP64_FLOP_PER_POINT}}
@@ -278,8 +288,9 @@ def run_ours(args, ws, rank, local):
         _t.cuda.synchronize()
         barrier(ws)
         msa = max_over_ranks(e0.elapsed_time(e1), ws, dev)
-        adj = {"value": pts * Ka * ws / (msa / 1e3) / 1e9, "unit": UNIT, "steps": Ka,
-               "ms_per_step": msa / Ka, "dtype": "f32"}
+        va = pts * Ka * ws / (msa / 1e3) / 1e9
+        adj = {"value": va, "unit": UNIT, "steps": Ka, "ms_per_step": msa / Ka, "dtype": "f32",
+               "hbm_roofline": step_roofline(va / ws, 4)}
         s.close()
         del s
 
@@ -469,6 +480,7 @@ def run_ours(args, ws, rank, local):
                          "avg_launch_ms": avg_launch_s * 1e3, "layer_time_share": layer_share,
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
+            "hbm_roofline": step_roofline(value / ws, 4),
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
             "cfg3": d3, "batched": d4, "stress": stress, "grad_sigma": gsig, "wall": dwall,
             "cpu_baseline": cpu,
