@@ -456,6 +456,51 @@ def run_ours(args, ws, rank, local):
         s.close()
         del s, u5
 
+    # ---- misfit gradient w.r.t. U0 and the source amplitudes (2048^2 + 32, 10^4 steps) ---
+    mgrad = None
+    if not args.no_misfit:
+        from paper_1804_01390_gb300.autograd import traces
+        wl5 = wk.cfg5()
+        n5 = wl5.steps if args.n5 is None else args.n5
+        src5 = wl5.sources
+        s = PMLSolver(wl5.N, wl5.w, dt=wl5.dt, precision=32, device=dev, adjoint=True)
+        # target traces: the seeded "true" model (another pulse, other amplitudes)
+        g_t, a_t = wk.cfg5_target(wl5)
+        wl_t = wk.Workload("cfg5-target", 2, wl5.N, wl5.w, dt=wl5.dt, steps=n5, gaussians=g_t,
+                           sources=src5, receivers=wl5.receivers, seed=6)
+        u_t = torch.from_numpy(wk.initial_field(wl_t, dtype=np.float32)).to(dev)
+        d5 = traces(s, u_t, torch.tensor(a_t, dtype=torch.float64), n5, src5["coords"], wl5.receivers,
+                    src5["f_peak"], src5["t_delay"]).detach().clone()
+        u5 = torch.from_numpy(wk.initial_field(wl5, dtype=np.float32)).to(dev).requires_grad_(True)
+        a5 = torch.tensor(src5["amp"], dtype=torch.float64, requires_grad=True)
+        # warm-up: 20 steps forward and back
+        trw = traces(s, u5, a5, 20, src5["coords"], wl5.receivers, src5["f_peak"], src5["t_delay"])
+        (0.5 * (trw.double() ** 2).sum()).backward()
+        u5.grad = None
+        a5.grad = None
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        tr5 = traces(s, u5, a5, n5, src5["coords"], wl5.receivers, src5["f_peak"], src5["t_delay"])
+        J5 = 0.5 * ((tr5.double() - d5.double()) ** 2).sum()
+        J5.backward()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sec = max_over_ranks(t1 - t0, ws, dev)
+        mgrad = {"workload": "2D 2048^2 interior + 32-cell quadratic PML, Gaussian s=8, 16 Ricker sources, 64 "
+                             "receivers on a line, FP32: L2 misfit of the traces against a seeded target model, "
+                             "gradient w.r.t. U0 and the 16 amplitudes through torch.autograd (forward with "
+                             "traces, then the transposed steps with the residual injected)",
+                 "steps": n5, "seconds": sec, "ms_per_step": sec * 1e3 / n5,
+                 "value": 2 * wl5.points * n5 * ws / sec / 1e9,
+                 "unit": "GPts/s (forward and transposed point-updates)",
+                 "misfit": float(J5.item()), "grad_u0_l2": float(u5.grad.double().norm().item()),
+                 "grad_amp": [float(x) for x in a5.grad.tolist()],
+                 "checkpoints": "none needed: the traces are linear in U0 and the amplitudes, so the "
+                                "adjoint needs no forward states"}
+        s.close()
+        del s, u5, u_t, d5
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -483,6 +528,7 @@ def run_ours(args, ws, rank, local):
             "hbm_roofline": step_roofline(value / ws, 4),
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
             "cfg3": d3, "batched": d4, "stress": stress, "grad_sigma": gsig, "wall": dwall,
+            "misfit_gradient": mgrad,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -563,6 +609,8 @@ def main():
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--no-grad-sigma", action="store_true")
     ap.add_argument("--no-wall", action="store_true")
+    ap.add_argument("--no-misfit", action="store_true")
+    ap.add_argument("--n5", type=int, default=None, help="steps of the misfit-gradient workload (default 10^4)")
     ap.add_argument("--n4", type=int, default=None, help="largest side of the batched grids (default 2048)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")

@@ -56,14 +56,17 @@ __device__ __forceinline__ void add_wrapped(T *base, const Geom &g, int64_t x, i
 //   S = dt (b1 + 4 b2 + b4)/6 + dt^2 A (b1 + 2 b2)/6 + dt^3 A^2 (b1 + b2)/12 + dt^4 A^3 b1/24
 // to P(dt A) y, and near the source (where no damping term is within reach)
 // A e_V = e_U, A^2 e_V = (0, L delta), A^3 e_V = (L delta, 0).  Then the receivers read U.
+// One thread per source; sources whose stencils meet are in different levels (PointArgs),
+// so every vertex receives its additions in source order.
 template <typename T>
 __global__ void k_post_step(T *U, T *V, const PointArgs a, int64_t step, T *trace_row)
 {
     const Geom &g = a.g;
-    if (threadIdx.x == 0) {
-        const double dt = a.dt, t = double(step) * dt, ih2 = 1.0 / (a.h * a.h);
-        const int nd = g.ndim;
-        for (int s = 0; s < a.ns; ++s) {
+    const double dt = a.dt, t = double(step) * dt, ih2 = 1.0 / (a.h * a.h);
+    const int nd = g.ndim;
+    for (int lv = 0; lv < a.src_levels; ++lv) {   // one thread per source of the level
+        for (int s = threadIdx.x; s < a.ns; s += blockDim.x) {
+            if (a.src_level[s] != lv) continue;
             const double am = a.src_amp[s];
             const double b1 = am * ricker(t, a.f_peak, a.t_delay);
             const double b2 = am * ricker(t + 0.5 * dt, a.f_peak, a.t_delay);
@@ -72,20 +75,39 @@ __global__ void k_post_step(T *U, T *V, const PointArgs a, int64_t step, T *trac
             const double cV = dt * dt * dt * (b1 + b2) / 12.0;
             const double sU0 = dt * dt * (b1 + 2.0 * b2) / 6.0;
             const double cU = dt * dt * dt * dt * b1 / 24.0;
-            const int64_t x = a.src_xyz[3 * s], y = a.src_xyz[3 * s + 1], z = a.src_xyz[3 * s + 2];
-            add_wrapped(V, g, x, y, z, sV0 - cV * 2.0 * nd * ih2);
-            add_wrapped(U, g, x, y, z, sU0 - cU * 2.0 * nd * ih2);
-            for (int ax = 0; ax < nd; ++ax) {
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    int64_t c[3] = {x, y, z};
-                    c[ax] = (c[ax] + sg + g.T[ax]) % g.T[ax];
-                    add_wrapped(V, g, c[0], c[1], c[2], cV * ih2);
-                    add_wrapped(U, g, c[0], c[1], c[2], cU * ih2);
+            // the stencil: the vertex and its 2 nd neighbours, all distinct, so every load can
+            // be issued before the first store
+            int64_t cc[7][3];
+            const int nk = 1 + 2 * nd;
+            cc[0][0] = a.src_xyz[3 * s];
+            cc[0][1] = a.src_xyz[3 * s + 1];
+            cc[0][2] = a.src_xyz[3 * s + 2];
+            for (int ax = 0, k = 1; ax < nd; ++ax) {
+                for (int sg = -1; sg <= 1; sg += 2, ++k) {
+                    cc[k][0] = cc[0][0];
+                    cc[k][1] = cc[0][1];
+                    cc[k][2] = cc[0][2];
+                    int64_t v = cc[0][ax] + sg;
+                    v += v < 0 ? g.T[ax] : 0;
+                    v -= v >= g.T[ax] ? g.T[ax] : 0;
+                    cc[k][ax] = v;
                 }
             }
+            T ov[7], ou[7];
+            for (int k = 0; k < nk; ++k) {
+                const int64_t o = g.origin + cc[k][0] + cc[k][1] * g.P + cc[k][2] * g.PS;
+                ov[k] = V[o];
+                ou[k] = U[o];
+            }
+            for (int k = 0; k < nk; ++k) {
+                const double dv = k == 0 ? sV0 - cV * 2.0 * nd * ih2 : cV * ih2;
+                const double du = k == 0 ? sU0 - cU * 2.0 * nd * ih2 : cU * ih2;
+                store_wrapped(V, g, cc[k][0], cc[k][1], cc[k][2], T(double(ov[k]) + dv));
+                store_wrapped(U, g, cc[k][0], cc[k][1], cc[k][2], T(double(ou[k]) + du));
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (trace_row)
         for (int r = threadIdx.x; r < a.nr; r += blockDim.x) trace_row[r] = U[g.origin + a.rec_off[r]];
 }
@@ -109,11 +131,13 @@ __global__ void k_adjoint_points(T *Ub, T *Vb, const PointArgs a, int64_t m, con
                                  double *grad_amp)
 {
     const Geom &g = a.g;
-    if (threadIdx.x == 0 && residual_row) {
-        for (int r = 0; r < a.nr; ++r) {
-            const int64_t o = a.rec_off[r];
-            const int64_t x = o % g.P, y = (o / g.P) % g.R, z = o / g.PS;
-            add_wrapped(Ub, g, x, y, z, double(residual_row[r]));
+    if (residual_row) {
+        for (int lv = 0; lv < a.rec_levels; ++lv) {   // one thread per receiver of the level
+            for (int r = threadIdx.x; r < a.nr; r += blockDim.x)
+                if (a.rec_level[r] == lv)
+                    add_wrapped(Ub, g, a.rec_xyz[3 * r], a.rec_xyz[3 * r + 1], a.rec_xyz[3 * r + 2],
+                                double(residual_row[r]));
+            __syncthreads();
         }
     }
     __syncthreads();

@@ -459,6 +459,15 @@ struct PointArgs {
     int nr;
     const int64_t *rec_off;
     double dt, h;
+    // Points whose updates touch a common vertex must add in index order: every source has
+    // a level one above the highest level of the earlier sources whose stencils (the
+    // vertex and its 2 d neighbours) meet its own, every receiver one above the earlier
+    // receivers at its vertex; the kernels run level after level, each level in parallel.
+    const int32_t *src_level;
+    int src_levels;
+    const int32_t *rec_xyz;    // logical coordinates [nr][3]
+    const int32_t *rec_level;
+    int rec_levels;
 };
 cudaError_t launch_post_step(int prec, void *U, void *V, const PointArgs &a, int64_t step,
                              void *trace_row, cudaStream_t st);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -42,7 +43,7 @@ struct Plan {
     size_t sig[3] = {};
     size_t tiles = 0, tiles_adj = 0, max_tiles = 0, tiles_l1 = 0, tiles_l2 = 0;
     size_t partials = 0, normout = 0, err = 0, queue = 0;
-    size_t src_off = 0, src_xyz = 0, src_amp = 0, grad = 0, rec_off = 0;
+    size_t src_off = 0, src_xyz = 0, src_amp = 0, grad = 0, rec_off = 0, src_level = 0, rec_xyz = 0, rec_level = 0;
     size_t total = 0;
 };
 
@@ -114,6 +115,9 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
     p->src_amp = off; off += align_up(kMaxSources * sizeof(double), kAlign);
     p->grad = off; off += align_up(kMaxSources * sizeof(double), kAlign);
     p->rec_off = off; off += align_up(kMaxReceivers * sizeof(int64_t), kAlign);
+    p->src_level = off; off += align_up(kMaxSources * sizeof(int32_t), kAlign);
+    p->rec_xyz = off; off += align_up(kMaxReceivers * 3 * sizeof(int32_t), kAlign);
+    p->rec_level = off; off += align_up(kMaxReceivers * sizeof(int32_t), kAlign);
     p->total = off;
     return true;
 }
@@ -147,7 +151,8 @@ struct pml_ctx {
     int64_t launches_fwd = 0, launches_adj = 0, launches_layer_fwd = 0, launches_layer_adj = 0, launches_layer2 = 0;
     int ns = 0, nr = 0;
     int64_t *dsrc_off = nullptr, *drec_off = nullptr;
-    int32_t *dsrc_xyz = nullptr;
+    int32_t *dsrc_xyz = nullptr, *dsrc_level = nullptr, *drec_xyz = nullptr, *drec_level = nullptr;
+    int src_levels = 0, rec_levels = 0;
     double *dsrc_amp = nullptr;
     double f_peak = 0, t_delay = 0;
     void *trace = nullptr;
@@ -517,6 +522,11 @@ PointArgs point_args(const pml_ctx *c)
     a.t_delay = c->t_delay;
     a.nr = c->nr;
     a.rec_off = c->drec_off;
+    a.src_level = c->dsrc_level;
+    a.src_levels = c->src_levels;
+    a.rec_xyz = c->drec_xyz;
+    a.rec_level = c->drec_level;
+    a.rec_levels = c->rec_levels;
     a.dt = c->dt;
     a.h = c->h;
     return a;
@@ -821,6 +831,9 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     c->dsrc_amp = reinterpret_cast<double *>(c->ws + plan.src_amp);
     c->dgrad = reinterpret_cast<double *>(c->ws + plan.grad);
     c->drec_off = reinterpret_cast<int64_t *>(c->ws + plan.rec_off);
+    c->dsrc_level = reinterpret_cast<int32_t *>(c->ws + plan.src_level);
+    c->drec_xyz = reinterpret_cast<int32_t *>(c->ws + plan.rec_xyz);
+    c->drec_level = reinterpret_cast<int32_t *>(c->ws + plan.rec_level);
 
     // state = 0 everywhere (both ping-pong halves, adjoint too)
     {
@@ -1085,12 +1098,28 @@ pml_status pml_set_sources(pml_ctx *c, int ns, const int64_t *coords, const doub
         }
         off[size_t(s)] = o;
     }
+    // levels: sources whose stencils (vertex and its 2d neighbours) meet add in index order
+    std::vector<int32_t> lvl(static_cast<size_t>(ns), 0);
+    int nlev = ns > 0 ? 1 : 0;
+    for (int s = 0; s < ns; ++s) {
+        for (int t = 0; t < s; ++t) {
+            int64_t d = 0;
+            for (int a = 0; a < c->nd; ++a) {
+                const int64_t e = std::llabs(int64_t(xyz[size_t(3 * s + a)]) - xyz[size_t(3 * t + a)]);
+                d += std::min<int64_t>(e, c->T[a] - e);
+            }
+            if (d <= 2) lvl[size_t(s)] = std::max(lvl[size_t(s)], lvl[size_t(t)] + 1);
+        }
+        nlev = std::max(nlev, lvl[size_t(s)] + 1);
+    }
     if (ns > 0) {
         PML_CU(c, cudaMemcpy(c->dsrc_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "sources");
         PML_CU(c, cudaMemcpy(c->dsrc_xyz, xyz.data(), xyz.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "sources");
+        PML_CU(c, cudaMemcpy(c->dsrc_level, lvl.data(), lvl.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "sources");
         PML_CU(c, cudaMemcpy(c->dsrc_amp, amp, size_t(ns) * sizeof(double), cudaMemcpyHostToDevice), "sources");
     }
     c->ns = ns;
+    c->src_levels = nlev;
     c->f_peak = f_peak;
     c->t_delay = t_delay;
     return PML_OK;
@@ -1102,18 +1131,28 @@ pml_status pml_set_receivers(pml_ctx *c, int nr, const int64_t *coords, void *tr
     if (nr < 0 || nr > kMaxReceivers) return fail(c, PML_EINVAL, "0 <= nr <= %d", kMaxReceivers);
     if (nr > 0 && (!coords || !trace_buf || capacity < 0)) return fail(c, PML_EINVAL, "receiver arguments");
     std::vector<int64_t> off(static_cast<size_t>(nr));
+    std::vector<int32_t> xyz(size_t(3 * nr), 0), lvl(static_cast<size_t>(nr), 0);
     const int64_t st[3] = {1, c->g.P, c->g.PS};
+    int nlev = nr > 0 ? 1 : 0;
     for (int r = 0; r < nr; ++r) {
         int64_t o = 0;
         for (int a = 0; a < c->nd; ++a) {
             const int64_t x = coords[r * c->nd + a];
             if (x < 0 || x >= c->T[a]) return fail(c, PML_EINVAL, "receiver %d outside the box", r);
             o += x * st[a];
+            xyz[size_t(3 * r + a)] = int32_t(x);
         }
         off[size_t(r)] = o;
+        for (int q = 0; q < r; ++q)   // receivers at one vertex inject in index order
+            if (off[size_t(q)] == o) lvl[size_t(r)] = std::max(lvl[size_t(r)], lvl[size_t(q)] + 1);
+        nlev = std::max(nlev, lvl[size_t(r)] + 1);
     }
-    if (nr > 0)
+    if (nr > 0) {
         PML_CU(c, cudaMemcpy(c->drec_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "receivers");
+        PML_CU(c, cudaMemcpy(c->drec_xyz, xyz.data(), xyz.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "receivers");
+        PML_CU(c, cudaMemcpy(c->drec_level, lvl.data(), lvl.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "receivers");
+    }
+    c->rec_levels = nlev;
     c->nr = nr;
     c->trace = trace_buf;
     c->trace_cap = capacity;
