@@ -311,8 +311,8 @@ struct Layer2DArgs {
 };
 // 2D layer work items: one strip of layer2d_tile_cols() output columns (one warp, halo
 // 4 columns per side) by a run of rows, taken by the warps from a work queue
-constexpr int kLayer2BandRows = 64;  // most output rows of one item of the y band
-constexpr int kLayer2SlabRows = 32;  // most output rows of one item of an x slab
+constexpr int kLayer2BandRows = 32;  // most output rows of one item of the y band
+constexpr int kLayer2SlabRows = 24;  // most output rows of one item of an x slab
 constexpr int kLayer2BandRowsTB = 32;  // the same for the frames of two-step blocks
 constexpr int kLayer2SlabRowsTB = 24;
 int layer2d_grid(int prec, int ntiles, int sm_count);   // CTAs of one layer launch (warps loop over items)
