@@ -300,6 +300,7 @@ def run_ours(args, ws, rank, local):
         wl3 = wk.cfg3() if args.n3 is None else wk.cfg3(N=args.n3)
         K3 = max(K // 20, 10)
         s = PMLSolver(wl3.N, wl3.w, dt=wl3.dt, precision=32, device=dev)
+        var3, tune3 = autotune.tune(s, steps=5, use_cache=not args.retune)   # tile kernel or level passes
         u3 = torch.from_numpy(wk.initial_field(wl3, dtype=np.float32)).to(dev)
         s.set_initial(u3)
         src = wl3.sources
@@ -315,6 +316,8 @@ def run_ours(args, ws, rank, local):
         d3 = {"workload": "3D %d^3 interior + %d-cell quadratic PML (T = %d^3), Gaussian s=6 + 8 Ricker sources, FP32"
                           % (wl3.N[0], wl3.w, wl3.T[0]),
               "value": pts3 * K3 * ws / (ms3 / 1e3) / 1e9, "unit": UNIT, "steps": K3, "ms_per_step": ms3 / K3,
+              "layer_variant": {0: "z-streaming tile kernel", 1: "level passes"}.get(var3, var3),
+              "autotune_ms_per_step": tune3,
               "roofline": {"bound": "hbm", "kernel": "k_interior3d<float>", "achieved": ach3, "peak": hbm_peak,
                            "unit": "GB/s", "frac": ach3 / hbm_peak, "avg_launch_ms": t_int3 * 1e3,
                            "bytes_per_launch": int3 * 16},

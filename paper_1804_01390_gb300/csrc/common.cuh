@@ -404,6 +404,22 @@ struct Layer3DArgs {
 constexpr int kLayer3TXf = 28, kLayer3TYf = 9;   // FP32: 36 x 17 region columns (20 warps)
 constexpr int kLayer3TXd = 12, kLayer3TYd = 4;   // FP64: 20 x 12 region columns
 constexpr int kLayer3LZ = 64;
+// The 3D frame by level passes (frame3d.cu): one Horner level per launch over dense
+// scratch buffers, on the frame widened by level - 1; tiles of kLevel3TX x kLevel3TY
+// columns by kLevel3TZ planes, one CTA each.
+struct Level3Args {
+    Geom g;
+    LayerConst k;
+    const void *sig[3];
+    const void *in[8];         // the level's operand (the state y for level 4), by global field id
+    const void *base[8];       // the state y
+    void *out[8];
+    const LayerTile *tiles;    // flags: axes whose aux fields reach the tile
+    int ntiles;
+    int level;                 // 4, 3, 2, 1: out = y + (dt / level) A in
+};
+constexpr int kLevel3TX = 32, kLevel3TY = 8, kLevel3TZ = 16;
+cudaError_t launch_level3d(int prec, bool adjoint, const Level3Args &a, cudaStream_t st);
 int layer3d_tile_x(int prec);
 int layer3d_tile_y(int prec);
 // The eight class launches follow each other with programmatic dependent launch (their

@@ -40,6 +40,9 @@ struct Plan {
     size_t adj[2][8] = {};
     size_t mid[8] = {};          // two-step blocks (2D FP32): first-step values of the widened frame
     bool tb2 = false;
+    size_t lvl[2][8] = {};       // 3D level passes: two scratch states
+    size_t ltiles[2][4] = {};    // 3D level passes: tiles of each level, forward / transposed
+    size_t max_ltiles = 0;
     size_t sig[3] = {};
     size_t tiles = 0, tiles_adj = 0, max_tiles = 0, tiles_l1 = 0, tiles_l2 = 0;
     size_t partials = 0, normout = 0, err = 0, queue = 0;
@@ -98,6 +101,9 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
     p->tb2 = p->nd == 2 && interior2d_tb2_variants(prec) > 0;
     if (p->tb2)
         for (int f = 0; f < p->nf; ++f) { p->mid[f] = off; off += fb; }
+    if (p->nd == 3)
+        for (int s = 0; s < 2; ++s)
+            for (int f = 0; f < p->nf; ++f) { p->lvl[s][f] = off; off += fb; }
     for (int a = 0; a < p->nd; ++a) { p->sig[a] = off; off += align_up(size_t(p->T[a]) * p->esz, kAlign); }
     p->max_tiles = tile_bound(p->nd, prec, p->T);
     p->tiles = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
@@ -105,6 +111,15 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
     if (p->tb2) {
         p->tiles_l1 = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
         p->tiles_l2 = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+    }
+    if (p->nd == 3) {
+        p->max_ltiles = size_t(3) * size_t(p->T[0] / kLevel3TX + 2) * size_t(p->T[1] / kLevel3TY + 2) *
+                        size_t(p->T[2] / kLevel3TZ + 3);
+        for (int d = 0; d < ((flags & PML_FLAG_ADJOINT) ? 2 : 1); ++d)
+            for (int k = 0; k < 4; ++k) {
+                p->ltiles[d][k] = off;
+                off += align_up(p->max_ltiles * sizeof(LayerTile), kAlign);
+            }
     }
     p->partials = off; off += align_up(size_t(kNormBlocks) * kNormVals * sizeof(double), kAlign);
     p->normout = off; off += kAlign;
@@ -171,6 +186,11 @@ struct pml_ctx {
     LayerTile *dtiles_l1 = nullptr, *dtiles_l2 = nullptr;
     int ntiles_l1 = 0, ntiles_l2 = 0;
     Range ir_tb[3];
+    // 3D: variant 1 advances the layer frame by level passes (frame3d.cu) instead of the
+    // z-streaming tile kernel: scratch states and each level's tiles (forward / transposed)
+    void *lvl[2][8] = {};
+    LayerTile *dlt[2][4] = {};
+    int nlt[2][4] = {};
     // kernel timing (pml_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs
@@ -432,6 +452,34 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
     return t;
 }
 
+// Tiles of the 3D level passes over the frame of `ir`: kLevel3TX x kLevel3TY columns by
+// kLevel3TZ planes (z unwrapped across the periodic seam, as in frame_rects), with the set of
+// axes whose aux fields reach the tile and its one-vertex neighbourhood.
+std::vector<LayerTile> level_tiles(const pml_ctx *c, const Range *ir)
+{
+    std::vector<LayerTile> t;
+    for (const Rect &r : frame_rects(c, ir))
+        for (int64_t z0 = r.lo[2]; z0 <= r.hi[2]; z0 += kLevel3TZ)
+            for (int64_t y0 = r.lo[1]; y0 <= r.hi[1]; y0 += kLevel3TY)
+                for (int64_t x0 = r.lo[0] & ~int64_t(kLevel3TX - 1); x0 <= r.hi[0]; x0 += kLevel3TX) {
+                    LayerTile L{};
+                    L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = int32_t(z0);
+                    L.xlo = int32_t(std::max<int64_t>(x0, r.lo[0]));
+                    L.xhi = int32_t(std::min<int64_t>(x0 + kLevel3TX - 1, r.hi[0]));
+                    L.ylo = int32_t(y0);
+                    L.yhi = int32_t(std::min<int64_t>(y0 + kLevel3TY - 1, r.hi[1]));
+                    L.zlo = int32_t(z0);
+                    L.zhi = int32_t(std::min<int64_t>(z0 + kLevel3TZ - 1, r.hi[2]));
+                    int fl = 0;
+                    if (axis_active(c, 0, L.xlo - 2, L.xhi + 3)) fl |= 1;
+                    if (axis_active(c, 1, L.ylo - 2, L.yhi + 3)) fl |= 2;
+                    if (axis_active(c, 2, L.zlo - 2, L.zhi + 3)) fl |= 4;
+                    L.flags = fl;
+                    t.push_back(L);
+                }
+    return t;
+}
+
 pml_status encode_map(pml_ctx *c, CUtensorMap *m, void *base, const uint32_t *box)
 {
     if (!g_encode) {
@@ -596,26 +644,52 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
     } else {
         // layer classes first (chained), then the interior kernel overlapping them; all
         // read only the step's input and write disjoint outputs
-        Layer3DArgs l{};
-        l.g = c->g; l.k = layer_const(c);
-        for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
-        l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
-        l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
-        for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
-        l.err = c->derr;
-        long pi = prof_begin(c, 1);
-        e = launch_layer3d(c->prec, adjoint, tl, out, l, c->st);
-        prof_end(c, pi);
-        if (e != cudaSuccess) return cuda_fail(c, e, "layer 3D kernel");
+        bool layer_launched;
+        if (c->ivar == 1) {   // level passes: z4, z3, z2 into the scratch states, then y'
+            void **in = adjoint ? c->adj[p] : c->fld[p];
+            const int d = adjoint ? 1 : 0;
+            Level3Args L{};
+            L.g = c->g; L.k = layer_const(c);
+            for (int a2 = 0; a2 < 3; ++a2) L.sig[a2] = c->dsig[a2];
+            for (int f = 0; f < 8; ++f) L.base[f] = in[f];
+            layer_launched = false;
+            for (int k = 0; k < 4; ++k) {
+                for (int f = 0; f < 8; ++f) {
+                    L.in[f] = k == 0 ? in[f] : c->lvl[(k - 1) & 1][f];
+                    L.out[f] = k == 3 ? out[f] : c->lvl[k & 1][f];
+                }
+                L.tiles = c->dlt[d][k];
+                L.ntiles = c->nlt[d][k];
+                L.level = 4 - k;
+                long pi = prof_begin(c, 1);
+                e = launch_level3d(c->prec, adjoint, L, c->st);
+                prof_end(c, pi);
+                if (e != cudaSuccess) return cuda_fail(c, e, "level pass 3D kernel");
+                layer_launched = layer_launched || L.ntiles > 0;
+            }
+        } else {
+            Layer3DArgs l{};
+            l.g = c->g; l.k = layer_const(c);
+            for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
+            l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
+            l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
+            for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
+            l.err = c->derr;
+            long pi = prof_begin(c, 1);
+            e = launch_layer3d(c->prec, adjoint, tl, out, l, c->st);
+            prof_end(c, pi);
+            if (e != cudaSuccess) return cuda_fail(c, e, "layer 3D kernel");
+            layer_launched = l.ntiles > 0;
+        }
         Interior3DArgs a{};
         a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
         int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
         a.queue = c->dqueue + (adjoint ? 2 : 0);
         a.parity = int(nl & 1);
         if (!range_empty(ir[0]) && !range_empty(ir[1]) && !range_empty(ir[2])) ++nl;
-        pi = prof_begin(c, 0);
+        const long pi = prof_begin(c, 0);
         e = launch_interior3d(c->prec, adjoint, &ti[0], &ti[1], out[0], out[1], a,
-                              adjoint ? c->grid_int_adj : c->grid_int, l.ntiles > 0 && !c->prof_on, c->st);
+                              adjoint ? c->grid_int_adj : c->grid_int, layer_launched && !c->prof_on, c->st);
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "interior 3D kernel");
     }
@@ -668,7 +742,8 @@ pml_status enqueue_double_step(pml_ctx *c, int p)
     return PML_OK;
 }
 
-int one_step_variants(const pml_ctx *c) { return c->nd == 2 ? interior2d_variants(c->prec) : 1; }
+// 2D: the interior kernel's shapes; 3D: 0 the z-streaming layer tile kernel, 1 level passes
+int one_step_variants(const pml_ctx *c) { return c->nd == 2 ? interior2d_variants(c->prec) : 2; }
 int two_step_variants(const pml_ctx *c) { return c->plan.tb2 ? interior2d_tb2_variants(c->prec) : 0; }
 
 // Grid sizes of the interior kernels for the current variant: all resident CTAs.
@@ -819,6 +894,9 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         c->dtiles_l1 = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l1);
         c->dtiles_l2 = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l2);
     }
+    if (c->nd == 3)
+        for (int s2 = 0; s2 < 2; ++s2)
+            for (int f = 0; f < c->nf; ++f) c->lvl[s2][f] = c->ws + plan.lvl[s2][f];
     for (int a = 0; a < c->nd; ++a) c->dsig[a] = c->ws + plan.sig[a];
     c->dtiles = reinterpret_cast<LayerTile *>(c->ws + plan.tiles);
     c->dtiles_adj = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_adj);
@@ -868,6 +946,25 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         if (e == cudaSuccess && !ta.empty() && (flags & PML_FLAG_ADJOINT))
             e = cudaMemcpy(c->dtiles_adj, ta.data(), ta.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cuda_fail(c, e, "upload tiles"); return bail(PML_ECUDA); }
+    }
+    // 3D level passes: level 4 - k on the frame of the run shrunk by 3 - k
+    if (c->nd == 3) {
+        for (int d = 0; d < ((flags & PML_FLAG_ADJOINT) ? 2 : 1); ++d)
+            for (int k = 0; k < 4; ++k) {
+                Range rr[3];
+                for (int a = 0; a < 3; ++a) rr[a] = shrink_run(d ? c->ir_adj[a] : c->ir[a], c->T[a], 3 - k);
+                std::vector<LayerTile> lt = level_tiles(c, rr);
+                if (lt.size() > plan.max_ltiles) {
+                    fail(c, PML_ENOMEM, "level tile table exceeds its bound");
+                    return bail(PML_ENOMEM);
+                }
+                c->dlt[d][k] = reinterpret_cast<LayerTile *>(c->ws + plan.ltiles[d][k]);
+                c->nlt[d][k] = int(lt.size());
+                cudaError_t e = lt.empty() ? cudaSuccess
+                                           : cudaMemcpy(c->dlt[d][k], lt.data(), lt.size() * sizeof(LayerTile),
+                                                        cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) { cuda_fail(c, e, "upload level tiles"); return bail(PML_ECUDA); }
+            }
     }
     // two-step blocks: the second pass writes the frame of the run shrunk by 2, from first-
     // step values the first pass writes on the frame of the run shrunk by 6 (4 more: the
