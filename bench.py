@@ -214,6 +214,12 @@ def run_ours(args, ws, rank, local):
     achieved = bytes_per_launch / avg_launch_s / 1e9
     # the same launch counted per point-update at the one-step figure (16 B per update)
     effective = bytes_per_launch * tb / avg_launch_s / 1e9
+    # DRAM traffic of the dominant kernel from an ncu capture of this very kernel shape
+    # (variant 6, k_interior2d_tb2<float, 4, 3, 6, 2, 128>) on the 6144^2 case: 335.6 MB read
+    # + 256.8 MB written per launch over 6134^2 vertices, scaled by the vertices per launch
+    traffic = None
+    if tb == 2 and variant == 6:
+        traffic = (335.6e6 + 256.8e6) * interior_pts / 6134.0 ** 2
     launches = int(n_k.sum())
     layer_share = float(ms_k[1] / max(ms_k.sum(), 1e-30))
 
@@ -520,7 +526,10 @@ def run_ours(args, ws, rank, local):
                        "l2": "inputs larger than L2 (U and V are 272 MB each; 1.09 GB state read + written "
                              "per pass, one pass per %d step%s)" % (tb, "s" if tb > 1 else ""), "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "traffic_note": ("ncu dram bytes read + written of the same kernel shape on the 6144^2 case, "
+                                          "scaled by vertices per launch" if traffic else
+                                          "no capture of the chosen kernel shape"),
                          "kernel": "k_interior2d_tb2<float>" if tb == 2 else "k_interior2d<float>",
                          "steps_per_launch": tb, "bytes_per_launch": bytes_per_launch,
                          "bytes_rule": "16 B per vertex per launch (U, V read and written once)",
