@@ -212,6 +212,9 @@ pml_status pml_query_sigma(const pml_ctx *ctx, int axis, double *sigma);
  *   adjoint state (dJ/dU at the adjoint clock) is copied to grad_u (device dense T-grid,
  *   context precision), and if grad_amp is not NULL the accumulated dJ/da (host, FP64,
  *   [ns]) is copied there (synchronising).
+ *   With a two-step variant selected and neither a residual nor sources (nothing injected
+ *   or accumulated between steps), the transposed steps advance two per pass, as pml_step
+ *   does.
  */
 pml_status pml_adjoint_reset(pml_ctx *ctx);
 pml_status pml_adjoint_step(pml_ctx *ctx, int64_t n, const void *residual, void *grad_u,

@@ -287,15 +287,15 @@ int interior2d_max_blocks_per_sm(int prec, bool adjoint, int v);
 cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *tmU, const CUtensorMap *tmV,
                               void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
                               bool overlap_previous);
-// Two forward steps per pass (temporal blocking depth 2) over the run given in a.xr, a.yr
-// (the layer-free run shrunk by 2 where a layer bounds it); FP32 only (variants() = 0 for
-// FP64).  Its TMA box is interior2d_tb2_box_cols(prec, v) x interior2d_tb2_box_rows(prec, v).
+// Two steps per pass (temporal blocking depth 2; forward or transposed) over the run given
+// in a.xr, a.yr (the layer-free run shrunk by 2 where a layer bounds it); FP32 only
+// (variants() = 0 for FP64).  Its TMA box is interior2d_tb2_box_cols(prec, v) x interior2d_tb2_box_rows(prec, v).
 int interior2d_tb2_variants(int prec);
 int interior2d_tb2_box_rows(int prec, int v);
 int interior2d_tb2_box_cols(int prec, int v);
-int interior2d_tb2_max_blocks_per_sm(int prec, int v);
-cudaError_t launch_interior2d_tb2(int prec, int v, const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo,
-                                  void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
+int interior2d_tb2_max_blocks_per_sm(int prec, bool adjoint, int v);
+cudaError_t launch_interior2d_tb2(int prec, bool adjoint, int v, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                                  void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
                                   bool overlap_previous);
 
 // Layer step of 2D strips (Horner form of the RK4 polynomial with the full operator).

@@ -44,7 +44,7 @@ struct Plan {
     size_t ltiles[2][4] = {};    // 3D level passes: tiles of each level, forward / transposed
     size_t max_ltiles = 0;
     size_t sig[3] = {};
-    size_t tiles = 0, tiles_adj = 0, max_tiles = 0, tiles_l1 = 0, tiles_l2 = 0;
+    size_t tiles = 0, tiles_adj = 0, max_tiles = 0, tiles_l1 = 0, tiles_l2 = 0, tiles_l1_adj = 0, tiles_l2_adj = 0;
     size_t partials = 0, normout = 0, err = 0, queue = 0;
     size_t src_off = 0, src_xyz = 0, src_amp = 0, grad = 0, rec_off = 0, src_level = 0, rec_xyz = 0, rec_level = 0;
     size_t total = 0;
@@ -111,6 +111,10 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
     if (p->tb2) {
         p->tiles_l1 = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
         p->tiles_l2 = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+        if (flags & PML_FLAG_ADJOINT) {
+            p->tiles_l1_adj = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+            p->tiles_l2_adj = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
+        }
     }
     if (p->nd == 3) {
         p->max_ltiles = size_t(3) * size_t(p->T[0] / kLevel3TX + 2) * size_t(p->T[1] / kLevel3TY + 2) *
@@ -162,8 +166,9 @@ struct pml_ctx {
     double *dpart = nullptr, *dnorm = nullptr, *dgrad = nullptr;
     DeviceError *derr = nullptr;
     int *dqueue = nullptr;              // work counters: interior fwd 0/1, adj 2/3; 2D layer fwd 4/5, adj 6/7,
-                                        // second layer pass of a two-step block 8/9
-    int64_t launches_fwd = 0, launches_adj = 0, launches_layer_fwd = 0, launches_layer_adj = 0, launches_layer2 = 0;
+                                        // second layer pass of a two-step block 8/9 (transposed 10/11)
+    int64_t launches_fwd = 0, launches_adj = 0, launches_layer_fwd = 0, launches_layer_adj = 0, launches_layer2 = 0,
+            launches_layer2_adj = 0;
     int ns = 0, nr = 0;
     int64_t *dsrc_off = nullptr, *drec_off = nullptr;
     int32_t *dsrc_xyz = nullptr, *dsrc_level = nullptr, *drec_xyz = nullptr, *drec_level = nullptr;
@@ -180,12 +185,12 @@ struct pml_ctx {
     // temporal blocking depth 2 (2D FP32): forward steps without sources or receiver rows
     // advance two at a time (layer pass 1 on the frame widened by 6 into mid, layer pass 2
     // on the frame widened by 2, two-step interior kernel on the run shrunk by 2)
-    int tb = 1, tbvar = 0, grid_tb = 0;
+    int tb = 1, tbvar = 0, grid_tb = 0, grid_tb_adj = 0;
     void *mid[8] = {};
-    CUtensorMap tm_mid[8], tm_tb[2][2];
-    LayerTile *dtiles_l1 = nullptr, *dtiles_l2 = nullptr;
-    int ntiles_l1 = 0, ntiles_l2 = 0;
-    Range ir_tb[3];
+    CUtensorMap tm_mid[8], tm_tb[2][2], tm_tb_adj[2][2];
+    LayerTile *dtiles_l1 = nullptr, *dtiles_l2 = nullptr, *dtiles_l1_adj = nullptr, *dtiles_l2_adj = nullptr;
+    int ntiles_l1 = 0, ntiles_l2 = 0, ntiles_l1_adj = 0, ntiles_l2_adj = 0;
+    Range ir_tb[3], ir_tb_adj[3];
     // 3D: variant 1 advances the layer frame by level passes (frame3d.cu) instead of the
     // z-streaming tile kernel: scratch states and each level's tiles (forward / transposed)
     void *lvl[2][8] = {};
@@ -702,43 +707,52 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
 //                 early, it waits for pass 1 before reading;
 //   interior:     steps n+1, n+2 in one pass on the run shrunk by 2, fld[p] -> fld[1-p];
 //                 launched while pass 2 runs, it completes only after pass 2.
-pml_status enqueue_double_step(pml_ctx *c, int p)
+pml_status enqueue_double_step(pml_ctx *c, bool adjoint, int p)
 {
     const int q = 1 - p;
     StepCoef k;
-    step_coef(c, false, &k);
+    step_coef(c, adjoint, &k);
+    void **out = adjoint ? c->adj[q] : c->fld[q];
     Layer2DArgs l{};
     l.g = c->g; l.k = layer_const(c);
     l.sig[0] = c->dsig[0]; l.sig[1] = c->dsig[1];
     l.err = c->derr;
-    l.tiles = c->dtiles_l1; l.ntiles = c->ntiles_l1;
-    l.queue = c->dqueue + 4;
-    l.parity = int(c->launches_layer_fwd & 1);
-    if (l.ntiles > 0) ++c->launches_layer_fwd;
+    l.tiles = adjoint ? c->dtiles_l1_adj : c->dtiles_l1;
+    l.ntiles = adjoint ? c->ntiles_l1_adj : c->ntiles_l1;
+    int64_t &ll = adjoint ? c->launches_layer_adj : c->launches_layer_fwd;
+    l.queue = c->dqueue + (adjoint ? 6 : 4);
+    l.parity = int(ll & 1);
+    if (l.ntiles > 0) ++ll;
     long pi = prof_begin(c, 1);
-    cudaError_t e = launch_layer2d(c->prec, false, c->tm_lay[p], c->mid, l, layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st);
+    cudaError_t e = launch_layer2d(c->prec, adjoint, adjoint ? c->tm_lay_adj[p] : c->tm_lay[p], c->mid, l,
+                                   layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st);
     prof_end(c, pi);
     if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel (pass 1)");
     const bool pass1 = l.ntiles > 0;
-    l.tiles = c->dtiles_l2; l.ntiles = c->ntiles_l2;
-    l.queue = c->dqueue + 8;
-    l.parity = int(c->launches_layer2 & 1);
-    if (l.ntiles > 0) ++c->launches_layer2;
+    l.tiles = adjoint ? c->dtiles_l2_adj : c->dtiles_l2;
+    l.ntiles = adjoint ? c->ntiles_l2_adj : c->ntiles_l2;
+    int64_t &l2 = adjoint ? c->launches_layer2_adj : c->launches_layer2;
+    l.queue = c->dqueue + (adjoint ? 10 : 8);
+    l.parity = int(l2 & 1);
+    if (l.ntiles > 0) ++l2;
     pi = prof_begin(c, 1);
-    e = launch_layer2d(c->prec, false, c->tm_mid, c->fld[q], l, layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st,
+    e = launch_layer2d(c->prec, adjoint, c->tm_mid, out, l, layer2d_grid(c->prec, l.ntiles, c->sm_count), c->st,
                        pass1 && !c->prof_on);
     prof_end(c, pi);
     if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel (pass 2)");
     Interior2DArgs a{};
-    a.g = c->g; a.xr = c->ir_tb[0]; a.yr = c->ir_tb[1]; a.c = k; a.err = c->derr;
-    a.queue = c->dqueue + 0;
-    a.parity = int(c->launches_fwd & 1);
+    const Range *irt = adjoint ? c->ir_tb_adj : c->ir_tb;
+    a.g = c->g; a.xr = irt[0]; a.yr = irt[1]; a.c = k; a.err = c->derr;
+    int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
+    a.queue = c->dqueue + (adjoint ? 2 : 0);
+    a.parity = int(nl & 1);
+    const CUtensorMap *tt = adjoint ? c->tm_tb_adj[p] : c->tm_tb[p];
     pi = prof_begin(c, 0);
-    e = launch_interior2d_tb2(c->prec, c->tbvar, &c->tm_tb[p][0], &c->tm_tb[p][1], c->fld[q][0], c->fld[q][1], a,
-                              c->grid_tb, c->st, (pass1 || l.ntiles > 0) && !c->prof_on);
+    e = launch_interior2d_tb2(c->prec, adjoint, c->tbvar, &tt[0], &tt[1], out[0], out[1], a,
+                              adjoint ? c->grid_tb_adj : c->grid_tb, c->st, (pass1 || l.ntiles > 0) && !c->prof_on);
     prof_end(c, pi);
     if (e != cudaSuccess) return cuda_fail(c, e, "interior 2D kernel (two steps)");
-    if (!range_empty(a.xr) && !range_empty(a.yr)) ++c->launches_fwd;
+    if (!range_empty(a.xr) && !range_empty(a.yr)) ++nl;
     return PML_OK;
 }
 
@@ -758,9 +772,12 @@ pml_status interior_grids(pml_ctx *c)
     c->grid_int = bps * c->sm_count;
     c->grid_int_adj = bpa * c->sm_count;
     if (c->plan.tb2) {
-        const int bt = interior2d_tb2_max_blocks_per_sm(c->prec, c->tbvar);
-        if (bt <= 0) return fail(c, PML_ECUDA, "two-step interior kernel cannot be resident (shared memory / registers)");
+        const int bt = interior2d_tb2_max_blocks_per_sm(c->prec, false, c->tbvar);
+        const int bta = adj ? interior2d_tb2_max_blocks_per_sm(c->prec, true, c->tbvar) : 1;
+        if (bt <= 0 || bta <= 0)
+            return fail(c, PML_ECUDA, "two-step interior kernel cannot be resident (shared memory / registers)");
         c->grid_tb = bt * c->sm_count;
+        c->grid_tb_adj = bta * c->sm_count;
     }
     return PML_OK;
 }
@@ -774,8 +791,11 @@ pml_status encode_tb_maps(pml_ctx *c)
                        uint32_t(interior2d_tb2_box_rows(c->prec, c->tbvar)), 1};
     pml_status s;
     for (int p = 0; p < 2; ++p)
-        for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < 2; ++f) {
             if ((s = encode_map(c, &c->tm_tb[p][f], c->fld[p][f], box)) != PML_OK) return s;
+            if ((c->flags & PML_FLAG_ADJOINT) && (s = encode_map(c, &c->tm_tb_adj[p][f], c->adj[p][f], box)) != PML_OK)
+                return s;
+        }
     return PML_OK;
 }
 
@@ -893,6 +913,10 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         for (int f = 0; f < c->nf; ++f) c->mid[f] = c->ws + plan.mid[f];
         c->dtiles_l1 = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l1);
         c->dtiles_l2 = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l2);
+        if (flags & PML_FLAG_ADJOINT) {
+            c->dtiles_l1_adj = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l1_adj);
+            c->dtiles_l2_adj = reinterpret_cast<LayerTile *>(c->ws + plan.tiles_l2_adj);
+        }
     }
     if (c->nd == 3)
         for (int s2 = 0; s2 < 2; ++s2)
@@ -992,6 +1016,24 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         if (e == cudaSuccess && !t2.empty())
             e = cudaMemcpy(c->dtiles_l2, t2.data(), t2.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cuda_fail(c, e, "upload tiles"); return bail(PML_ECUDA); }
+        if (flags & PML_FLAG_ADJOINT) {   // the same for the transposed step's frames
+            for (int a = 0; a < 3; ++a) {
+                r6[a] = shrink_run(c->ir_adj[a], c->T[a], 6);
+                r2[a] = c->ir_tb_adj[a] = shrink_run(c->ir_adj[a], c->T[a], 2);
+            }
+            std::vector<LayerTile> a1 = build_tiles(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
+                                   a2 = build_tiles(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+            if (a1.size() > plan.max_tiles || a2.size() > plan.max_tiles) {
+                fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
+                return bail(PML_ENOMEM);
+            }
+            c->ntiles_l1_adj = int(a1.size());
+            c->ntiles_l2_adj = int(a2.size());
+            if (!a1.empty()) e = cudaMemcpy(c->dtiles_l1_adj, a1.data(), a1.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && !a2.empty())
+                e = cudaMemcpy(c->dtiles_l2_adj, a2.data(), a2.size() * sizeof(LayerTile), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { cuda_fail(c, e, "upload tiles"); return bail(PML_ECUDA); }
+        }
     }
     // tensor maps
     {
@@ -1266,7 +1308,7 @@ pml_status pml_step(pml_ctx *c, int64_t n)
         const int p = c->cur, q = 1 - p;
         // two steps per pass where nothing has to happen between the two
         if (c->tb == 2 && n - k >= 2 && c->ns == 0 && !(c->nr > 0 && c->trace_k < c->trace_cap)) {
-            pml_status s = enqueue_double_step(c, p);
+            pml_status s = enqueue_double_step(c, false, p);
             if (s != PML_OK) return s;
             c->cur = q;
             c->step += 2;
@@ -1367,6 +1409,15 @@ pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *g
     for (int64_t k = 0; k < n; ++k) {
         const int p = c->acur;
         const int64_t m = c->astep;
+        // two transposed steps per pass where nothing is injected or accumulated between them
+        if (c->tb == 2 && n - k >= 2 && c->ns == 0 && !(residual && c->nr > 0)) {
+            pml_status s = enqueue_double_step(c, true, p);
+            if (s != PML_OK) return s;
+            c->acur = 1 - p;
+            c->astep = m - 2;
+            ++k;
+            continue;
+        }
         const void *row = (residual && c->nr > 0)
                               ? static_cast<const char *>(residual) + size_t(k) * size_t(c->nr) * c->esz
                               : nullptr;

@@ -266,16 +266,16 @@ template <typename T, int NH> struct StepRing {
     T ul[3], ur[3], vl[3], vr[3], dul[3], dur[3], dvl[3], dvr[3];
 };
 
-template <typename T> struct FwdCoefP {
-    typename Pair<T>::P A1, A2, A3, A4, B2, B3, B4, B5;
+template <typename T> struct StepCoefP {
+    typename Pair<T>::P A1, A2, A3, A4, A5, B1, B2, B3, B4, B5;
 };
 
 // Row q of one step's input sits in R.u[j % 3], R.v[j % 3] (j = q mod 3 after unrolling):
 // its edge columns go to the neighbouring lanes; with d1 the differences of row q-1
 // follow, with d2 the step's new values of row q-2 are returned in uo, vo.  Same
-// arithmetic, in the same order, as the forward case of interior2d_seg.
-template <typename T, int NH>
-__device__ __forceinline__ void ring_push(StepRing<T, NH> &R, const FwdCoefP<T> &k, int j, bool d1, bool d2,
+// arithmetic, in the same order, as interior2d_seg (ADJ: the transposed step).
+template <typename T, bool ADJ, int NH>
+__device__ __forceinline__ void ring_push(StepRing<T, NH> &R, const StepCoefP<T> &k, int j, bool d1, bool d2,
                                           typename Pair<T>::P (&uo)[NH], typename Pair<T>::P (&vo)[NH])
 {
     using M = Pair<T>;
@@ -300,8 +300,13 @@ __device__ __forceinline__ void ring_push(StepRing<T, NH> &R, const FwdCoefP<T> 
 #pragma unroll
         for (int c = 0; c < NH; ++c) {
             const PT uc = R.u[J2][c], vc = R.v[J2][c], duc = R.du[J2][c], dvc = R.dv[J2][c];
-            uo[c] = M::add(uc, M::fma(k.A1, vc, M::fma(k.A2, duc, M::fma(k.A3, dvc, M::mul(k.A4, d2u[c])))));
-            vo[c] = M::add(vc, M::fma(k.B2, duc, M::fma(k.B3, dvc, M::fma(k.B4, d2u[c], M::mul(k.B5, d2v[c])))));
+            if (!ADJ) {
+                uo[c] = M::add(uc, M::fma(k.A1, vc, M::fma(k.A2, duc, M::fma(k.A3, dvc, M::mul(k.A4, d2u[c])))));
+                vo[c] = M::add(vc, M::fma(k.B2, duc, M::fma(k.B3, dvc, M::fma(k.B4, d2u[c], M::mul(k.B5, d2v[c])))));
+            } else {
+                uo[c] = M::add(uc, M::fma(k.A2, duc, M::fma(k.A3, dvc, M::fma(k.A4, d2u[c], M::mul(k.A5, d2v[c])))));
+                vo[c] = M::add(vc, M::fma(k.B1, uc, M::fma(k.B2, duc, M::fma(k.B3, dvc, M::mul(k.B5, d2v[c])))));
+            }
         }
     }
 }
@@ -337,7 +342,7 @@ __device__ __forceinline__ void stg_pairs(T *p, const typename Pair<T>::P (&v)[N
 // at column xs (ring and barrier conventions as in interior2d_seg).  NC = 4 columns per
 // lane (lanes 0 and 31 carry the 4-column halo, 120 outputs) or NC = 2 (lanes 0-1 and
 // 30-31, 56 outputs).
-template <typename T, int NC, int CH, int S>
+template <typename T, bool ADJ, int NC, int CH, int S>
 __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CUtensorMap *tmV, T *__restrict__ Uo,
                                                 T *__restrict__ Vo, const Interior2DArgs &a, int64_t xs, int64_t y0,
                                                 int cnt, unsigned char *wbase, uint64_t *bars, int lane,
@@ -353,8 +358,9 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
     constexpr int HL = 4 / NC;   // halo lanes per side
     const Geom &g = a.g;
     const StepCoefT<T> &kc = coef_of<T>(a.c);
-    const FwdCoefP<T> k{M::mk(kc.a1, kc.a1), M::mk(kc.a2, kc.a2), M::mk(kc.a3, kc.a3), M::mk(kc.a4, kc.a4),
-                        M::mk(kc.b2, kc.b2), M::mk(kc.b3, kc.b3), M::mk(kc.b4, kc.b4), M::mk(kc.b5, kc.b5)};
+    const StepCoefP<T> k{M::mk(kc.a1, kc.a1), M::mk(kc.a2, kc.a2), M::mk(kc.a3, kc.a3), M::mk(kc.a4, kc.a4),
+                         M::mk(kc.a5, kc.a5), M::mk(kc.b1, kc.b1), M::mk(kc.b2, kc.b2), M::mk(kc.b3, kc.b3),
+                         M::mk(kc.b4, kc.b4), M::mk(kc.b5, kc.b5)};
     const int n_in = cnt + 8;
     const int nch = (n_in + CH - 1) / CH;
     const int32_t tx = int32_t(xs - 4 + G);
@@ -393,7 +399,7 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
         lds_pairs<T, NH>(sV, RA.v[J0]);
         PT u1[NH], v1[NH];
         const bool a2 = !guard || q >= 4;
-        ring_push<T, NH>(RA, k, j, !guard || q >= 2, a2, u1, v1);
+        ring_push<T, ADJ, NH>(RA, k, j, !guard || q >= 2, a2, u1, v1);
         if (!a2) return;
         const int jb = j + 2;   // first-step row q-2 is row q-4 of the second step's input
 #pragma unroll
@@ -403,7 +409,7 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
         }
         PT uo[NH], vo[NH];
         const bool b2 = !guard || q >= 8;
-        ring_push<T, NH>(RB, k, jb, !guard || q >= 6, b2, uo, vo);
+        ring_push<T, ADJ, NH>(RB, k, jb, !guard || q >= 6, b2, uo, vo);
         if (!b2) return;
         if (!guard) {   // fast item: predicated vector stores
             if (out_lane) {
@@ -1330,7 +1336,7 @@ cudaError_t launch_interior2d(int prec, bool adjoint, int v, const CUtensorMap *
 
 // Two-step interior kernel: persistent CTAs of 4 warps take ROWS-row strip segments of
 // the shrunk run from the work queue, as k_interior2d does.
-template <typename T, int NC, int CH, int S, int MINB, int ROWS>
+template <typename T, bool ADJ, int NC, int CH, int S, int MINB, int ROWS>
 __global__ void __launch_bounds__(128, MINB)
     k_interior2d_tb2(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmV,
                      T *__restrict__ Uo, T *__restrict__ Vo, const Interior2DArgs a)
@@ -1384,7 +1390,7 @@ __global__ void __launch_bounds__(128, MINB)
             y0 = big + int64_t(sb) * SR;
             cnt = nrows - y0 < SR ? nrows - y0 : SR;
         }
-        if (!interior2d_seg2<T, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(OUT) * st, a.yr.lo + y0,
+        if (!interior2d_seg2<T, ADJ, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(OUT) * st, a.yr.lo + y0,
                                            int(cnt), wbase, bars[warp], lane, use))
             break;
     }
@@ -1392,13 +1398,13 @@ __global__ void __launch_bounds__(128, MINB)
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct I2TKernel {
+template <typename T, bool ADJ, int NC, int CH, int S, int MINB, int ROWS> struct I2TKernel {
     static constexpr size_t smem() { return size_t(4) * S * 2 * CH * 32 * NC * sizeof(T) + 128; }
     static cudaError_t prep()
     {
         static bool done = false;
         if (done) return cudaSuccess;
-        cudaError_t e = cudaFuncSetAttribute(k_interior2d_tb2<T, NC, CH, S, MINB, ROWS>,
+        cudaError_t e = cudaFuncSetAttribute(k_interior2d_tb2<T, ADJ, NC, CH, S, MINB, ROWS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         if (e == cudaSuccess) done = true;
         return e;
@@ -1407,7 +1413,7 @@ template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct I2TKerne
     {
         if (prep() != cudaSuccess) return 0;
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d_tb2<T, NC, CH, S, MINB, ROWS>, 128,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior2d_tb2<T, ADJ, NC, CH, S, MINB, ROWS>, 128,
                                                           smem()) != cudaSuccess)
             return 0;
         return n;
@@ -1427,7 +1433,7 @@ template <typename T, int NC, int CH, int S, int MINB, int ROWS> struct I2TKerne
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = overlap_previous ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, k_interior2d_tb2<T, NC, CH, S, MINB, ROWS>, *tmU, *tmV, (T *)Uo, (T *)Vo, a);
+        return cudaLaunchKernelEx(&cfg, k_interior2d_tb2<T, ADJ, NC, CH, S, MINB, ROWS>, *tmU, *tmV, (T *)Uo, (T *)Vo, a);
     }
 };
 
@@ -1440,30 +1446,33 @@ struct I2TVar {
 constexpr I2TVar kI2TVars32[] = {{4, 6, 4, 2, 128}, {4, 3, 6, 2, 128}, {2, 3, 6, 3, 128}};
 constexpr int kNI2TVars32 = sizeof(kI2TVars32) / sizeof(I2TVar);
 
-template <typename F> static auto with_i2t(int v, F &&f)
+template <bool ADJ, typename F> static auto with_i2t(int v, F &&f)
 {
     switch (v) {
-    case 0: return f(I2TKernel<float, 4, 6, 4, 2, 128>{});
-    case 1: return f(I2TKernel<float, 4, 3, 6, 2, 128>{});
-    default: return f(I2TKernel<float, 2, 3, 6, 3, 128>{});
+    case 0: return f(I2TKernel<float, ADJ, 4, 6, 4, 2, 128>{});
+    case 1: return f(I2TKernel<float, ADJ, 4, 3, 6, 2, 128>{});
+    default: return f(I2TKernel<float, ADJ, 2, 3, 6, 3, 128>{});
     }
 }
 
 int interior2d_tb2_variants(int prec) { return prec == 32 ? kNI2TVars32 : 0; }
 int interior2d_tb2_box_rows(int prec, int v) { return prec == 32 ? kI2TVars32[v].ch : 0; }
 int interior2d_tb2_box_cols(int prec, int v) { return prec == 32 ? 32 * kI2TVars32[v].nc : 0; }
-int interior2d_tb2_max_blocks_per_sm(int prec, int v)
+int interior2d_tb2_max_blocks_per_sm(int prec, bool adjoint, int v)
 {
     if (prec != 32) return 0;
-    return with_i2t(v, [](auto k) { return decltype(k)::occupancy(); });
+    auto occ = [](auto k) { return decltype(k)::occupancy(); };
+    return adjoint ? with_i2t<true>(v, occ) : with_i2t<false>(v, occ);
 }
 
-cudaError_t launch_interior2d_tb2(int prec, int v, const CUtensorMap *tmU, const CUtensorMap *tmV, void *Uo, void *Vo,
-                                  const Interior2DArgs &a, int grid, cudaStream_t st, bool overlap_previous)
+cudaError_t launch_interior2d_tb2(int prec, bool adjoint, int v, const CUtensorMap *tmU, const CUtensorMap *tmV,
+                                  void *Uo, void *Vo, const Interior2DArgs &a, int grid, cudaStream_t st,
+                                  bool overlap_previous)
 {
     if (prec != 32 || v < 0 || v >= kNI2TVars32) return cudaErrorInvalidValue;
     if (a.xr.lo > a.xr.hi || a.yr.lo > a.yr.hi || grid <= 0) return cudaSuccess;
-    return with_i2t(v, [&](auto k) { return decltype(k)::launch(tmU, tmV, Uo, Vo, a, grid, st, overlap_previous); });
+    auto go = [&](auto k) { return decltype(k)::launch(tmU, tmV, Uo, Vo, a, grid, st, overlap_previous); };
+    return adjoint ? with_i2t<true>(v, go) : with_i2t<false>(v, go);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1703,7 +1712,7 @@ __global__ void __launch_bounds__(128, MINB) k_interior2d_tb2_batch(const Batch2
         const int64_t y0 = a.yr.lo + int64_t(rb) * ROWS;
         const int64_t rem = a.yr.hi - y0 + 1;
         const int64_t xs = (a.xr.lo & ~int64_t(3)) + int64_t(OUT) * st;
-        if (!interior2d_seg2<T, NC, CH, S>(&d.tm_tb[b.parity][0], &d.tm_tb[b.parity][1],
+        if (!interior2d_seg2<T, false, NC, CH, S>(&d.tm_tb[b.parity][0], &d.tm_tb[b.parity][1],
                                            static_cast<T *>(d.out[b.parity][0]), static_cast<T *>(d.out[b.parity][1]),
                                            a, xs, y0, int(rem < ROWS ? rem : ROWS), wbase, bars[warp], lane, use))
             break;

@@ -289,3 +289,43 @@ def test_batch_two_step_equals_single_context_two_step():
     for x, y in zip(a, c):
         for f in range(6):
             assert torch.equal(x.read(f), y.read(f)), f
+
+
+# ------------------------------------------------------------------------------------
+# transposed steps
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N,w,wall", [((290, 61), 7, False), ((96, 130), 16, False), ((120, 90), 12, True),
+                                      ((64, 72), 0, False), ((5, 7), 3, False)])
+def test_two_step_transposed_matches_oracle(N, w, wall):
+    """One transposed step with receiver residuals (a nonzero adjoint state), then 12 more
+    with nothing injected: those pair up.  Against the oracle's adjoint with the same residual
+    rows (the first one nonzero)."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    from paper_1804_01390_gb300.solver import PMLSolver
+    rng = np.random.default_rng(sum(N) + w + 7)
+    T = tuple(n + 2 * w for n in N)
+    rec = [tuple(int(rng.integers(0, t)) for t in T) for _ in range(5)]
+    steps = 13
+    residual = np.zeros((steps, len(rec)))
+    residual[0] = rng.normal(size=len(rec))
+    s = PMLSolver(N, w, sigma="quadratic", sigma_max=2.0, precision=32, device=torch.device("cuda:0"),
+                  adjoint=True, wall=wall)
+    vs = _two_step_variants(s)
+    _lib.pml_set_variant(s.ctx, vs[0])
+    s.set_initial(torch.from_numpy(gaussian_u0(N, w, 3)))
+    s.set_receivers(rec, steps)
+    s.step(steps)
+    s.adjoint_reset()
+    s.adjoint_step(1, torch.from_numpy(residual[:1].copy()))
+    gu, _ = s.adjoint_step(steps - 1)
+    fields = [s.adjoint_read(k).double().cpu().numpy() for k in range(6)]
+    s.close()
+    g0 = oracle_grid(N, w)
+    if wall:
+        g0 = oracle.Grid(g0.T, 1.0, [np.concatenate([s_[:-1], [0.0]]) for s_ in g0.sigmas], wall=True)
+    yb, _ = oracle.adjoint(g0, g0.zeros_state(), steps, 0.5, steps, receivers=[g0.flat(c) for c in rec],
+                           residual=residual)
+    assert rel_l2(gu.double().cpu().numpy(), yb[0]) <= TOL[32]
+    for k, fk in enumerate(fields):
+        assert rel_l2(fk, yb[k]) <= TOL[32], (k, rel_l2(fk, yb[k]))
