@@ -275,6 +275,7 @@ struct Interior2DArgs {
     DeviceError *err;
     int *queue;
     int parity;
+    int rows;                  // rows per work item of the warp-streaming shape (0: its default)
 };
 // Variant v of the 2D interior kernel (see kI2Vars32 / kI2Vars64 in step2d.cu): its TMA
 // box is interior2d_box_cols(prec, v) x interior2d_box_rows(prec, v).

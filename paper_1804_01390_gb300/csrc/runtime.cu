@@ -70,7 +70,7 @@ Geom make_geom(int nd, const int64_t T[3], bool wall = false)
 size_t tile_bound(int nd, int prec, const int64_t T[3])
 {
     if (nd == 2)
-        return size_t(3) * size_t(T[0] / layer2d_tile_cols(prec) + 3) * size_t(T[1] / kLayer2SlabRowsTB + 2);
+        return size_t(3) * size_t(T[0] / layer2d_tile_cols(prec) + 3) * size_t(T[1] / 6 + 2);   // runs >= 6 rows
     const int TX = prec == 32 ? kLayer3TXf : kLayer3TXd, TY = prec == 32 ? kLayer3TYf : kLayer3TYd;
     return size_t(5) * size_t(T[0] / TX + 2) * size_t(T[1] / TY + 2) * size_t(T[2] / kLayer3LZ + 2);
 }
@@ -457,6 +457,20 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
     return t;
 }
 
+// 2D frame tiles: on small grids, where the default runs give fewer items than half the
+// warps of a full layer launch, proportionally shorter runs (down to 8 band / 6 slab rows):
+// a warp streams its item's rows one after another, so there the launch lasts as long as
+// its longest item.  (Below that point longer items win: a layer item has a start-up cost.)
+std::vector<LayerTile> build_tiles_2d(const pml_ctx *c, const Range *ir, int class_off[9],
+                                      int64_t band0 = kLayer2BandRows, int64_t slab0 = kLayer2SlabRows)
+{
+    std::vector<LayerTile> t = build_tiles(c, ir, class_off, band0, slab0);
+    const size_t target = size_t(8) * size_t(std::max(c->sm_count, 1));
+    if (c->nd != 2 || t.empty() || t.size() >= target) return t;
+    const double f = double(t.size()) / double(target);
+    return build_tiles(c, ir, class_off, std::max<int64_t>(8, int64_t(band0 * f)), std::max<int64_t>(6, int64_t(slab0 * f)));
+}
+
 // Tiles of the 3D level passes over the frame of `ir`: kLevel3TX x kLevel3TY columns by
 // kLevel3TZ planes (z unwrapped across the periodic seam, as in frame_rects), with the set of
 // axes whose aux fields reach the tile and its one-vertex neighbourhood.
@@ -636,6 +650,15 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel");
         Interior2DArgs a{};
         a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.c = k; a.err = c->derr;
+        // small grids: shorter work items (down to 16 rows) so that every warp of the launch
+        // gets one (a warp streams its item's rows one after another)
+        if (!range_empty(ir[0]) && !range_empty(ir[1])) {
+            const int64_t nrows = ir[1].hi - ir[1].lo + 1;
+            const int64_t nstrips = (ir[0].hi - (ir[0].lo & ~int64_t(3))) / 120 + 1;
+            const int64_t warps = int64_t(adjoint ? c->grid_int_adj : c->grid_int) * 4;
+            const int64_t items = nstrips * ((nrows + 63) / 64);
+            if (items < warps) a.rows = int(std::max<int64_t>(16, (nrows * nstrips + warps - 1) / warps));
+        }
         int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
         a.queue = c->dqueue + (adjoint ? 2 : 0);
         a.parity = int(nl & 1);
@@ -957,8 +980,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     }
     // layer tiles
     {
-        std::vector<LayerTile> tf = build_tiles(c, c->ir, c->class_off),
-                               ta = build_tiles(c, c->ir_adj, c->class_off_adj);
+        std::vector<LayerTile> tf = build_tiles_2d(c, c->ir, c->class_off),
+                               ta = build_tiles_2d(c, c->ir_adj, c->class_off_adj);
         if (tf.size() > plan.max_tiles || ta.size() > plan.max_tiles) {
             fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
             return bail(PML_ENOMEM);
@@ -1003,8 +1026,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         // interior kernel, so a pass lasts as long as its longest item; about one short item
         // per warp of a full launch
         int dummy[9];
-        std::vector<LayerTile> t1 = build_tiles(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
-                               t2 = build_tiles(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+        std::vector<LayerTile> t1 = build_tiles_2d(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
+                               t2 = build_tiles_2d(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
         if (t1.size() > plan.max_tiles || t2.size() > plan.max_tiles) {
             fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
             return bail(PML_ENOMEM);
@@ -1021,8 +1044,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
                 r6[a] = shrink_run(c->ir_adj[a], c->T[a], 6);
                 r2[a] = c->ir_tb_adj[a] = shrink_run(c->ir_adj[a], c->T[a], 2);
             }
-            std::vector<LayerTile> a1 = build_tiles(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
-                                   a2 = build_tiles(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+            std::vector<LayerTile> a1 = build_tiles_2d(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
+                                   a2 = build_tiles_2d(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
             if (a1.size() > plan.max_tiles || a2.size() > plan.max_tiles) {
                 fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
                 return bail(PML_ENOMEM);

@@ -1200,7 +1200,8 @@ __global__ void __launch_bounds__(128, MINB)
     uint32_t use = 0;
     const int64_t xs0 = a.xr.lo & ~int64_t(3);
     const int64_t nrows = a.yr.hi - a.yr.lo + 1;
-    const int rblocks = int((nrows + kI2Rows - 1) / kI2Rows);
+    const int R = a.rows > 0 ? a.rows : kI2Rows;
+    const int rblocks = int((nrows + R - 1) / R);
     const int nstrips = int((a.xr.hi - xs0) / (30 * NC) + 1);
     const int n_items = nstrips * rblocks;
     for (;;) {
@@ -1209,10 +1210,10 @@ __global__ void __launch_bounds__(128, MINB)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int st = item / rblocks, rb = item - st * rblocks;
-        const int64_t y0 = a.yr.lo + int64_t(rb) * kI2Rows;
+        const int64_t y0 = a.yr.lo + int64_t(rb) * R;
         const int64_t rem = a.yr.hi - y0 + 1;
         if (!interior2d_seg<T, ADJ, NC, CH, S>(&tmU, &tmV, Uo, Vo, a, xs0 + int64_t(30 * NC) * st, y0,
-                                               int(rem < kI2Rows ? rem : kI2Rows), wbase, bars[warp], lane, use))
+                                               int(rem < R ? rem : R), wbase, bars[warp], lane, use))
             break;
     }
     // When this launch overlapped the layer kernel, finish only after it: later work in the
