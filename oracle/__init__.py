@@ -173,7 +173,10 @@ def ricker(t, f_peak, t_delay):
 
 
 def sigma_profile(N, w, kind=KIND_POWER, sigma_max=2.0, order=2.0, draws=None):
-    """Edge-centred damping profile of length N + 2w (Sec. 1.1.2; readings in the design doc)."""
+    """Edge-centred damping profile of length N + 2w (Sec. 1.1.2): sigma[e] belongs to the
+    edge (e, e+1); the physical edges w-1 .. w+N-1 carry 0, the layer edges
+    sigma_max (d/w)^order with d the edge's depth into the layer (kind POWER), sigma_max
+    (CONSTANT) or sigma_max times a given uniform draw (RANDOM)."""
     T = int(N) + 2 * int(w)
     out = np.zeros(T, dtype=np.float64)
     d = None if draws is None else _f64(draws)

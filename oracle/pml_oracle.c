@@ -16,7 +16,7 @@
  * Compiled with -O2 -ffp-contract=off so every product and sum is rounded once, in
  * source order.
  *
- * Conventions (readings of the paper, listed in the design doc):
+ * Conventions (readings of the paper where it leaves a choice open):
  *   - axis a has T[a] vertices 0..T[a]-1, periodic; the physical vertices are
  *     w..w+N-1 and the layer vertices the other 2w;
  *   - sigma_a[e] is edge-centred: it belongs to the edge (e, e+1 mod T) - this is the

@@ -66,8 +66,9 @@ def test_single_rank_needs_no_process_group():
 
 
 def test_reference_arm_under_torchrun_two_ranks():
-    """`bench.py --impl reference` launched as the driver launches N > 1 runs: rank 0 runs the
-    oracle and prints exactly one JSON line, rank 1 exits 0 without work."""
+    """`bench.py --impl reference` launched with torchrun on two ranks (as N > 1 runs are
+    launched): rank 0 runs the oracle and prints exactly one JSON line, rank 1 exits 0
+    without work."""
     pytest.importorskip("torch.distributed.run")
     port = _free_port()
     env = dict(os.environ, OMP_NUM_THREADS="2")
