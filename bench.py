@@ -215,11 +215,11 @@ def run_ours(args, ws, rank, local):
     # the same launch counted per point-update at the one-step figure (16 B per update)
     effective = bytes_per_launch * tb / avg_launch_s / 1e9
     # DRAM traffic of the dominant kernel from an ncu capture of this very kernel shape
-    # (variant 6, k_interior2d_tb2<float, 4, 3, 6, 2, 128>) on the 6144^2 case: 335.6 MB read
-    # + 256.8 MB written per launch over 6134^2 vertices, scaled by the vertices per launch
+    # (variant 6, k_interior2d_tb2<float, false, 4, 3, 6, 2, 128>) on the 6144^2 case: 335.3 MB
+    # read + 256.8 MB written per launch over 6134^2 vertices, scaled by the vertices per launch
     traffic = None
     if tb == 2 and variant == 6:
-        traffic = (335.6e6 + 256.8e6) * interior_pts / 6134.0 ** 2
+        traffic = (335.3e6 + 256.8e6) * interior_pts / 6134.0 ** 2
     launches = int(n_k.sum())
     layer_share = float(ms_k[1] / max(ms_k.sum(), 1e-30))
 
