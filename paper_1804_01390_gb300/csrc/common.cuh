@@ -404,7 +404,7 @@ struct Layer3DArgs {
 // 3D layer column tiles (x, y output extent; halo 4 on each side) and z segment length
 constexpr int kLayer3TXf = 28, kLayer3TYf = 9;   // FP32: 36 x 17 region columns (20 warps)
 constexpr int kLayer3TXd = 12, kLayer3TYd = 4;   // FP64: 20 x 12 region columns
-constexpr int kLayer3LZ = 64;
+constexpr int kLayer3LZ = 32;
 // The 3D frame by level passes (frame3d.cu): one Horner level per launch over dense
 // scratch buffers, on the frame widened by level - 1; tiles of kLevel3TX x kLevel3TY
 // columns by kLevel3TZ planes, one CTA each.
