@@ -68,3 +68,23 @@ def test_batch_argument_checks_without_gpu(lib):
     assert L.pml_batch_set_variant(None, 0) == _lib.PML_EINVAL
     assert L.pml_batch_info(None, None) == _lib.PML_EINVAL
     L.pml_batch_destroy(None)
+
+
+def test_variant_and_time_block_queries_reject_null_without_gpu(lib):
+    """The variant and temporal-block queries check their arguments before any device
+    work; the two-step scratch state enlarges the 2D FP32 workspace only."""
+    import ctypes
+    from paper_1804_01390_gb300 import _lib
+    L = _lib.load()
+    d = ctypes.c_int(0)
+    assert L.pml_get_time_block(None, ctypes.byref(d)) == _lib.PML_EINVAL
+    assert L.pml_batch_get_time_block(None, ctypes.byref(d)) == _lib.PML_EINVAL
+    assert L.pml_get_variant(None, None, None) == _lib.PML_EINVAL
+    assert L.pml_set_variant(None, 0) == _lib.PML_EINVAL
+    # 2D FP32 holds a third state (the two-step blocks' first-step values): 3 states x 6
+    # fields x 4 B per vertex against FP64's 2 x 6 x 8 B, a ratio near 4/3 (2 without it)
+    b32 = _lib.pml_workspace_bytes(2, (2000, 2000), 16, 32)
+    b64 = _lib.pml_workspace_bytes(2, (2000, 2000), 16, 64)
+    field32 = (2032 + 8 + 31) // 32 * 32 * (2032 + 8) * 4
+    assert b32 >= 3 * 6 * field32
+    assert 1.25 < b64 / b32 < 1.45
