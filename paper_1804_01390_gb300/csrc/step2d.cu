@@ -219,10 +219,18 @@ __device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUt
         }
         const T *sU = reinterpret_cast<const T *>(wbase + slot * STAGE_BYTES) + NC * lane;
         const T *sV = sU + CH * ROW;
-        if (c == 0) {   // priming rows: differences start at q = 2, outputs at q = 4
+        if (c * CH < 4) {   // priming rows 0..3: differences start at q = 2, outputs at q = 4
+            if constexpr (CH >= 4) {   // box 0 holds them all
 #pragma unroll
-            for (int j = 0; j < CH; ++j)
-                if (j < n_in) row(sU + j * ROW, sV + j * ROW, j, j, j >= 2, j >= 4);
+                for (int j = 0; j < CH; ++j)
+                    if (j < n_in) row(sU + j * ROW, sV + j * ROW, j, j, j >= 2, j >= 4);
+            } else {                   // shallower boxes: every box that holds one of them
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int q = c * CH + j;
+                    if (q < n_in) row(sU + j * ROW, sV + j * ROW, j, q, q >= 2, q >= 4);
+                }
+            }
         } else if (c < nch - 1) {   // steady state: every row complete, no guards
 #pragma unroll
             for (int j = 0; j < CH; ++j) row(sU + j * ROW, sV + j * ROW, j, c * CH + j, true, true);

@@ -217,3 +217,44 @@ def test_full_size_batched_96_grids_sampled():
         err = rel_l2(got, want)
         assert err <= TOL[32], (k, err)
     b.close()
+
+
+def test_batch_of_wall_boxes_every_variant():
+    """A batch of contexts backed by reflecting walls (one-step and two-step shapes) against
+    the oracle's wall mode, per grid."""
+    import torch
+    from paper_1804_01390_gb300.solver import PMLBatch, PMLSolver
+    grids = [((60, 44), 6), ((23, 41), 1), ((90, 37), 9)]
+
+    def make():
+        solvers, inits = [], []
+        for k, (N, w) in enumerate(grids):
+            s = PMLSolver(N, w, sigma="quadratic", sigma_max=2.0, precision=32, device=torch.device("cuda:0"),
+                          wall=True)
+            u0, v0 = _initial(N, w, 500 + k)
+            s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
+            solvers.append(s)
+            inits.append((u0, v0))
+        return solvers, inits
+
+    probe, _ = make()
+    nvar = PMLBatch(probe).variant_count
+    for v in range(nvar):
+        solvers, inits = make()
+        b = PMLBatch(solvers)
+        b.set_variant(v)
+        b.step(35)
+        for k, ((N, w), s, (u0, v0)) in enumerate(zip(grids, solvers, inits)):
+            g0 = oracle_grid(N, w)
+            g = oracle.Grid(g0.T, 1.0, [np.concatenate([s_[:-1], [0.0]]) for s_ in g0.sigmas], wall=True)
+            y = g.zeros_state()
+            y[0] = u0.reshape(-1)
+            y[1] = v0.reshape(-1)
+            want, _ = oracle.rk4(g, y, 35, 0.5)
+            for f in range(6):
+                got = s.read(f).double().cpu().numpy()
+                err = rel_l2(got, want[f].reshape(got.shape))
+                assert err <= TOL[32], (v, k, f, err)
+        b.close()
+        for s in solvers:
+            s.close()

@@ -115,3 +115,28 @@ def test_wall_adjoint_parity(N, w):
     for f in range(nf):
         err = rel_l2(got[f], yb[f])
         assert err <= 1e-12, (f, err)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_wall_every_variant_2d(prec):
+    """Every kernel shape of a 2D context (one-step shapes, including those with 3-row TMA
+    boxes, and the two-step shapes) with reflecting walls against the oracle."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    N, w, steps = (70, 53), 3, 21
+    T, draws, sig, u0, v0 = _setup(N, w, "quadratic", seed=404)
+    g = oracle.Grid(T, 1.0, sig, wall=True)
+    y = g.zeros_state()
+    y[0] = u0.reshape(-1)
+    y[1] = v0.reshape(-1)
+    want, _ = oracle.rk4(g, y, steps, 0.5)
+    s = _solver(N, w, "quadratic", draws, prec)
+    _, nv = _lib.pml_get_variant(s.ctx)
+    for v in range(nv):
+        _lib.pml_set_variant(s.ctx, v)
+        s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
+        s.step(steps)
+        for f in range(6):
+            err = rel_l2(s.read(f).double().cpu().numpy(), want[f])
+            assert err <= TOL[prec], (v, f, err)
+    s.close()
