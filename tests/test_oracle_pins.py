@@ -448,6 +448,37 @@ def test_reflectionless_noise_random_sigma(orc):
     assert err < 1e-14, err
 
 
+def test_reflectionless_3d_random_sigma(orc):
+    """Thm 1.1 holds in any dimension: in 3D, with independent random damping per edge on
+    all three axes, a pulse near a corner (it crosses an interface of every axis) matches an
+    undamped box whose edges stay out of reach, to machine zero over the physical window."""
+    N, w, steps = 16, 16, 16
+    rng = np.random.default_rng(26)
+    T = N + 2 * w
+    sigs = [orc.sigma_profile(N, w, orc.KIND_RANDOM, 2.0, draws=rng.random(T)) for _ in range(3)]
+    wl = wk.Workload("t", 3, (N, N, N), w, gaussians=[wk.Gaussian((w + 3.0, w + 12.5, w + 2.5), 2.0, 2.0)])
+    u0 = wk.initial_field(wl)
+    g = orc.Grid((T, T, T), 1.0, sigs)
+    y = g.zeros_state()
+    y[0] = u0.reshape(-1)
+    yn, _ = orc.rk4(g, y, steps, 0.5)
+    M = 80
+    off = (M - N) // 2
+    ub = np.zeros((M, M, M))
+    ub[off:off + N, off:off + N, off:off + N] = u0[w:w + N, w:w + N, w:w + N]
+    gb = orc.Grid((M, M, M), 1.0, [np.zeros(M)] * 3)
+    yb = gb.zeros_state()
+    yb[0] = ub.reshape(-1)
+    ybn, _ = orc.rk4(gb, yb, steps, 0.5, openmp=True)
+    a = g.field(yn, 0)[w:w + N, w:w + N, w:w + N]
+    big = gb.field(ybn, 0)
+    b = big[off:off + N, off:off + N, off:off + N]
+    beyond = big.copy()
+    beyond[off:off + N, off:off + N, off:off + N] = 0.0
+    assert np.abs(b).max() > 1e-2 and np.abs(beyond).max() > 1e-2   # part of the pulse has left
+    assert np.abs(a - b).max() < 1e-14, np.abs(a - b).max()
+
+
 def test_residual_waves_shrink_with_thickness(orc):
     """Sec. 1.1.4: residual waves shrink exponentially as the layer thickens linearly."""
     N = 24
@@ -525,6 +556,22 @@ def test_adjoint_dot_product(orc):
     n = 7
     Px, _ = orc.rk4(g, x, n, 0.5)
     PTz, _ = orc.adjoint(g, z, n, 0.5, n)
+    lhs = float(np.sum(Px * z))
+    rhs = float(np.sum(x * PTz))
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_adjoint_dot_product_3d_random_sigma(orc):
+    rng = np.random.default_rng(27)
+    N, w = 4, 3
+    T = N + 2 * w
+    sigs = [orc.sigma_profile(N, w, orc.KIND_RANDOM, 2.0, draws=rng.random(T)) for _ in range(3)]
+    g = orc.Grid((T, T, T), 1.0, sigs)
+    x = _random_state(g, rng)
+    z = _random_state(g, rng)
+    n = 5
+    Px, _ = orc.rk4(g, x, n, 0.4)
+    PTz, _ = orc.adjoint(g, z, n, 0.4, n)
     lhs = float(np.sum(Px * z))
     rhs = float(np.sum(x * PTz))
     assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
