@@ -190,10 +190,9 @@ def _mode(T, m):
     return np.cos(th).reshape(-1)
 
 
-@pytest.mark.parametrize("T,m,dt", [((16, 12), (3, 2), 0.5), ((9, 8, 10), (2, 3, 4), 0.4),
-                                    ((32,), (7,), 0.9)])
-def test_rk4_single_mode_exact(orc, T, m, dt):
-    h = 1.0
+@pytest.mark.parametrize("T,m,dt,h", [((16, 12), (3, 2), 0.5, 1.0), ((9, 8, 10), (2, 3, 4), 0.4, 1.0),
+                                      ((32,), (7,), 0.9, 1.0), ((16, 12), (3, 2), 0.3, 0.6)])
+def test_rk4_single_mode_exact(orc, T, m, dt, h):
     g = orc.Grid(T, h, [np.zeros(t) for t in T])
     om2 = sum(4 * np.sin(np.pi * mm / t) ** 2 for mm, t in zip(m, T)) / h ** 2
     y = g.zeros_state()
@@ -213,6 +212,80 @@ def test_rk4_single_mode_exact(orc, T, m, dt):
     R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
     En = orc.energy(g, yn)
     assert abs(En - E0 * abs(R) ** (2 * n)) < 1e-11 * E0
+
+
+def test_wall_box_sine_mode_exact(orc):
+    """With reflecting walls (every field zero at the vertices -1 and T_a) and no damping,
+    products of sin(pi m_a (i_a + 1) / (T_a + 1)) are the eigenvectors of the discrete
+    Laplacian with eigenvalue -sum_a 4 sin^2(pi m_a / (2 (T_a + 1))) / h^2, so one mode
+    evolves by the 2 x 2 RK4 polynomial; a periodic seam at either end breaks this."""
+    T, m, h, dt, n = (13, 9), (3, 2), 0.8, 0.35, 29
+    g = orc.Grid(T, h, [np.zeros(t) for t in T], wall=True)
+    idx = np.indices(T[::-1])
+    u = np.ones(T[::-1])
+    for a in range(2):
+        u = u * np.sin(np.pi * m[a] * (idx[1 - a] + 1) / (T[a] + 1))
+    om2 = sum(4 * np.sin(np.pi * mm / (2 * (t + 1))) ** 2 for mm, t in zip(m, T)) / h ** 2
+    y = g.zeros_state()
+    y[0] = u.reshape(-1)
+    yn, _ = orc.rk4(g, y, n, dt)
+    M = np.array([[0, 1.0], [-om2, 0]])
+    P = np.eye(2) + dt * M + (dt * M) @ (dt * M) / 2 + np.linalg.matrix_power(dt * M, 3) / 6 \
+        + np.linalg.matrix_power(dt * M, 4) / 24
+    uv = np.linalg.matrix_power(P, n) @ np.array([1.0, 0.0])
+    assert np.abs(yn[0] - uv[0] * y[0]).max() < 1e-12
+    assert np.abs(yn[1] - uv[1] * y[0]).max() < 1e-12
+
+
+def test_energy_is_additive_over_windows(orc):
+    """eq:Energy is a sum of per-vertex terms: the windows [lo, k] and [k+1, hi] along any
+    axis add up to [lo, hi] (inclusive bounds, each vertex counted once)."""
+    rng = np.random.default_rng(28)
+    T = (11, 9, 7)
+    g = orc.Grid(T, 0.7, [np.zeros(t) for t in T])
+    y = g.zeros_state()
+    y[0] = rng.normal(size=g.n)
+    y[1] = rng.normal(size=g.n)
+    lo, hi = [1, 2, 0], [9, 7, 5]
+    whole = orc.energy(g, y, lo, hi)
+    for a in range(3):
+        k = (lo[a] + hi[a]) // 2
+        h1, l2 = list(hi), list(lo)
+        h1[a], l2[a] = k, k + 1
+        parts = orc.energy(g, y, lo, h1) + orc.energy(g, y, l2, hi)
+        assert abs(parts - whole) < 1e-12 * whole
+    assert orc.energy(g, y, [0, 0, 0], [t - 1 for t in T]) > whole
+
+
+def test_energy_of_a_point_at_the_window_corners(orc):
+    """eq:Energy by hand for U = u at one vertex p: the forward difference (tau_a U - U)/h
+    equals -u/h at p and +u/h at p - e_a, so each axis gives u^2/h^2 when both vertices
+    lie in the window (p at its upper corner) and u^2/(2h^2) when p - e_a lies outside it
+    (p at its lower corner)."""
+    T, h, u = (9, 8, 7), 0.6, 1.7
+    g = orc.Grid(T, h, [np.zeros(t) for t in T])
+    lo, hi = (2, 1, 3), (6, 5, 5)
+    for p, per_axis in ((hi, u * u / h ** 2), (lo, u * u / (2 * h ** 2))):
+        y = g.zeros_state()
+        y[0, g.flat(p)] = u
+        assert abs(orc.energy(g, y, lo, hi) - 3 * per_axis) < 1e-13 * per_axis
+
+
+def test_norms_over_a_window(orc):
+    """max |U|, the L2 norm and the L2 distance to a reference over an inclusive window,
+    against numpy on the same slice."""
+    rng = np.random.default_rng(29)
+    T = (13, 10)
+    g = orc.Grid(T, 1.0, [np.zeros(t) for t in T])
+    U = rng.normal(size=T[::-1])
+    ref = rng.normal(size=T[::-1])
+    lo, hi = (2, 3), (11, 8)
+    win = (slice(lo[1], hi[1] + 1), slice(lo[0], hi[0] + 1))
+    mx, l2, d2 = orc.norms(g, U, ref, lo, hi)
+    assert mx == np.abs(U[win]).max()
+    assert abs(l2 - np.linalg.norm(U[win])) < 1e-13 * l2
+    assert abs(d2 - np.linalg.norm(U[win] - ref[win])) < 1e-13 * d2
+    assert orc.norms(g, U, None, lo, hi)[2] == 0.0
 
 
 def test_energy_closed_form_velocity_mode(orc):
@@ -532,10 +605,14 @@ def test_long_run_bounded_energy_decays(orc, kind):
 
 def test_transpose_matches_dense(orc):
     rng = np.random.default_rng(23)
-    for T, w, nd in (((9,), 3, 1), ((7, 8), 2, 2), ((6, 5, 7), 2, 3)):
-        sigs = [orc.sigma_profile(t - 2 * w, w, orc.KIND_RANDOM, 2.0, draws=rng.random(t))
+    for T, w, nd, h, wall in (((9,), 3, 1, 1.0, False), ((7, 8), 2, 2, 1.0, False), ((6, 5, 7), 2, 3, 1.0, False),
+                              ((7, 8), 2, 2, 0.7, False), ((8, 7), 2, 2, 0.7, True)):
+        sigs = [orc.sigma_profile(t - 2 * w, w, orc.KIND_RANDOM, 2.0 / h, draws=rng.random(t))
                 for t in T]
-        g = orc.Grid(T, 1.0, sigs)
+        if wall:
+            for sg in sigs:
+                sg[-1] = 0.0
+        g = orc.Grid(T, h, sigs, wall=wall)
         A = _dense_A(orc, g)
         N = A.shape[0]
         AT = np.zeros((N, N))
