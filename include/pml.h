@@ -60,7 +60,7 @@ typedef enum {
     PML_ECUDA = 3,       /* a CUDA runtime/driver call failed                          */
     PML_ESTATE = 4,      /* call not valid in the context's current state              */
     PML_EUNSTABLE = 5,   /* dt beyond the RK4 stability limit sqrt(2/d) h              */
-    PML_ENONFINITE = 6,  /* non-finite value found in inputs or in the state           */
+    PML_ENONFINITE = 6,  /* non-finite input (a source amplitude); states are not scanned */
     PML_ETIMEOUT = 7     /* a bounded device-side wait gave up (kernel error flag set) */
 } pml_status;
 
