@@ -86,3 +86,20 @@ def test_user_and_random_profiles_are_checked(L):
     assert _status(n=n, w=w, kind=_lib.PML_SIGMA_RANDOM, user=p4) == _lib.PML_EINVAL
     assert _status(n=n, w=w, kind=_lib.PML_SIGMA_RANDOM, user=None) == _lib.PML_EINVAL
     assert _status(n=n, w=w, kind=_lib.PML_SIGMA_USER, user=[ptr[0], None]) == _lib.PML_EINVAL
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_limit_is_where_the_oracle_starts_to_grow(L, orc, ndim):
+    """The same bound seen from the oracle: the checkerboard mode (the discrete Laplacian's
+    largest frequency) stays bounded just below sqrt(2/d) h and grows just above it."""
+    T, h = (8,) * ndim, 0.7
+    g = orc.Grid(T, h, [np.zeros(t) for t in T])
+    idx = np.indices(T[::-1]).sum(axis=0)
+    y0 = g.zeros_state()
+    y0[0] = ((-1.0) ** idx).reshape(-1)
+    limit = np.sqrt(2.0 / ndim) * h
+    grow = []
+    for f in (0.99, 1.01):
+        y, _ = orc.rk4(g, y0.copy(), 3000, f * limit)
+        grow.append(np.abs(y).max())
+    assert grow[0] < 2.0 and grow[1] > 10.0, grow
