@@ -3,8 +3,10 @@
 The library times its interior-kernel variants (one-step shapes and, for 2D FP32, the
 two-step temporally blocked shapes) on a live context (``pml_autotune``).
 This module keys the winner by (device name, dimension, precision, box shape, layer
-width) and keeps it in a JSON file (``$PML_AUTOTUNE_CACHE`` or
-``~/.cache/pml_autotune.json``) so later contexts of the same shape skip the timing.
+width, number of variants the library offers) and keeps it in a JSON file
+(``$PML_AUTOTUNE_CACHE`` or ``~/.cache/pml_autotune.json``) so later contexts of the same
+shape skip the timing.  A cached choice the library rejects (a build with other variants)
+is timed again.
 """
 from __future__ import annotations
 
@@ -22,8 +24,9 @@ def cache_path() -> str:
 def _key(solver) -> str:
     import torch
     name = torch.cuda.get_device_name(solver.device)
-    return "%s|%dd|fp%d|%s|w%d" % (name, solver.ndim, solver.precision,
-                                   "x".join(str(t) for t in solver.T), solver.w)
+    nvar = _lib.pml_get_variant(solver.ctx)[1]
+    return "%s|%dd|fp%d|%s|w%d|n%d" % (name, solver.ndim, solver.precision,
+                                       "x".join(str(t) for t in solver.T), solver.w, nvar)
 
 
 def _load() -> dict:
@@ -65,9 +68,12 @@ def tune(solver, steps: int = 20, use_cache: bool = True):
     if key in cache:
         rec = cache[key]
         one = int(rec.get("one_step", rec["variant"]))
-        select(solver.ctx, int(rec["variant"]), one)
-        solver.one_step_variant = one
-        return int(rec["variant"]), None
+        try:
+            select(solver.ctx, int(rec["variant"]), one)
+            solver.one_step_variant = one
+            return int(rec["variant"]), None
+        except _lib.PMLError:
+            pass   # not a variant of this build: time them again
     chosen, times = _lib.pml_autotune(solver.ctx, steps)
     one = _best_one_step(solver.ctx, times)
     select(solver.ctx, chosen, one)

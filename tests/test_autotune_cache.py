@@ -77,3 +77,23 @@ def test_select_one_step_choice(fake):
     assert fake.selected == [1]
     autotune.select(object(), 4, 2)
     assert fake.selected[-2:] == [2, 4]
+
+
+def test_stale_cached_choice_is_timed_again(fake, tmp_path):
+    """A cached index the library rejects (a build with fewer variants) falls back to
+    timing instead of failing."""
+    from paper_1804_01390_gb300 import _lib as real
+    json.dump({"dev|2d|fp32|160x160|w16": {"variant": 9, "one_step": 9}}, open(tmp_path / "cache.json", "w"))
+
+    def set_variant(ctx, v):
+        if not 0 <= int(v) < len(fake.times):
+            raise real.PMLError(real.PML_EINVAL, "variant out of range")
+        fake.cur = int(v)
+        fake.selected.append(int(v))
+
+    fake.pml_set_variant = set_variant
+    fake.PMLError = real.PMLError
+    s = _solver()
+    v, table = autotune.tune(s, steps=5)
+    assert fake.tuned == 1 and v == 3 and table is not None
+    assert json.load(open(tmp_path / "cache.json"))["dev|2d|fp32|160x160|w16"]["variant"] == 3
