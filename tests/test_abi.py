@@ -88,3 +88,27 @@ def test_variant_and_time_block_queries_reject_null_without_gpu(lib):
     field32 = (2032 + 8 + 31) // 32 * 32 * (2032 + 8) * 4
     assert b32 >= 3 * 6 * field32
     assert 1.25 < b64 / b32 < 1.45
+
+
+def test_no_cpu_fallback(tmp_path):
+    """The product path has no CPU fallback: a missing library is an error on first use, and
+    a solver refuses any device but CUDA (the oracle is never called in its place)."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    from paper_1804_01390_gb300.solver import PMLSolver
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            _lib.load(str(tmp_path / "libpml.so"))
+    finally:
+        _lib._lib = saved
+    with pytest.raises(ValueError, match="CUDA"):
+        PMLSolver((16, 16), 4, precision=64, device=torch.device("cpu"))
+    # no module of the package imports the oracle
+    import re
+    pkg = os.path.join(ROOT, "paper_1804_01390_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
