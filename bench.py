@@ -29,8 +29,12 @@ if ROOT not in sys.path:
 
 METRIC = "grid-point updates/s (GPts/s) and % HBM roofline, FP32 vs FP64, fwd and adjoint"
 UNIT = "GPts/s"
-NOMINAL_FP64_TFLOPS = 1.25          # GB300 dense FP64 (nominal, no tensor-core path)
-FP64_FLOP_PER_POINT = 38            # interior kernel: 4 differences (5 flop) + 2 outputs (9 flop)
+# algorithmic flops of one point-update (one RK4 step of one vertex): 4 stages x (a 5-point
+# difference, 6 flop, plus 4 fused stage / accumulate operations, 8 flop)
+FLOP_PER_UPDATE_2D = 56
+# flops the FP64 interior kernel executes per vertex (the RK4 polynomial in closed form):
+# four 5-point differences (5 flop each) and two outputs of four FMAs and an add (9 flop each)
+FP64_KERNEL_FLOP_PER_POINT = 38
 
 
 def _peaks():
@@ -41,6 +45,30 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def measure_fp_peaks(local, target_s=0.15):
+    """FP64 and FP32 FMA throughput of this GPU from the library's own kernel
+    (pml_fma_peak), with the clocks sampled while it runs."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    st = torch.cuda.current_stream().cuda_stream
+    out = {}
+    clk = ClockSampler(local)
+    clk.start()
+    for prec in (64, 32):
+        iters = 1024
+        tf, ms = _lib.pml_fma_peak(prec, st, iters)
+        iters = max(1024, int(iters * target_s * 1e3 / max(ms, 1e-3)) // 16 * 16)
+        tf, ms = _lib.pml_fma_peak(prec, st, iters)
+        out["fp%d_tflops" % prec] = tf
+        out["fp%d_ms" % prec] = ms
+        out["fp%d_iters" % prec] = iters
+    clk.stop()
+    out["clocks"] = clk.summary()
+    out["method"] = ("pml_fma_peak: 4 x 512 threads per SM, 8 independent FMA chains per thread, one "
+                     "timed launch of ~%.0f ms per precision (CUDA events), 2 flop per FMA" % (target_s * 1e3))
+    return out
 
 
 class ClockSampler:
@@ -163,6 +191,72 @@ def timed_steps(solver, steps, warmup, ws, profile=False):
     return ms, prof
 
 
+def _errs(got, want, scale_peak=None, scale_l2=None):
+    import numpy as np
+    d = got - want
+    peak = float(np.abs(want).max()) if scale_peak is None else scale_peak
+    nrm = float(np.linalg.norm(want)) if scale_l2 is None else scale_l2
+    mx = float(np.abs(d).max())
+    return {"max_abs": mx, "max_abs_rel_peak": mx / peak if peak > 0 else None,
+            "rel_l2": float(np.linalg.norm(d)) / nrm if nrm > 0 else None}
+
+
+def accuracy_section(wl, u0, variant, one_step, dev, steps=100):
+    """FP32 against FP64 on the headline workload after `steps` steps (the FP64 path is the
+    one the oracle pins element by element in the parity tests), and the truncation error of
+    32- and 64-cell layers against a 1024^2 box whose boundary is never reached (128^2
+    window, 1000 steps; the paper's check of the layer, Sec. 1.1.4), in both precisions."""
+    import numpy as np
+    import torch
+    from paper_1804_01390_gb300 import autotune
+    from paper_1804_01390_gb300 import workloads as wk
+    from paper_1804_01390_gb300.solver import PMLSolver
+    res = {}
+    fields = {}
+    for prec in (64, 32):
+        s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=prec, device=dev)
+        if prec == 32:
+            autotune.select(s.ctx, variant, one_step)
+        s.set_initial(torch.from_numpy(u0.astype(np.float64 if prec == 64 else np.float32)).to(dev))
+        s.step(steps)
+        fields[prec] = [s.read(f).double().cpu().numpy() for f in (0, 1)]
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    res["fp32_vs_fp64"] = {"steps": steps, "workload": "headline workload, the FP32 kernel shape of the headline",
+                           "U": _errs(fields[32][0], fields[64][0]), "V": _errs(fields[32][1], fields[64][1])}
+    del fields
+
+    def window_u(wlx, prec, M=None, n=1000):
+        if M is None:
+            s = PMLSolver(wlx.N, wlx.w, dt=wlx.dt, precision=prec, device=dev)
+            s.set_initial(torch.from_numpy(wk.initial_field(wlx)).to(dev))
+            lo = (wlx.w, wlx.w)
+        else:
+            big, offs = wk.reference_box(wlx, M)
+            s = PMLSolver(big.N, 0, dt=wlx.dt, precision=prec, device=dev)
+            s.set_initial(torch.from_numpy(wk.reference_initial_field(wlx, M)).to(dev))
+            lo = offs
+        s.step(n)
+        u = s.read(0).double().cpu().numpy()[lo[1]:lo[1] + wlx.N[1], lo[0]:lo[0] + wlx.N[0]]
+        s.close()
+        return u
+
+    ref_wl = wk.cfg1(w=64)
+    b64 = window_u(ref_wl, 64, M=1024)
+    u_init = wk.initial_field(ref_wl)
+    peak0, n0 = float(np.abs(u_init).max()), float(np.linalg.norm(u_init))
+    trunc = {"reference": "1024^2 box without layer, FP64, same masked initial data, 1000 steps; errors "
+                          "relative to the initial field's peak and norm",
+             "fp32_floor": _errs(window_u(ref_wl, 32, M=1024), b64, peak0, n0)}
+    for w in (16, 32, 64):
+        wlx = wk.cfg1(w=w)
+        trunc["w%d" % w] = {"fp64": _errs(window_u(wlx, 64), b64, peak0, n0),
+                            "fp32": _errs(window_u(wlx, 32), b64, peak0, n0)}
+    res["truncation_vs_big_domain"] = trunc
+    return res
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -257,26 +351,71 @@ def run_ours(args, ws, rank, local):
         s.close()
         del s
 
-    # ---- FP64 ------------------------------------------------------------------------
+    # ---- FP64: the paper's precision, bound by the FP64 pipe ---------------------------
     fp64 = None
+    peaks = None
     if not args.no_fp64:
+        peaks = measure_fp_peaks(local)
+        fp64_peak = peaks["fp64_tflops"]
         K64 = max(K // 10, 10)
         s = PMLSolver(wl.N, wl.w, dt=wl.dt, precision=64, device=dev)
         autotune.tune(s, steps=5, use_cache=not args.retune)
-        s.set_initial(torch.from_numpy(u0.astype(np.float64)).to(dev))
-        ms64, prof64 = timed_steps(s, K64, min(W, 3), ws, profile=True)
+        u64 = u0.astype(np.float64)
+        s.set_initial(torch.from_numpy(u64).to(dev))
+        clk64 = ClockSampler(local)
+        clk64.start()
+        ms64, _ = timed_steps(s, K64, min(W, 3), ws, profile=False)
+        clk64.stop()
         ms64 = max_over_ranks(ms64, ws, dev)
         v64 = pts * K64 * ws / (ms64 / 1e3) / 1e9
+        _, prof64 = timed_steps(s, K64, 0, ws, profile=True)
         m64, n64 = prof64
         t_int = m64[0] / max(n64[0], 1) / 1e3
-        tflops = int(np.prod([n - 2 for n in wl.N])) * FP64_FLOP_PER_POINT / t_int / 1e12
-        fp64 = {"value": v64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64,
+        int64_pts = int(np.prod([n - 2 for n in wl.N]))
+        kernel_tflops = int64_pts * FP64_KERNEL_FLOP_PER_POINT / t_int / 1e12
+        step_tflops = v64 / ws * FLOP_PER_UPDATE_2D / 1e3
+        # end to end through the C ABI with host buffers, as for the FP32 headline
+        e2e64 = None
+        if not args.no_e2e:
+            from paper_1804_01390_gb300 import _lib
+            u_host64 = torch.from_numpy(u64).pin_memory()
+            out_host64 = torch.empty_like(u_host64).pin_memory()
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            _lib.pml_set_initial(s.ctx, u_host64.data_ptr(), None, 0)
+            _lib.pml_step(s.ctx, K64)
+            _lib.pml_read_field(s.ctx, 0, out_host64.data_ptr(), 0)
+            t1 = time.perf_counter()
+            barrier(ws)
+            e_ms64 = max_over_ranks((t1 - t0) * 1e3, ws, dev)
+            nb64 = u_host64.numel() * 8
+            e2e64 = {"value": pts * K64 * ws / (e_ms64 / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb64 / K64,
+                     "d2h_bytes_per_step": nb64 / K64, "ms": e_ms64,
+                     "how": "pml_set_initial(host pinned U0) + pml_step(K) + pml_read_field(host U), wall clock"}
+        fp64 = {"metric": METRIC, "value": v64, "unit": UNIT, "dtype": "f64", "steps": K64, "warmup": min(W, 3),
+                "ms_per_step": ms64 / K64, "workload": "the headline workload in FP64",
+                "roofline": {"bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": step_tflops / fp64_peak, "peak_kind": "measured",
+                             "peak_method": peaks["method"], "flop_per_update": FLOP_PER_UPDATE_2D,
+                             "definition": "point-updates/s x 56 algorithmic flop per point-update / measured "
+                                           "FP64 FMA throughput",
+                             "traffic": None},
+                "kernel_roofline": {"kernel": "k_interior2d<double>", "bound": "alu",
+                                    "flop_per_vertex": FP64_KERNEL_FLOP_PER_POINT, "achieved": kernel_tflops,
+                                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": kernel_tflops / fp64_peak,
+                                    "avg_launch_ms": t_int * 1e3,
+                                    "note": "flops the closed-form interior kernel executes per vertex"},
                 "hbm_roofline": step_roofline(v64 / ws, 8),
-                "roofline": {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS,
-                             "unit": "TFLOP/s", "frac": tflops / NOMINAL_FP64_TFLOPS,
-                             "peak_kind": "nominal GB300 FP64", "flop_per_point": FP64_FLOP_PER_POINT}}
+                "e2e": e2e64, "clocks": clk64.summary(),
+                "cpu_baseline": "see the top-level cpu_baseline (the FP64 oracle on the same layer)"}
         s.close()
         del s
+
+    # ---- accuracy of the FP32 path: against the FP64 path, and truncation vs a big box ----
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = accuracy_section(wl, u0, variant, one_step, dev)
 
     # ---- adjoint (FP32) --------------------------------------------------------------
     adj = None
@@ -519,6 +658,8 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
 
+    if fp64 is not None and cpu is not None:
+        fp64["cpu_baseline"] = cpu   # the oracle is FP64: the same baseline serves both lines
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
@@ -543,7 +684,8 @@ def run_ours(args, ws, rank, local):
                          "timing": "per-kernel CUDA events on the solver stream over a second pass of the "
                                    "same K steps (%.3f ms/step with events)" % (ms_prof / K)},
             "hbm_roofline": step_roofline(value / ws, 4),
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64, "adjoint": adj,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64,
+            "fp_peaks": peaks, "accuracy": accuracy, "adjoint": adj,
             "cfg3": d3, "batched": d4, "stress": stress, "grad_sigma": gsig, "wall": dwall,
             "misfit_gradient": mgrad,
             "cpu_baseline": cpu,
@@ -618,6 +760,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-3d", action="store_true")

@@ -60,7 +60,8 @@ typedef enum {
     PML_ECUDA = 3,       /* a CUDA runtime/driver call failed                          */
     PML_ESTATE = 4,      /* call not valid in the context's current state              */
     PML_EUNSTABLE = 5,   /* dt beyond the RK4 stability limit sqrt(2/d) h              */
-    PML_ENONFINITE = 6,  /* non-finite input (a source amplitude); states are not scanned */
+    PML_ENONFINITE = 6,  /* non-finite input (a source amplitude), or the periodic scan of
+                            the state found a non-finite value (pml_set_check_interval)   */
     PML_ETIMEOUT = 7     /* a bounded device-side wait gave up (kernel error flag set) */
 } pml_status;
 
@@ -96,8 +97,7 @@ enum {
     PML_FLAG_WALL = 2        /* end every axis with a reflecting wall instead of the periodic
                                 wrap: U, V, Phi, Psi are zero at the vertices -1 and T[a]
                                 (the layer backed by a reflecting boundary, Sec. 1.1.4).
-                                sigma_a[T[a]-1] (the wrap edge) is set to 0.  Not with
-                                pml_sigma_gradient. */
+                                sigma_a[T[a]-1] (the wrap edge) is set to 0. */
 };
 
 /*
@@ -182,6 +182,30 @@ pml_status pml_get_step(const pml_ctx *ctx, int64_t *step);
 pml_status pml_sync(pml_ctx *ctx);
 
 /*
+ * Failure detection.  The device-side error word of a context is sticky: once a kernel
+ * has set it, every synchronising call reports it, until pml_set_initial or
+ * pml_load_state replaces the state (and clears the word).
+ *
+ * pml_set_check_interval: every `steps` steps of pml_step (and of pml_adjoint_step, on
+ *   the adjoint state) the library scans U and V of the current state for NaN and Inf
+ *   (one read of both fields, about 0.05 % of the step time at the default); the first
+ *   non-finite value makes the next synchronising call return PML_ENONFINITE, naming the
+ *   field and the step.  A blow-up shows up in U or V within one step wherever it starts,
+ *   since every Phi_a / Psi_a feeds dV/dt.  The scan runs when the step counter crosses a
+ *   multiple of `steps`; 0 turns it off; the default is 1000.  Batches (pml_batch_step)
+ *   do not scan.
+ * pml_set_wait_limit: the limit in nanoseconds of every bounded device wait (a kernel
+ *   waiting for its own tile copies; 0 restores the default of 2 s).  A wait that runs out
+ *   records its site, lets the copies in flight land (0.1 s at most each) and ends its
+ *   work; the next synchronising call returns PML_ETIMEOUT.  Limits below 1000 ns make
+ *   every wait give up at once, which exercises that error path on purpose (for tests of
+ *   a caller's error handling).  Takes effect for work
+ *   enqueued afterwards; a batch keeps the limits its contexts had at pml_batch_create.
+ */
+pml_status pml_set_check_interval(pml_ctx *ctx, int64_t steps);
+pml_status pml_set_wait_limit(pml_ctx *ctx, uint64_t ns);
+
+/*
  * Integer layout tables of axis `axis` (host arrays of length T[axis]):
  *   phi_active[i] = sigma[i] != 0, psi_active[i] = sigma[i-1] != 0 (supports, Sec. 1.1.2)
  *   interior[i]   = 1 on the run of vertices where sigma vanishes on edges i-2..i+1, the
@@ -235,7 +259,10 @@ pml_status pml_adjoint_step(pml_ctx *ctx, int64_t n, const void *residual, void 
  * stages of kbar_i^T (dA/dsigma) Y_i, with Y_i the stage inputs of the forward step and
  * kbar_i the stage cotangents, in FP64.  Forward states are recomputed from checkpoints
  * taken every `interval` steps (0: ceil(sqrt(n))), so the call holds about
- * n/interval + interval + 7 states in device memory (cudaMalloc for its duration).
+ * n/interval + interval + 7 states in device memory (cudaMalloc for its duration).  The
+ * stage vectors are formed only where the contraction needs them: within three stencil
+ * steps of the edges with nonzero sigma.  Periodic boxes and boxes with walls
+ * (PML_FLAG_WALL: fields zero beyond the ends) alike.
  *
  * Outputs: grad_sigma (host FP64, T[0] + T[1] (+ T[2]) values, axis by axis, indexed by
  * edge): dJ/dsigma_a[e] with the supports of Phi/Psi held fixed; edges with sigma = 0
@@ -262,7 +289,7 @@ pml_status pml_load_state(pml_ctx *ctx, const void *src, int on_device);
 /*
  * Kernel timing.  With enable = 1 every kernel the context launches is bracketed by CUDA
  * events recorded on the context's stream (kinds: 0 interior, 1 layer, 2 point kernels
- * for sources / receivers).  pml_profile_read synchronises, returns the summed
+ * for sources / receivers and the finiteness scan).  pml_profile_read synchronises, returns the summed
  * durations in milliseconds and the launch counts per kind, and clears them.
  */
 pml_status pml_profile_enable(pml_ctx *ctx, int enable);
@@ -300,17 +327,21 @@ pml_status pml_autotune(pml_ctx *ctx, int steps, double *times_ms, int *chosen);
  *   wlo, whi     inclusive window per axis, 0 <= wlo <= whi < T
  *   h            grid spacing; ref: NULL or a device FP64 array of the window shape
  *   cuda_stream  stream the two reduction kernels run on; the call synchronises it
- *   out          host double[5]: the energy eq:Energy over the window (forward
- *                differences wrap periodically at the box edge), max |U|, ||U||_2,
- *                ||U - ref||_2, max |U - ref|, exactly as pml_norms reports them
+ *   out          host double[5]: the energy over the window,
+ *                  1/2 sum_i (V(i)^2 + sum_a ((U(i + e_a) - U(i)) / h)^2),
+ *                with the forward differences wrapping periodically at the box edge;
+ *                max |U|, ||U||_2, ||U - ref||_2, max |U - ref|, exactly as pml_norms
+ *                reports them
  *
  * The per-row partial sums live in one fixed array of this library's device memory
  * (16384 rows x 5 doubles, 640 KB, held on every device that uses it until the process
  * exits).  A window with more than 16384 rows (y extent times z extent) is rejected with
- * PML_EINVAL.  The first call on a device looks up that array's device address, so make it
- * before any stream capture.  Every call reuses the same array and overwrites the partials
- * it reads, so results never mix across calls; but two calls whose kernels overlap on the
- * GPU (other streams, other host threads) race for it: serialise them.
+ * PML_EINVAL.  The array's device address is looked up once per device and context (again
+ * after a device reset).  The call copies the results to host memory and synchronises the
+ * stream, so it must never be made while that stream is being captured into a CUDA graph.
+ * Every call reuses the same array and overwrites the partials it reads, so results never
+ * mix across calls; but two calls whose kernels overlap on the GPU (other streams, other
+ * host threads) race for it: serialise them.
  */
 pml_status pml_norms_dense_static(int ndim, const int64_t *T, int precision, const void *U, const void *V,
                                   const int64_t *wlo, const int64_t *whi, double h, const double *ref,
@@ -382,6 +413,19 @@ pml_status pml_residual_factor(int m, const double *sigma_h, double kh_re, doubl
                                int backed, double *factor);
 pml_status pml_design_width(int kind, double sigma_max_h, double order, double cos_min, double omega_h_max,
                             double eps, int backed, int w_max, int *w_out, double *worst_out);
+
+/*
+ * Arithmetic peak of the current device, measured by the library's own kernel (the paper
+ * has no counterpart: it is the denominator of the FP64 step's roofline, since that path
+ * is bound by the FP64 pipe rather than by memory).  Every thread of 4 x 512-thread
+ * blocks per SM runs eight independent fused multiply-add chains for `iters` iterations
+ * (a positive multiple of 16) in `precision` (32 or 64); one warm-up launch, then one
+ * timed launch bracketed by CUDA events on `cuda_stream` (synchronising).
+ *   tflops  2 x FMAs / elapsed time, in 10^12 flop/s
+ *   ms      elapsed time of the timed launch (may be NULL)
+ * Allocates nothing.  Errors are described by pml_last_error(NULL).
+ */
+pml_status pml_fma_peak(int precision, void *cuda_stream, int64_t iters, double *tflops, double *ms);
 
 void pml_destroy(pml_ctx *ctx);
 const char *pml_last_error(const pml_ctx *ctx);

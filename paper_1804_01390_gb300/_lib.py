@@ -46,6 +46,7 @@ def PML_FIELD_PSI(a):
 EXPORTED = (
     "pml_workspace_bytes", "pml_create", "pml_set_initial", "pml_set_sources",
     "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
+    "pml_set_check_interval", "pml_set_wait_limit",
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
     "pml_adjoint_read_field", "pml_sigma_gradient", "pml_state_bytes", "pml_save_state", "pml_load_state",
     "pml_get_variant", "pml_set_variant", "pml_get_time_block", "pml_autotune",
@@ -53,7 +54,7 @@ EXPORTED = (
     "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
     "pml_batch_get_time_block",
     "pml_batch_autotune", "pml_batch_profile_enable", "pml_batch_profile_read", "pml_batch_info",
-    "pml_batch_destroy", "pml_residual_factor", "pml_design_width", "pml_destroy", "pml_last_error", "pml_status_string",
+    "pml_batch_destroy", "pml_residual_factor", "pml_design_width", "pml_fma_peak", "pml_destroy", "pml_last_error", "pml_status_string",
 )
 
 
@@ -102,6 +103,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_norms": [P, P, P],
         "pml_get_step": [P, ctypes.POINTER(i64)],
         "pml_sync": [P],
+        "pml_set_check_interval": [P, i64],
+        "pml_set_wait_limit": [P, ctypes.c_uint64],
         "pml_query_layout": [P, ctypes.c_int, P, P, P],
         "pml_query_sigma": [P, ctypes.c_int, P],
         "pml_adjoint_reset": [P],
@@ -128,6 +131,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_batch_profile_read": [P, P, P],
         "pml_batch_info": [P, P],
         "pml_residual_factor": [ctypes.c_int, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, P],
+        "pml_fma_peak": [ctypes.c_int, P, i64, P, P],
         "pml_design_width": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P],
     }
@@ -212,6 +216,14 @@ def pml_get_step(ctx) -> int:
 
 def pml_sync(ctx):
     _check(load().pml_sync(ctx), ctx)
+
+
+def pml_set_check_interval(ctx, steps):
+    _check(load().pml_set_check_interval(ctx, int(steps)), ctx)
+
+
+def pml_set_wait_limit(ctx, ns):
+    _check(load().pml_set_wait_limit(ctx, int(ns)), ctx)
 
 
 def pml_query_layout(ctx, axis, phi, psi, interior):
@@ -396,6 +408,14 @@ def pml_design_width(kind, sigma_max_h, order, cos_min, omega_h_max, eps, backed
     _check(load().pml_design_width(int(kind), float(sigma_max_h), float(order), float(cos_min), float(omega_h_max),
                                    float(eps), int(bool(backed)), int(w_max), ctypes.byref(w), ctypes.byref(worst)))
     return int(w.value), float(worst.value)
+
+
+def pml_fma_peak(precision, stream, iters):
+    """(TFLOP/s, ms) of the library's FMA-throughput kernel in FP32 or FP64."""
+    tf = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(load().pml_fma_peak(int(precision), stream, int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    return float(tf.value), float(ms.value)
 
 
 def pml_destroy(ctx):

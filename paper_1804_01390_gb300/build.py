@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpml.so")
-SOURCES = ["runtime.cu", "step2d.cu", "step3d.cu", "aux_kernels.cu", "noalloc.cu", "grad_sigma.cu", "design.cu", "layer3d_wall.cu", "frame3d.cu"]
+SOURCES = ["runtime.cu", "step2d.cu", "step3d.cu", "aux_kernels.cu", "noalloc.cu", "grad_sigma.cu", "design.cu", "layer3d_wall.cu", "frame3d.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -35,6 +35,42 @@ cudaError_t launch_fill_ghosts(int prec, void *f, const Geom &g, cudaStream_t st
 }
 
 // ---------------------------------------------------------------------------------
+// finiteness scan: one block per row (y, z) of the box, threads along x; the first
+// non-finite value sets the error word (code 2) that the host reads at its next
+// synchronising call
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_check_finite(const T *U, const T *V, const Geom g, DeviceError *err,
+                                                      long long step)
+{
+    const int64_t rows = g.T[1] * g.T[2];
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t y = r % g.T[1], z = r / g.T[1];
+        const int64_t o = g.origin + y * g.P + z * g.PS;
+        int bad = 0;
+        for (int64_t x = threadIdx.x; x < g.T[0]; x += blockDim.x)
+            bad |= (isfinite(U[o + x]) ? 0 : 1) | (isfinite(V[o + x]) ? 0 : 2);
+        if (__syncthreads_or(bad)) {   // the same answer in every thread: a uniform return
+            if (bad && atomicCAS(&err->code, 0, 2) == 0) {
+                err->where = (bad & 1) ? 0 : 1;
+                err->step = step;
+            }
+            return;
+        }
+    }
+}
+
+cudaError_t launch_check_finite(int prec, const void *U, const void *V, const Geom &g, DeviceError *err,
+                                int64_t step, cudaStream_t st)
+{
+    const int64_t rows = g.T[1] * g.T[2];
+    const int blocks = int(rows < 2048 ? rows : 2048);
+    if (prec == 32) k_check_finite<float><<<blocks, 256, 0, st>>>((const float *)U, (const float *)V, g, err, step);
+    else k_check_finite<double><<<blocks, 256, 0, st>>>((const double *)U, (const double *)V, g, err, step);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 // point sources and receivers
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ double ricker(double t, double f, double t0)

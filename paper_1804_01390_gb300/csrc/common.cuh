@@ -81,8 +81,10 @@ struct LayerTile {
 };
 
 struct DeviceError {
-    int code;                  // 0 = ok, 1 = mbarrier wait timed out
-    int where;
+    int code;                  // 0 = ok, 1 = a bounded mbarrier wait gave up, 2 = the finiteness
+                               // scan met a non-finite value
+    int where;                 // code 1: wait site; code 2: field (0 U, 1 V)
+    long long step;            // code 2: step counter when the scan ran
 };
 
 // ---------------------------------------------------------------------------------
@@ -132,9 +134,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Bounded wait: gives up after `limit_ns` nanoseconds of the global timer (checked every
 // 256 polls), records the failure and returns false.  No wait in this library can spin
-// forever.  The default limit is far above any legitimate wait (a few microseconds).
+// forever.  limit_ns = 0 means the default, far above any legitimate wait (a few
+// microseconds); a limit below kImmediateNs gives up at once without probing (the
+// context's wait-limit setting uses this to exercise the error path of every kernel on
+// purpose: each kernel then waits, bounded by kDrainLimitNs, for the copies it has in
+// flight, including the one it gave up on, before it ends).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 constexpr uint64_t kDrainLimitNs = 100000000ull;   // 0.1 s, waits on the error path
+constexpr uint64_t kImmediateNs = 1000ull;
 
 __device__ __forceinline__ uint64_t global_ns()
 {
@@ -144,14 +151,19 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, DeviceError *err, int where,
-                                          uint64_t limit_ns = kWaitLimitNs)
+                                          uint64_t limit_ns = 0)
 {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        for (int i = 0; i < 256; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) break;
+    if (limit_ns != 0 && limit_ns < kImmediateNs) {
+        // give up at once, landed or not: the caller's error path then lets the copy land
+    } else {
+        if (mbar_try_wait(bar, parity)) return true;
+        const uint64_t lim = limit_ns ? limit_ns : kWaitLimitNs;
+        const uint64_t t0 = global_ns();
+        for (;;) {
+            for (int i = 0; i < 256; ++i)
+                if (mbar_try_wait(bar, parity)) return true;
+            if (global_ns() - t0 > lim) break;
+        }
     }
     if (err) {
         atomicCAS(&err->code, 0, 1);
@@ -273,6 +285,7 @@ struct Interior2DArgs {
     Range xr, yr;
     StepCoef c;
     DeviceError *err;
+    uint64_t wait_ns;          // limit of every bounded wait (0: the default 2 s)
     int *queue;
     int parity;
     int rows;                  // rows per work item of the warp-streaming shape (0: its default)
@@ -307,6 +320,7 @@ struct Layer2DArgs {
     const LayerTile *tiles;
     int ntiles;
     DeviceError *err;
+    uint64_t wait_ns;          // limit of every bounded wait (0: the default 2 s)
     int *queue;                // work counters (this launch: queue[parity]; clears the other)
     int parity;
 };
@@ -381,6 +395,7 @@ struct Interior3DArgs {
     Range xr, yr, zr;
     StepCoef c;
     DeviceError *err;
+    uint64_t wait_ns;          // limit of every bounded wait (0: the default 2 s)
     int *queue;                // work counters (this launch: queue[parity])
     int parity;
 };
@@ -400,6 +415,7 @@ struct Layer3DArgs {
     int ntiles;
     int class_off[9];          // tiles of flags m are [class_off[m], class_off[m+1])
     DeviceError *err;
+    uint64_t wait_ns;          // limit of every bounded wait (0: the default 2 s)
 };
 // 3D layer column tiles (x, y output extent; halo 4 on each side) and z segment length
 constexpr int kLayer3TXf = 28, kLayer3TYf = 9;   // FP32: 36 x 17 region columns (20 warps)
@@ -450,17 +466,19 @@ inline cudaError_t launch_pdl(K kernel, int grid, int threads, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Damping gradient (grad_sigma.cu): explicit operator applications over the whole box,
-// stage combinations and the per-edge contraction kbar^T (dA/dsigma_a[e]) Y.
+// Damping gradient (grad_sigma.cu): explicit stage evaluations on lists of row segments
+// {x0, x1, y, z} (inclusive x range of row (y, z)) and the per-edge contraction
+// kbar^T (dA/dsigma_a[e]) Y of the four stage pairs of a step.
 struct SigmaPtrs {
     const void *p[3];          // device sigma per axis (context precision)
 };
-cudaError_t launch_apply_op(int prec, bool adjoint, void *const *in, void *const *out, int nf, const Geom &g,
-                            const SigmaPtrs &s, double h, cudaStream_t st);
-cudaError_t launch_axpby(int prec, void *const *x, void *const *y, void *const *out, double alpha, double beta,
-                         int nf, int64_t elems, cudaStream_t st);
-cudaError_t launch_contract(int prec, void *const *kb, void *const *Y, int nf, const Geom &g, const SigmaPtrs &s,
-                            double h, double *acc, cudaStream_t st);
+// out = alpha base + cop Op(in) on the segments (Op = A or A^T)
+cudaError_t launch_stage(int prec, bool adjoint, void *const *in, void *const *base, void *const *out, int nf,
+                         const Geom &g, const SigmaPtrs &s, double h, double alpha, double cop, const int4 *seg,
+                         int nseg, cudaStream_t st);
+// acc[edge] += sum_i scale[i] kb[i]^T (dA/dsigma) Y[i], i = 0..3
+cudaError_t launch_contract4(int prec, void *const *const *kb, void *const *const *Y, const double *scale, int nf,
+                             const Geom &g, const SigmaPtrs &s, double h, double *acc, cudaStream_t st);
 cudaError_t launch_residual(int prec, const void *trace, const void *target, void *res, int64_t count,
                             double *misfit, cudaStream_t st);
 
@@ -490,6 +508,11 @@ cudaError_t launch_post_step(int prec, void *U, void *V, const PointArgs &a, int
                              void *trace_row, cudaStream_t st);
 cudaError_t launch_adjoint_points(int prec, void *Ub, void *Vb, const PointArgs &a, int64_t m,
                                   const void *residual_row, double *grad_amp, cudaStream_t st);
+
+// Finiteness scan of U and V over the box (ghost ring and row padding excluded): the
+// first non-finite value found sets err->code = 2 (where = field, step = `step`).
+cudaError_t launch_check_finite(int prec, const void *U, const void *V, const Geom &g, DeviceError *err,
+                                int64_t step, cudaStream_t st);
 
 // Ghost ring refresh, dense <-> padded copies and FP64 norms.
 cudaError_t launch_fill_ghosts(int prec, void *f, const Geom &g, cudaStream_t st);

@@ -5,8 +5,14 @@
 // Y4 = y_n + dt k3, k_i = A Y_i) and kbar_i the stage cotangents of the reverse stage
 // graph driven by the adjoint state ybar_{n+1} (kbar4 = dt/6 ybar, kbar3 = dt/3 ybar +
 // dt A^T kbar4, kbar2 = dt/3 ybar + dt/2 A^T kbar3, kbar1 = dt/6 ybar + dt/2 A^T kbar2).
-// These kernels evaluate the stages explicitly over the whole box (plain global loads,
-// periodic neighbours by index wrap, so ghost cells are never read), and contract them
+// The contraction reads kbar_i and Y_i only on the vertices next to an edge with nonzero
+// sigma (the set C: along each axis a, the slab of coordinates e, e + 1 of those edges).
+// Since the stencil of A is a cross, C widened by r stencil steps is the union of those
+// slabs widened by r along their own axis (C_r), so Y2 is formed on C_2, Y3 on C_1, Y4 on
+// C, and likewise kbar3 on C_2, kbar2 on C_1, kbar1 on C (kbar4 = dt/6 ybar is a scaling,
+// applied inside the kernels).  The kernels evaluate these stages explicitly on host-built
+// lists of row segments of C_r (plain global loads; neighbours by index wrap, or zero
+// beyond the ends of a box with walls, so ghost cells are never read), and contract them
 // edge by edge.  Source terms are left out of the stages: a source sits where sigma is
 // zero on the edges within two of it, so it never reaches the vertices the contraction
 // reads (those next to an edge with nonzero sigma) within one step.
@@ -32,73 +38,92 @@ template <typename T> struct FldW {
     T *f[8];
 };
 
-// out = A in (forward operator of Eq. 3) or A^T in, at every vertex of the box.
-template <typename T, bool ADJ>
-__global__ void __launch_bounds__(256) k_apply(const Fld<T> in, const FldW<T> out, const Idx ix, SigmaPtrs s, T ih,
-                                               T ih2, T i2h)
+// Neighbour of flat offset o along axis a (s = +1 / -1) at coordinate c_a: the periodic
+// image, or with a wall no vertex at all beyond the ends (the value there is zero).
+struct Nb {
+    int64_t off;
+    bool ok;
+};
+__device__ __forceinline__ Nb neighbour(const Idx &ix, int64_t o, int a, int64_t ca, int s, bool wall)
 {
-    // boxes handled here have fewer than 2^31 vertices (checked by the caller): 32-bit index math
-    const uint32_t T0 = uint32_t(ix.T[0]), T1 = uint32_t(ix.T[1]);
-    const uint32_t n = T0 * T1 * uint32_t(ix.T[2]);
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int64_t c[3];
-        const uint32_t q = v / T0;
-        c[0] = v - q * T0;
-        c[1] = q % T1;
-        c[2] = q / T1;
-        const int64_t o = ix.off(c[0], c[1], c[2]);
-        T acc = T(0);   // V row (forward) or U row (transpose)
-        const int lapf = ADJ ? 1 : 0;
-        for (int a = 0; a < ix.nd; ++a) {
-            int64_t cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
-            cp[a] = wrap(c[a] + 1, ix.T[a]);
-            cm[a] = wrap(c[a] - 1, ix.T[a]);
-            const int64_t op = ix.off(cp[0], cp[1], cp[2]), om = ix.off(cm[0], cm[1], cm[2]);
-            const T *sg = static_cast<const T *>(s.p[a]);
-            const T si = sg[c[a]], sm = sg[wrap(c[a] - 1, ix.T[a])];
-            const T *L = in.f[lapf];
-            acc += (L[op] - T(2) * L[o] + L[om]) * ih2;
-            const T *Ph = in.f[2 + 2 * a], *Ps = in.f[3 + 2 * a];
-            T *oPh = out.f[2 + 2 * a], *oPs = out.f[3 + 2 * a];
-            if (!ADJ) {
-                const T *U = in.f[0];
-                const T dU = (U[op] - U[om]) * i2h;
-                acc += (si * Ps[op] - sm * Ph[om]) * ih;
-                oPh[o] = si != T(0) ? -T(0.5) * (sm * Ph[om] + si * Ph[o]) - dU : T(0);
-                oPs[o] = sm != T(0) ? -T(0.5) * (sm * Ps[o] + si * Ps[op]) - dU : T(0);
-            } else {
-                const T *Vb = in.f[1];
-                acc += ((Ph[op] - Ph[om]) + (Ps[op] - Ps[om])) * i2h;
-                oPh[o] = si != T(0) ? -si * Vb[op] * ih - T(0.5) * si * (Ph[op] + Ph[o]) : T(0);
-                oPs[o] = sm != T(0) ? sm * Vb[om] * ih - T(0.5) * sm * (Ps[o] + Ps[om]) : T(0);
+    const int64_t st = a == 0 ? 1 : (a == 1 ? ix.P : ix.PS);
+    const int64_t Ta = ix.T[a];
+    int64_t c = ca + s;
+    if (c < 0 || c >= Ta) {
+        if (wall) return {o, false};
+        c = c < 0 ? c + Ta : c - Ta;
+    }
+    return {o + (c - ca) * st, true};
+}
+
+// out = alpha base + cop Op(in) on the row segments seg[0..nseg) (Op = A, the forward
+// operator of Eq. 3, or its transpose), one warp per segment in turn.  Every value of
+// `in` the stencil reads must be valid: the caller's segments for `out` lie one vertex
+// inside those on which `in` was formed.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(256) k_stage(const Fld<T> in, const Fld<T> base, const FldW<T> out, const Idx ix,
+                                               SigmaPtrs s, T ih, T ih2, T i2h, T alpha, T cop, const int4 *seg,
+                                               int nseg, int wall)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarp = int(gridDim.x * blockDim.x) >> 5;
+    for (int k = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nseg; k += nwarp) {
+        const int4 sg4 = seg[k];
+        const int64_t y = sg4.z, z = sg4.w;
+        for (int64_t x = sg4.x + lane; x <= sg4.y; x += 32) {
+            const int64_t c[3] = {x, y, z};
+            const int64_t o = ix.off(x, y, z);
+            T acc = T(0);   // V row (forward) or U row (transpose)
+            for (int a = 0; a < ix.nd; ++a) {
+                const Nb p = neighbour(ix, o, a, c[a], +1, wall != 0), m = neighbour(ix, o, a, c[a], -1, wall != 0);
+                const T *sgm = static_cast<const T *>(s.p[a]);
+                const int64_t Ta = ix.T[a];
+                const T si = sgm[c[a]], sm = sgm[c[a] == 0 ? Ta - 1 : c[a] - 1];
+                const T *L = in.f[ADJ ? 1 : 0];
+                const T Lp = p.ok ? L[p.off] : T(0), Lm = m.ok ? L[m.off] : T(0);
+                acc += (Lp - T(2) * L[o] + Lm) * ih2;
+                const T *Ph = in.f[2 + 2 * a], *Ps = in.f[3 + 2 * a];
+                const T php = p.ok ? Ph[p.off] : T(0), phm = m.ok ? Ph[m.off] : T(0);
+                const T psp = p.ok ? Ps[p.off] : T(0), psm = m.ok ? Ps[m.off] : T(0);
+                T oph, ops;
+                if (!ADJ) {
+                    const T *U = in.f[0];
+                    const T dU = ((p.ok ? U[p.off] : T(0)) - (m.ok ? U[m.off] : T(0))) * i2h;
+                    acc += (si * psp - sm * phm) * ih;
+                    oph = si != T(0) ? -T(0.5) * (sm * phm + si * Ph[o]) - dU : T(0);
+                    ops = sm != T(0) ? -T(0.5) * (sm * Ps[o] + si * psp) - dU : T(0);
+                } else {
+                    const T *Vb = in.f[1];
+                    acc += ((php - phm) + (psp - psm)) * i2h;
+                    oph = si != T(0) ? -si * (p.ok ? Vb[p.off] : T(0)) * ih - T(0.5) * si * (php + Ph[o]) : T(0);
+                    ops = sm != T(0) ? sm * (m.ok ? Vb[m.off] : T(0)) * ih - T(0.5) * sm * (Ps[o] + psm) : T(0);
+                }
+                out.f[2 + 2 * a][o] = alpha * base.f[2 + 2 * a][o] + cop * oph;
+                out.f[3 + 2 * a][o] = alpha * base.f[3 + 2 * a][o] + cop * ops;
             }
-        }
-        if (!ADJ) {
-            out.f[0][o] = in.f[1][o];
-            out.f[1][o] = acc;
-        } else {
-            out.f[0][o] = acc;
-            out.f[1][o] = in.f[0][o];
+            if (!ADJ) {
+                out.f[0][o] = alpha * base.f[0][o] + cop * in.f[1][o];
+                out.f[1][o] = alpha * base.f[1][o] + cop * acc;
+            } else {
+                out.f[0][o] = alpha * base.f[0][o] + cop * acc;
+                out.f[1][o] = alpha * base.f[1][o] + cop * in.f[0][o];
+            }
         }
     }
 }
 
-// out = alpha x + beta y over the nf padded arrays (elementwise, ghosts included)
-template <typename T>
-__global__ void __launch_bounds__(256) k_axpby(const Fld<T> x, const Fld<T> y, const FldW<T> out, T alpha, T beta,
-                                               int nf, int64_t elems)
-{
-    for (int f = 0; f < nf; ++f)
-        for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < elems;
-             i += int64_t(gridDim.x) * blockDim.x)
-            out.f[f][i] = alpha * x.f[f][i] + beta * y.f[f][i];
-}
+// The four stage pairs of one step in one launch: one block per edge (a, e) with
+// sigma_a[e] != 0, acc[a-block + e] += sum_i scale_i kb_i^T (dA/dsigma_a[e]) Y_i over the
+// vertices with i_a = e and i_a = e + 1 (FP64, fixed order, no atomics).
+struct Pairs4 {
+    const void *kb[4][8];
+    const void *Y[4][8];
+    double scale[4];
+};
 
-// One block per edge (a, e) with sigma_a[e] != 0: acc[a-block + e] += kb^T (dA/dsigma_a[e]) Y
-// over the vertices with i_a = e and i_a = e + 1 (FP64, fixed order, no atomics).
 template <typename T>
-__global__ void __launch_bounds__(256) k_contract(const Fld<T> kb, const Fld<T> Y, const Idx ix, SigmaPtrs s, double ih,
-                                                  double *acc)
+__global__ void __launch_bounds__(256) k_contract4(const Pairs4 pr, const Idx ix, SigmaPtrs s, double ih, int wall,
+                                                   double *acc)
 {
     int a = 0, e = int(blockIdx.x), off = 0;
     while (a < ix.nd - 1 && e >= ix.T[a]) {
@@ -109,29 +134,35 @@ __global__ void __launch_bounds__(256) k_contract(const Fld<T> kb, const Fld<T> 
     const T *sg = static_cast<const T *>(s.p[a]);
     const int64_t Ta = ix.T[a];
     if (sg[e] == T(0)) return;   // whole block: no barrier below is reached
+    // (with a wall sigma_a[T - 1] = 0, so e + 1 never leaves the box here)
     const bool psi_at_e = sg[wrap(e - 1, Ta)] != T(0);    // Psi row active at i_a = e
     const bool phi_at_e1 = sg[wrap(e + 1, Ta)] != T(0);   // Phi row active at i_a = e + 1
     const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;   // the other axes
     const int64_t n1 = ix.T[b1], n2 = ix.nd == 3 ? ix.T[b2] : 1;
-    const T *kV = kb.f[1], *kPh = kb.f[2 + 2 * a], *kPs = kb.f[3 + 2 * a];
-    const T *Ph = Y.f[2 + 2 * a], *Ps = Y.f[3 + 2 * a];
     double sum = 0.0;
-    for (int64_t j = threadIdx.x; j < n1 * n2; j += blockDim.x) {
-        int64_t c[3] = {0, 0, 0};
-        c[b1] = j % n1;
-        if (ix.nd == 3) c[b2] = j / n1;
-        // i_a = e: sigma_a[i_a] terms
-        c[a] = e;
-        int64_t cp[3] = {c[0], c[1], c[2]};
-        cp[a] = wrap(e + 1, Ta);
-        const int64_t o = ix.off(c[0], c[1], c[2]), op = ix.off(cp[0], cp[1], cp[2]);
-        sum += double(kV[o]) * double(Ps[op]) * ih;
-        sum += -0.5 * double(kPh[o]) * double(Ph[o]);
-        if (psi_at_e) sum += -0.5 * double(kPs[o]) * double(Ps[op]);
-        // i_a = e + 1: sigma_a[i_a - 1] terms (o is now the vertex i - e_a)
-        sum += -double(kV[op]) * double(Ph[o]) * ih;
-        if (phi_at_e1) sum += -0.5 * double(kPh[op]) * double(Ph[o]);
-        sum += -0.5 * double(kPs[op]) * double(Ps[op]);
+    for (int i = 0; i < 4; ++i) {
+        const T *kV = static_cast<const T *>(pr.kb[i][1]), *kPh = static_cast<const T *>(pr.kb[i][2 + 2 * a]),
+                *kPs = static_cast<const T *>(pr.kb[i][3 + 2 * a]);
+        const T *Ph = static_cast<const T *>(pr.Y[i][2 + 2 * a]), *Ps = static_cast<const T *>(pr.Y[i][3 + 2 * a]);
+        double part = 0.0;
+        for (int64_t j = threadIdx.x; j < n1 * n2; j += blockDim.x) {
+            int64_t c[3] = {0, 0, 0};
+            c[b1] = j % n1;
+            if (ix.nd == 3) c[b2] = j / n1;
+            // i_a = e: sigma_a[i_a] terms
+            c[a] = e;
+            int64_t cp[3] = {c[0], c[1], c[2]};
+            cp[a] = wrap(e + 1, Ta);
+            const int64_t o = ix.off(c[0], c[1], c[2]), op = ix.off(cp[0], cp[1], cp[2]);
+            part += double(kV[o]) * double(Ps[op]) * ih;
+            part += -0.5 * double(kPh[o]) * double(Ph[o]);
+            if (psi_at_e) part += -0.5 * double(kPs[o]) * double(Ps[op]);
+            // i_a = e + 1: sigma_a[i_a - 1] terms (o is now the vertex i - e_a)
+            part += -double(kV[op]) * double(Ph[o]) * ih;
+            if (phi_at_e1) part += -0.5 * double(kPh[op]) * double(Ph[o]);
+            part += -0.5 * double(kPs[op]) * double(Ps[op]);
+        }
+        sum += pr.scale[i] * part;
     }
     __shared__ double red[256];
     red[threadIdx.x] = sum;
@@ -174,12 +205,6 @@ Idx make_idx(const Geom &g)
     return ix;
 }
 
-int grid_for(int64_t n)
-{
-    const int64_t b = (n + 255) / 256;
-    return int(b < 4096 ? (b > 0 ? b : 1) : 4096);
-}
-
 template <typename T> Fld<T> fld(void *const *p, int nf)
 {
     Fld<T> r{};
@@ -195,45 +220,51 @@ template <typename T> FldW<T> fldw(void *const *p, int nf)
 
 }  // namespace
 
-cudaError_t launch_apply_op(int prec, bool adjoint, void *const *in, void *const *out, int nf, const Geom &g,
-                            const SigmaPtrs &s, double h, cudaStream_t st)
+cudaError_t launch_stage(int prec, bool adjoint, void *const *in, void *const *base, void *const *out, int nf,
+                         const Geom &g, const SigmaPtrs &s, double h, double alpha, double cop, const int4 *seg,
+                         int nseg, cudaStream_t st)
 {
-    if (g.T[0] * g.T[1] * g.T[2] >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+    if (nseg <= 0) return cudaSuccess;
     const Idx ix = make_idx(g);
-    const int grid = grid_for(g.T[0] * g.T[1] * g.T[2]);
+    const int grid = nseg / 8 + 1 < 2048 ? nseg / 8 + 1 : 2048;   // 8 warps per block, a warp per segment
+    const int wall = g.wall;
     if (prec == 32) {
         const float ih = float(1.0 / h), ih2 = float(1.0 / (h * h)), i2h = float(0.5 / h);
-        if (adjoint) k_apply<float, true><<<grid, 256, 0, st>>>(fld<float>(in, nf), fldw<float>(out, nf), ix, s, ih, ih2, i2h);
-        else k_apply<float, false><<<grid, 256, 0, st>>>(fld<float>(in, nf), fldw<float>(out, nf), ix, s, ih, ih2, i2h);
+        if (adjoint)
+            k_stage<float, true><<<grid, 256, 0, st>>>(fld<float>(in, nf), fld<float>(base, nf), fldw<float>(out, nf), ix,
+                                                      s, ih, ih2, i2h, float(alpha), float(cop), seg, nseg, wall);
+        else
+            k_stage<float, false><<<grid, 256, 0, st>>>(fld<float>(in, nf), fld<float>(base, nf), fldw<float>(out, nf), ix,
+                                                       s, ih, ih2, i2h, float(alpha), float(cop), seg, nseg, wall);
     } else {
         const double ih = 1.0 / h, ih2 = 1.0 / (h * h), i2h = 0.5 / h;
-        if (adjoint) k_apply<double, true><<<grid, 256, 0, st>>>(fld<double>(in, nf), fldw<double>(out, nf), ix, s, ih, ih2, i2h);
-        else k_apply<double, false><<<grid, 256, 0, st>>>(fld<double>(in, nf), fldw<double>(out, nf), ix, s, ih, ih2, i2h);
+        if (adjoint)
+            k_stage<double, true><<<grid, 256, 0, st>>>(fld<double>(in, nf), fld<double>(base, nf), fldw<double>(out, nf),
+                                                       ix, s, ih, ih2, i2h, alpha, cop, seg, nseg, wall);
+        else
+            k_stage<double, false><<<grid, 256, 0, st>>>(fld<double>(in, nf), fld<double>(base, nf),
+                                                        fldw<double>(out, nf), ix, s, ih, ih2, i2h, alpha, cop, seg,
+                                                        nseg, wall);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_axpby(int prec, void *const *x, void *const *y, void *const *out, double alpha, double beta, int nf,
-                         int64_t elems, cudaStream_t st)
-{
-    const int grid = grid_for(elems);
-    if (prec == 32)
-        k_axpby<float><<<grid, 256, 0, st>>>(fld<float>(x, nf), fld<float>(y, nf), fldw<float>(out, nf), float(alpha),
-                                            float(beta), nf, elems);
-    else
-        k_axpby<double><<<grid, 256, 0, st>>>(fld<double>(x, nf), fld<double>(y, nf), fldw<double>(out, nf), alpha,
-                                             beta, nf, elems);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_contract(int prec, void *const *kb, void *const *Y, int nf, const Geom &g, const SigmaPtrs &s,
-                            double h, double *acc, cudaStream_t st)
+cudaError_t launch_contract4(int prec, void *const *const *kb, void *const *const *Y, const double *scale, int nf,
+                             const Geom &g, const SigmaPtrs &s, double h, double *acc, cudaStream_t st)
 {
     const Idx ix = make_idx(g);
+    Pairs4 pr{};
+    for (int i = 0; i < 4; ++i) {
+        for (int f = 0; f < nf; ++f) {
+            pr.kb[i][f] = kb[i][f];
+            pr.Y[i][f] = Y[i][f];
+        }
+        pr.scale[i] = scale[i];
+    }
     int nblk = 0;
     for (int a = 0; a < g.ndim; ++a) nblk += int(g.T[a]);
-    if (prec == 32) k_contract<float><<<nblk, 256, 0, st>>>(fld<float>(kb, nf), fld<float>(Y, nf), ix, s, 1.0 / h, acc);
-    else k_contract<double><<<nblk, 256, 0, st>>>(fld<double>(kb, nf), fld<double>(Y, nf), ix, s, 1.0 / h, acc);
+    if (prec == 32) k_contract4<float><<<nblk, 256, 0, st>>>(pr, ix, s, 1.0 / h, g.wall, acc);
+    else k_contract4<double><<<nblk, 256, 0, st>>>(pr, ix, s, 1.0 / h, g.wall, acc);
     return cudaGetLastError();
 }
 

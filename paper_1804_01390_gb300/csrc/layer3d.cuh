@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
         for (int PH = 0; PH < 3; ++PH) {
             const int p = p0 + PH;
             if (p < nin) {
-                if (!mbar_wait(&bars[p % S], (p / S) & 1, a.err, 4)) ok = false;
+                if (!mbar_wait(&bars[p % S], (p / S) & 1, a.err, 4, a.wait_ns)) ok = false;
                 if (ok) {
                     // level 4 at plane q = p-1 from the input planes in the stage ring
                     if (p >= 2 && v4) {

@@ -9,6 +9,8 @@
 // gives them pml_norms_dense_static: the caller passes the fields and receives the five
 // numbers; the per-row partial sums go to a fixed array in this library's own device
 // memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,20 +33,48 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_scratch[kMaxRows * kVals + 8];
 
 std::mutex g_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per device; the
-// host-side name of the array is not a device address).
+// Device address of g_scratch in the context current on device `dev`.  The host-side name
+// of the array is not a device address; the address is looked up with the device current,
+// once per device and context: after cudaDeviceReset, or with another context made current
+// on the same device, the array lives at a new address, so the cached one is replaced.
+struct ScratchEntry {
+    CUcontext ctx;
+    double *addr;
+};
+ScratchEntry g_scratch_addr[kMaxDevices] = {};
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+
+CUcontext current_context()
+{
+    if (!g_ctx_current) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return nullptr;
+        g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    }
+    CUcontext c = nullptr;
+    if (g_ctx_current(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
 cudaError_t scratch_address(int dev, double **out)
 {
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
+    ScratchEntry &e = g_scratch_addr[dev];
+    const CUcontext before = current_context();
+    if (before && e.addr && e.ctx == before) {
+        *out = e.addr;
+        return cudaSuccess;
     }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t r = cudaGetSymbolAddress(&p, g_scratch);   // makes the device's context current
+    if (r != cudaSuccess) return r;
+    e.ctx = current_context();
+    e.addr = e.ctx ? static_cast<double *>(p) : nullptr;          // no context to key on: look up again next time
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 

@@ -26,6 +26,7 @@ namespace {
 constexpr int kMaxSources = 1024;
 constexpr int kMaxReceivers = 16384;
 constexpr size_t kAlign = 256;
+constexpr int64_t kDefaultCheckEvery = 1000;   // steps between finiteness scans of U and V
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -196,6 +197,10 @@ struct pml_ctx {
     void *lvl[2][8] = {};
     LayerTile *dlt[2][4] = {};
     int nlt[2][4] = {};
+    // failure detection: limit of every bounded device wait (0: the default 2 s) and the
+    // interval in steps of the finiteness scan of U and V (0: off)
+    uint64_t wait_ns = 0;
+    int64_t check_every = kDefaultCheckEvery;
     // kernel timing (pml_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs
@@ -527,7 +532,11 @@ pml_status check_device_error(pml_ctx *c)
     DeviceError h{};
     PML_CU(c, cudaMemcpyAsync(&h, c->derr, sizeof h, cudaMemcpyDeviceToHost, c->st), "read error flag");
     PML_CU(c, cudaStreamSynchronize(c->st), "stream synchronize");
-    if (h.code != 0) return fail(c, PML_ETIMEOUT, "a bounded device wait gave up (site %d)", h.where);
+    if (h.code == 1) return fail(c, PML_ETIMEOUT, "a bounded device wait gave up (site %d)", h.where);
+    if (h.code == 2)
+        return fail(c, PML_ENONFINITE, "the state holds a non-finite value (field %s, scan after step %lld)",
+                    h.where == 0 ? "U" : "V", h.step);
+    if (h.code != 0) return fail(c, PML_ECUDA, "unknown device error code %d", h.code);
     return PML_OK;
 }
 
@@ -622,6 +631,76 @@ void prof_end(pml_ctx *c, long i)
     if (i >= 0) cudaEventRecord(c->prof_ev[2 * size_t(i) + 1], c->st);
 }
 
+// Finiteness scan of the given state's U and V when the step counter went from `before`
+// to `after` across a multiple of the scan interval.
+pml_status maybe_check_finite(pml_ctx *c, void *const *state, int64_t before, int64_t after)
+{
+    const int64_t k = c->check_every;
+    if (k <= 0 || before == after) return PML_OK;
+    auto fl = [k](int64_t v) { return v >= 0 ? v / k : -((-v + k - 1) / k); };
+    if (fl(before) == fl(after)) return PML_OK;
+    const long pi = prof_begin(c, 2);
+    const cudaError_t e = launch_check_finite(c->prec, state[0], state[1], c->g, c->derr, after, c->st);
+    prof_end(c, pi);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finiteness scan");
+    return PML_OK;
+}
+
+// Row segments {x0, x1, y, z} of C_r: the vertices within r stencil steps of those the
+// damping-gradient contraction reads (along each axis a, the coordinates e and e + 1 of
+// every edge e with sigma_a[e] != 0).  The stencil is a cross, so C_r is the union over
+// the axes of those slabs widened by r along their own axis (periodic distance, or plain
+// distance with walls).
+void gradient_segments(const pml_ctx *c, int r, std::vector<int4> *out)
+{
+    std::vector<uint8_t> m[3];
+    for (int a = 0; a < 3; ++a) {
+        const int64_t T = c->T[a];
+        m[a].assign(size_t(T), 0);
+        if (a >= c->nd) continue;
+        std::vector<uint8_t> base(size_t(T), 0);
+        for (int64_t e = 0; e < T; ++e)
+            if (c->sig[a][size_t(e)] != 0.0) {
+                base[size_t(e)] = 1;
+                base[size_t((e + 1) % T)] = 1;
+            }
+        for (int64_t i = 0; i < T; ++i) {
+            if (!base[size_t(i)]) continue;
+            for (int64_t d = -r; d <= r; ++d) {
+                int64_t j = i + d;
+                if (c->g.wall) {
+                    if (j < 0 || j >= T) continue;
+                } else {
+                    j = ((j % T) + T) % T;
+                }
+                m[a][size_t(j)] = 1;
+            }
+        }
+    }
+    out->clear();
+    const int64_t T0 = c->T[0], T1 = c->T[1], T2 = c->nd == 3 ? c->T[2] : 1;
+    for (int64_t z = 0; z < T2; ++z)
+        for (int64_t y = 0; y < T1; ++y) {
+            if (m[1][size_t(y)] || (c->nd == 3 && m[2][size_t(z)])) {
+                out->push_back(make_int4(0, int(T0 - 1), int(y), int(z)));
+                continue;
+            }
+            for (int64_t x = 0; x < T0;) {
+                if (!m[0][size_t(x)]) { ++x; continue; }
+                int64_t x1 = x;
+                while (x1 + 1 < T0 && m[0][size_t(x1 + 1)]) ++x1;
+                out->push_back(make_int4(int(x), int(x1), int(y), int(z)));
+                x = x1 + 1;
+            }
+        }
+}
+
+pml_status clear_device_error(pml_ctx *c)
+{
+    PML_CU(c, cudaMemsetAsync(c->derr, 0, sizeof(DeviceError), c->st), "clear error flag");
+    return PML_OK;
+}
+
 // One step (forward or transposed) from buffers `in` to buffers `out`.
 pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
 {
@@ -640,6 +719,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         l.tiles = adjoint ? c->dtiles_adj : c->dtiles;
         l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
         l.err = c->derr;
+        l.wait_ns = c->wait_ns;
         int64_t &ll = adjoint ? c->launches_layer_adj : c->launches_layer_fwd;
         l.queue = c->dqueue + (adjoint ? 6 : 4);
         l.parity = int(ll & 1);
@@ -649,7 +729,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
         prof_end(c, pi);
         if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel");
         Interior2DArgs a{};
-        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.c = k; a.err = c->derr;
+        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.c = k; a.err = c->derr; a.wait_ns = c->wait_ns;
         // small grids: shorter work items (down to 16 rows) so that every warp of the launch
         // gets one (a warp streams its item's rows one after another)
         if (!range_empty(ir[0]) && !range_empty(ir[1])) {
@@ -703,6 +783,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
             l.ntiles = adjoint ? c->ntiles_adj : c->ntiles;
             for (int m = 0; m < 9; ++m) l.class_off[m] = adjoint ? c->class_off_adj[m] : c->class_off[m];
             l.err = c->derr;
+            l.wait_ns = c->wait_ns;
             long pi = prof_begin(c, 1);
             e = launch_layer3d(c->prec, adjoint, tl, out, l, c->st);
             prof_end(c, pi);
@@ -710,7 +791,7 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
             layer_launched = l.ntiles > 0;
         }
         Interior3DArgs a{};
-        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr;
+        a.g = c->g; a.xr = ir[0]; a.yr = ir[1]; a.zr = ir[2]; a.c = k; a.err = c->derr; a.wait_ns = c->wait_ns;
         int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
         a.queue = c->dqueue + (adjoint ? 2 : 0);
         a.parity = int(nl & 1);
@@ -740,6 +821,7 @@ pml_status enqueue_double_step(pml_ctx *c, bool adjoint, int p)
     l.g = c->g; l.k = layer_const(c);
     l.sig[0] = c->dsig[0]; l.sig[1] = c->dsig[1];
     l.err = c->derr;
+    l.wait_ns = c->wait_ns;
     l.tiles = adjoint ? c->dtiles_l1_adj : c->dtiles_l1;
     l.ntiles = adjoint ? c->ntiles_l1_adj : c->ntiles_l1;
     int64_t &ll = adjoint ? c->launches_layer_adj : c->launches_layer_fwd;
@@ -765,7 +847,7 @@ pml_status enqueue_double_step(pml_ctx *c, bool adjoint, int p)
     if (e != cudaSuccess) return cuda_fail(c, e, "layer 2D kernel (pass 2)");
     Interior2DArgs a{};
     const Range *irt = adjoint ? c->ir_tb_adj : c->ir_tb;
-    a.g = c->g; a.xr = irt[0]; a.yr = irt[1]; a.c = k; a.err = c->derr;
+    a.g = c->g; a.xr = irt[0]; a.yr = irt[1]; a.c = k; a.err = c->derr; a.wait_ns = c->wait_ns;
     int64_t &nl = adjoint ? c->launches_adj : c->launches_fwd;
     a.queue = c->dqueue + (adjoint ? 2 : 0);
     a.parity = int(nl & 1);
@@ -1234,7 +1316,7 @@ pml_status pml_set_initial(pml_ctx *c, const void *u0, const void *v0, int on_de
     }
     c->step = 0;
     c->trace_k = 0;
-    return PML_OK;
+    return clear_device_error(c);   // a new state: earlier device errors no longer apply
 }
 
 pml_status pml_set_sources(pml_ctx *c, int ns, const int64_t *coords, const double *amp, double f_peak,
@@ -1327,6 +1409,7 @@ pml_status pml_step(pml_ctx *c, int64_t n)
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, PML_EINVAL, "n must be >= 0");
     const PointArgs pa = point_args(c);
+    const int64_t step0 = c->step;
     for (int64_t k = 0; k < n; ++k) {
         const int p = c->cur, q = 1 - p;
         // two steps per pass where nothing has to happen between the two
@@ -1353,7 +1436,7 @@ pml_status pml_step(pml_ctx *c, int64_t n)
         c->cur = q;
         c->step++;
     }
-    return PML_OK;
+    return maybe_check_finite(c, c->fld[c->cur], step0, c->step);
 }
 
 pml_status pml_read_field(pml_ctx *c, int field, void *dst, int on_device)
@@ -1389,6 +1472,21 @@ pml_status pml_sync(pml_ctx *c)
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     return check_device_error(c);
+}
+
+pml_status pml_set_wait_limit(pml_ctx *c, uint64_t ns)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    c->wait_ns = ns;
+    return PML_OK;
+}
+
+pml_status pml_set_check_interval(pml_ctx *c, int64_t steps)
+{
+    if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
+    if (steps < 0) return fail(c, PML_EINVAL, "steps must be >= 0");
+    c->check_every = steps;
+    return PML_OK;
 }
 
 pml_status pml_query_layout(const pml_ctx *c, int axis, uint8_t *phi_active, uint8_t *psi_active, uint8_t *interior)
@@ -1429,6 +1527,7 @@ pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *g
     if (!c->adj_ready) return fail(c, PML_ESTATE, "call pml_adjoint_reset first");
     if (n < 0) return fail(c, PML_EINVAL, "n must be >= 0");
     const PointArgs pa = point_args(c);
+    const int64_t astep0 = c->astep;
     for (int64_t k = 0; k < n; ++k) {
         const int p = c->acur;
         const int64_t m = c->astep;
@@ -1452,6 +1551,10 @@ pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *g
         c->acur = 1 - p;
         c->astep = m - 1;
     }
+    {
+        pml_status s = maybe_check_finite(c, c->adj[c->acur], astep0, c->astep);
+        if (s != PML_OK) return s;
+    }
     if (grad_u) {
         pml_status s = copy_dense(c, c->adj[c->acur][0], grad_u, true, false);
         if (s != PML_OK) return s;
@@ -1469,7 +1572,6 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (!(c->flags & PML_FLAG_ADJOINT)) return fail(c, PML_ESTATE, "context was created without PML_FLAG_ADJOINT");
-    if (c->g.wall) return fail(c, PML_EINVAL, "pml_sigma_gradient supports periodic boxes only");
     if (n < 1) return fail(c, PML_EINVAL, "n must be >= 1");
     if (!grad_sigma || !misfit) return fail(c, PML_EINVAL, "grad_sigma and misfit are required");
     if (c->nr > 0 && !target == !residual)
@@ -1497,6 +1599,15 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
     const size_t o_res = off; off += align_up(size_t(n) * size_t(c->nr > 0 ? c->nr : 1) * c->esz, kAlign);
     const size_t o_acc = off; off += align_up(size_t(tot) * sizeof(double), kAlign);
     const size_t o_mis = off; off += kAlign;
+    // row segments of C_0, C_1, C_2 (the vertices the contraction reads, widened by 0, 1, 2
+    // stencil steps): the stages are formed there only
+    std::vector<int4> segs[3];
+    for (int r = 0; r < 3; ++r) gradient_segments(c, r, &segs[r]);
+    size_t o_seg_tab[3];
+    for (int r = 0; r < 3; ++r) {
+        o_seg_tab[r] = off;
+        off += align_up(std::max<size_t>(segs[r].size(), 1) * sizeof(int4), kAlign);
+    }
     char *mem = nullptr;
     cudaError_t ce = cudaMalloc(&mem, off);
     if (ce != cudaSuccess) return fail(c, PML_ENOMEM, "cudaMalloc(%zu) for checkpoints: %s", off, cudaGetErrorString(ce));
@@ -1507,15 +1618,22 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
     auto state_at = [&](size_t base, void *out[8]) {
         for (int f = 0; f < nf; ++f) out[f] = mem + base + size_t(f) * fb;
     };
-    void *K1[8], *Y2[8], *Y3[8], *Y4[8], *KB[8], *YB[8];
-    state_at(o_stage + 0 * sb, K1);
-    state_at(o_stage + 1 * sb, Y2);
-    state_at(o_stage + 2 * sb, Y3);
-    state_at(o_stage + 3 * sb, Y4);
-    state_at(o_stage + 4 * sb, KB);
-    state_at(o_stage + 5 * sb, YB);
+    void *Y2[8], *Y3[8], *Y4[8], *KB3[8], *KB2[8], *KB1[8];
+    state_at(o_stage + 0 * sb, Y2);
+    state_at(o_stage + 1 * sb, Y3);
+    state_at(o_stage + 2 * sb, Y4);
+    state_at(o_stage + 3 * sb, KB3);
+    state_at(o_stage + 4 * sb, KB2);
+    state_at(o_stage + 5 * sb, KB1);
     PML_CU(c, cudaMemsetAsync(mem + o_stage, 0, sb * 6, c->st), "clear stage buffers");
     double *dacc = reinterpret_cast<double *>(mem + o_acc), *dmis = reinterpret_cast<double *>(mem + o_mis);
+    const int4 *dseg[3];
+    for (int r = 0; r < 3; ++r) {
+        dseg[r] = reinterpret_cast<const int4 *>(mem + o_seg_tab[r]);
+        if (!segs[r].empty())
+            PML_CU(c, cudaMemcpyAsync(mem + o_seg_tab[r], segs[r].data(), segs[r].size() * sizeof(int4),
+                                      cudaMemcpyHostToDevice, c->st), "segment table");
+    }
     PML_CU(c, cudaMemsetAsync(dacc, 0, size_t(tot) * sizeof(double), c->st), "clear gradient");
     PML_CU(c, cudaMemsetAsync(dmis, 0, sizeof(double), c->st), "clear misfit");
 
@@ -1564,25 +1682,27 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
             void *Y1[8];
             state_at(o_seg + size_t(m - 1 - sa) * sb, Y1);
             void *const *yb = c->adj[p];
-            // forward stage inputs
-            PML_CU(c, launch_apply_op(c->prec, false, Y1, K1, nf, c->g, sp, c->h, c->st), "stage");
-            PML_CU(c, launch_axpby(c->prec, Y1, K1, Y2, 1.0, 0.5 * dt, nf, c->g.elems, c->st), "stage");
-            PML_CU(c, launch_apply_op(c->prec, false, Y2, K1, nf, c->g, sp, c->h, c->st), "stage");
-            PML_CU(c, launch_axpby(c->prec, Y1, K1, Y3, 1.0, 0.5 * dt, nf, c->g.elems, c->st), "stage");
-            PML_CU(c, launch_apply_op(c->prec, false, Y3, K1, nf, c->g, sp, c->h, c->st), "stage");
-            PML_CU(c, launch_axpby(c->prec, Y1, K1, Y4, 1.0, dt, nf, c->g.elems, c->st), "stage");
-            // stage cotangents, each contracted with its stage input
-            PML_CU(c, launch_axpby(c->prec, yb, yb, KB, dt / 6.0, 0.0, nf, c->g.elems, c->st), "cotangent");
-            PML_CU(c, launch_contract(c->prec, KB, Y4, nf, c->g, sp, c->h, dacc, c->st), "contraction");
-            PML_CU(c, launch_apply_op(c->prec, true, KB, YB, nf, c->g, sp, c->h, c->st), "cotangent");
-            PML_CU(c, launch_axpby(c->prec, yb, YB, KB, dt / 3.0, dt, nf, c->g.elems, c->st), "cotangent");
-            PML_CU(c, launch_contract(c->prec, KB, Y3, nf, c->g, sp, c->h, dacc, c->st), "contraction");
-            PML_CU(c, launch_apply_op(c->prec, true, KB, YB, nf, c->g, sp, c->h, c->st), "cotangent");
-            PML_CU(c, launch_axpby(c->prec, yb, YB, KB, dt / 3.0, 0.5 * dt, nf, c->g.elems, c->st), "cotangent");
-            PML_CU(c, launch_contract(c->prec, KB, Y2, nf, c->g, sp, c->h, dacc, c->st), "contraction");
-            PML_CU(c, launch_apply_op(c->prec, true, KB, YB, nf, c->g, sp, c->h, c->st), "cotangent");
-            PML_CU(c, launch_axpby(c->prec, yb, YB, KB, dt / 6.0, 0.5 * dt, nf, c->g.elems, c->st), "cotangent");
-            PML_CU(c, launch_contract(c->prec, KB, Y1, nf, c->g, sp, c->h, dacc, c->st), "contraction");
+            void *const *ybv = yb;
+            const int n0 = int(segs[0].size()), n1 = int(segs[1].size()), n2 = int(segs[2].size());
+            // forward stage inputs: Y2 = Y1 + dt/2 A Y1 (on C_2), Y3 = Y1 + dt/2 A Y2 (C_1),
+            // Y4 = Y1 + dt A Y3 (C_0)
+            PML_CU(c, launch_stage(c->prec, false, Y1, Y1, Y2, nf, c->g, sp, c->h, 1.0, 0.5 * dt, dseg[2], n2, c->st), "stage");
+            PML_CU(c, launch_stage(c->prec, false, Y2, Y1, Y3, nf, c->g, sp, c->h, 1.0, 0.5 * dt, dseg[1], n1, c->st), "stage");
+            PML_CU(c, launch_stage(c->prec, false, Y3, Y1, Y4, nf, c->g, sp, c->h, 1.0, dt, dseg[0], n0, c->st), "stage");
+            // stage cotangents of the reverse stage graph driven by ybar (kbar4 = dt/6 ybar):
+            // kbar3 = dt/3 ybar + dt A^T kbar4 (C_2), kbar2 = dt/3 ybar + dt/2 A^T kbar3 (C_1),
+            // kbar1 = dt/6 ybar + dt/2 A^T kbar2 (C_0)
+            PML_CU(c, launch_stage(c->prec, true, yb, yb, KB3, nf, c->g, sp, c->h, dt / 3.0, dt * dt / 6.0, dseg[2], n2,
+                                   c->st), "cotangent");
+            PML_CU(c, launch_stage(c->prec, true, KB3, yb, KB2, nf, c->g, sp, c->h, dt / 3.0, 0.5 * dt, dseg[1], n1,
+                                   c->st), "cotangent");
+            PML_CU(c, launch_stage(c->prec, true, KB2, yb, KB1, nf, c->g, sp, c->h, dt / 6.0, 0.5 * dt, dseg[0], n0,
+                                   c->st), "cotangent");
+            // each cotangent contracted with its stage input, all four in one launch
+            void *const *kbs[4] = {ybv, KB3, KB2, KB1};
+            void *const *ys[4] = {Y4, Y3, Y2, Y1};
+            const double scl[4] = {dt / 6.0, 1.0, 1.0, 1.0};
+            PML_CU(c, launch_contract4(c->prec, kbs, ys, scl, nf, c->g, sp, c->h, dacc, c->st), "contraction");
             // the adjoint step itself
             if ((s = enqueue_step(c, true, p)) != PML_OK) return s;
             c->acur = 1 - p;
@@ -1650,6 +1770,8 @@ pml_status pml_load_state(pml_ctx *c, const void *src, int on_device)
                "load field");
     c->cur = 0;
     c->step = hdr[1];
+    pml_status s = clear_device_error(c);   // a new state: earlier device errors no longer apply
+    if (s != PML_OK) return s;
     return check_device_error(c);
 }
 
@@ -1738,11 +1860,13 @@ pml_status batch_upload(pml_batch *b)
         d.in.yr = c->ir[1];
         step_coef(c, false, &d.in.c);
         d.in.err = c->derr;
+        d.in.wait_ns = c->wait_ns;
         d.lay.g = c->g;
         d.lay.k = layer_const(c);
         d.lay.sig[0] = c->dsig[0];
         d.lay.sig[1] = c->dsig[1];
         d.lay.err = c->derr;
+        d.lay.wait_ns = c->wait_ns;
         if (b->tb_ok) {
             const uint32_t box2[3] = {uint32_t(batch2d_tb2_box_cols(b->prec, b->var2)),
                                       uint32_t(batch2d_tb2_box_rows(b->prec, b->var2)), 1};

@@ -211,9 +211,10 @@ __device__ __forceinline__ bool interior2d_seg(const CUtensorMap *tmU, const CUt
     for (int c = 0; c < nch; ++c) {
         const uint32_t uu = use + c;
         const int slot = uu % S;
-        if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 1)) {
-            // give the copies still in flight a bounded chance to land, then stop
-            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2)
+        if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 1, a.wait_ns)) {
+            // give the copies still in flight (this box's included) a bounded chance to
+            // land, then stop
+            for (int c2 = c; c2 < nch && c2 < c + S; ++c2)
                 mbar_wait(&bars[(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0, kDrainLimitNs);
             return false;
         }
@@ -450,8 +451,8 @@ __device__ __forceinline__ bool interior2d_seg2(const CUtensorMap *tmU, const CU
     for (int c = 0; c < nch; ++c) {
         const uint32_t uu = use + c;
         const int slot = uu % S;
-        if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 6)) {
-            for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2)
+        if (!mbar_wait(&bars[slot], (uu / S) & 1u, a.err, 6, a.wait_ns)) {
+            for (int c2 = c; c2 < nch && c2 < c + S; ++c2)
                 mbar_wait(&bars[(use + c2) % S], ((use + c2) / S) & 1u, nullptr, 0, kDrainLimitNs);
             return false;
         }
@@ -751,8 +752,8 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
             }
             if (c < nch) {
                 const uint32_t k = use + uint32_t(c);
-                if (!mbar_wait(&bars[k % S], (k / S) & 1, a.err, 2)) {
-                    for (int c2 = c + 1; c2 < nch && c2 < c + S; ++c2) {
+                if (!mbar_wait(&bars[k % S], (k / S) & 1, a.err, 2, a.wait_ns)) {
+                    for (int c2 = c; c2 < nch && c2 < c + S; ++c2) {
                         const uint32_t k2 = use + uint32_t(c2);
                         mbar_wait(&bars[k2 % S], (k2 / S) & 1, nullptr, 0, kDrainLimitNs);
                     }
@@ -982,7 +983,7 @@ __global__ void __launch_bounds__(32 * BY, MINB)
         };
         auto wait_chunk = [&](int c) {
             const uint32_t uu = use + c;
-            return mbar_wait(&bars[uu % NCH], (uu / NCH) & 1u, a.err, 5);
+            return mbar_wait(&bars[uu % NCH], (uu / NCH) & 1u, a.err, 5, a.wait_ns);
         };
         if (tid == 0) {
             fence_proxy_async();

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
                 if (p < n_in && ok) {
                     const uint32_t uu = use + p;
                     const int st = uu % S;
-                    if (!mbar_wait(&bars[st], (uu / S) & 1u, a.err, 3)) {
+                    if (!mbar_wait(&bars[st], (uu / S) & 1u, a.err, 3, a.wait_ns)) {
                         ok = false;
                     } else {
                         const T *sU = reinterpret_cast<const T *>(smem + st * C::STAGE);

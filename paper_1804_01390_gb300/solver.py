@@ -135,6 +135,14 @@ class PMLSolver:
     def sync(self):
         _lib.pml_sync(self.ctx)
 
+    def set_check_interval(self, steps):
+        """Scan U and V for non-finite values every `steps` steps (0: off)."""
+        _lib.pml_set_check_interval(self.ctx, int(steps))
+
+    def set_wait_limit(self, ns):
+        """Limit of every bounded device wait in nanoseconds (0: the default)."""
+        _lib.pml_set_wait_limit(self.ctx, int(ns))
+
     def read(self, field=0, out=None):
         if out is None:
             out = torch.empty(self.shape, dtype=self.dtype, device=self.device)

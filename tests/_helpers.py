@@ -12,6 +12,35 @@ KIND = {"quadratic": oracle.KIND_POWER, "constant": oracle.KIND_CONSTANT,
 TOL = {64: 1e-12, 32: 1e-5}
 
 
+# Elementwise bound beside the relative L2 one: max |got - want| <= MAXABS_TOL * max |want|.
+# The largest elementwise error, measured against the field's peak, may exceed the relative
+# L2 error by up to the ratio of the field's peak to its RMS over the error's support, so the
+# bound is ten times the L2 tolerance; a wrong or raced vertex (an error of the order of the
+# field itself) fails it whatever the size of the box.
+MAXABS_TOL = {64: 1e-11, 32: 1e-4}
+
+
+def errors(got, want):
+    """(relative L2 error, max-abs error, max-abs error relative to max |want|)."""
+    got = np.asarray(got, dtype=np.float64).reshape(-1)
+    want = np.asarray(want, dtype=np.float64).reshape(-1)
+    d = np.abs(got - want)
+    mx = float(d.max()) if d.size else 0.0
+    peak = float(np.abs(want).max()) if want.size else 0.0
+    return rel_l2(got, want), mx, (mx / peak if peak > 0 else mx)
+
+
+def assert_close(got, want, prec, what="", tol=None, tol_max=None):
+    """Assert rel-L2 <= tol (TOL[prec]) and max-abs <= tol_max (MAXABS_TOL[prec]) x peak;
+    the message states both errors."""
+    tol = TOL[prec] if tol is None else tol
+    tol_max = MAXABS_TOL[prec] if tol_max is None else tol_max
+    r, mx, mr = errors(got, want)
+    msg = "%s: rel-L2 %.3e (tol %.0e), max-abs %.3e = %.3e of peak (tol %.0e)" % (what, r, tol, mx, mr, tol_max)
+    assert r <= tol and mr <= tol_max, msg
+    return r, mx
+
+
 def rel_l2(got, want):
     got = np.asarray(got, dtype=np.float64).reshape(-1)
     want = np.asarray(want, dtype=np.float64).reshape(-1)

@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_1804_01390_gb300 import workloads as wk
 
-from ._helpers import TOL, gaussian_u0, make_solver, oracle_grid, rel_l2
+from ._helpers import assert_close, TOL, gaussian_u0, make_solver, oracle_grid, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -54,8 +54,7 @@ def _check(solvers, inits, steps, prec, grids=GRIDS):
         want = _oracle_fields(N, w, u0, v0, steps)
         assert s.step_count == steps
         for f in range(6):
-            err = rel_l2(s.read(f).double().cpu().numpy(), want[f])
-            assert err <= TOL[prec], (k, N, w, f, err)
+            assert_close(s.read(f).double().cpu().numpy(), want[f], prec, repr((k, N, w, f)))
 
 
 @pytest.mark.parametrize("prec", [64, 32])
@@ -214,8 +213,7 @@ def test_full_size_batched_96_grids_sampled():
             wu, wv = _patch_oracle(u0, v0, sig, x, y, steps, 4 * steps + 2)
             got += [U[y, x], V[y, x]]
             want += [wu, wv]
-        err = rel_l2(got, want)
-        assert err <= TOL[32], (k, err)
+        assert_close(got, want, 32, repr((k)))
     b.close()
 
 
@@ -253,8 +251,7 @@ def test_batch_of_wall_boxes_every_variant():
             want, _ = oracle.rk4(g, y, 35, 0.5)
             for f in range(6):
                 got = s.read(f).double().cpu().numpy()
-                err = rel_l2(got, want[f].reshape(got.shape))
-                assert err <= TOL[32], (v, k, f, err)
+                assert_close(got, want[f].reshape(got.shape), 32, repr((v, k, f)))
         b.close()
         for s in solvers:
             s.close()

@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_1804_01390_gb300 import workloads as wk
 
-from ._helpers import TOL, rel_l2
+from ._helpers import assert_close, TOL, rel_l2
 from .test_golden_figures import _load, _setup
 
 pytestmark = pytest.mark.gpu
@@ -59,7 +59,7 @@ def test_forward_at_printed_scale(prec):
     y[1] = v0.reshape(-1)
     want, _ = oracle.rk4(g, y, steps, dt)
     for f in range(6):
-        assert rel_l2(got[f], want[f]) <= TOL[prec], (f, rel_l2(got[f], want[f]))
+        assert_close(got[f], want[f], prec, repr((f,)))
 
 
 def test_reflection_at_machine_zero_fp64():
@@ -110,8 +110,8 @@ def test_transposed_step_at_printed_scale(prec):
     srcd = {"idx": [g.flat(c) for c in src], "amp": amp, "f_peak": f, "t_delay": t0}
     yb, gamp = oracle.adjoint(g, g.zeros_state(), n, dt, n, sources=srcd,
                               receivers=[g.flat(c) for c in rec], residual=residual)
-    assert rel_l2(gu.double().cpu().numpy(), yb[0]) <= TOL[prec]
+    assert_close(gu.double().cpu().numpy(), yb[0], prec)
     for k in range(6):
-        assert rel_l2(got[k], yb[k]) <= TOL[prec], (k, rel_l2(got[k], yb[k]))
+        assert_close(got[k], yb[k], prec, repr((k,)))
     assert np.abs(gamp).max() > 0
     assert rel_l2(ga, gamp) <= (1e-11 if prec == 64 else 1e-5)

@@ -30,11 +30,11 @@ def _case(N, w, steps, seed):
     return draws, sig, u0, v0, rec, src, amp, tgt
 
 
-def _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, interval):
+def _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, interval, wall=False):
     import torch
     from paper_1804_01390_gb300.solver import PMLSolver
     s = PMLSolver(N, w, sigma="random", sigma_max=2.0, draws=draws, precision=prec,
-                  device=torch.device("cuda:0"), adjoint=True)
+                  device=torch.device("cuda:0"), adjoint=True, wall=wall)
     s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
     s.set_sources(src, amp, 0.1, 10.0)
     s.set_receivers(rec, steps)
@@ -45,9 +45,11 @@ def _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, interval):
     return J, grad, gamp, gu
 
 
-def _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps):
+def _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps, wall=False):
     T = tuple(n + 2 * w for n in N)
-    g = oracle.Grid(T, 1.0, sig)
+    if wall:   # a wall leaves no wrap edge: sigma[T - 1] = 0, as the library sets it
+        sig = [np.concatenate([s_[:-1], [0.0]]) for s_ in sig]
+    g = oracle.Grid(T, 1.0, sig, wall=wall)
     y = g.zeros_state()
     y[0] = u0.reshape(-1)
     y[1] = v0.reshape(-1)
@@ -77,6 +79,23 @@ def test_sigma_gradient_matches_oracle(N, w, steps, prec):
     assert rel_l2(gu, guo) <= tol
 
 
+@pytest.mark.parametrize("N,w,steps", [((20, 18), 5, 30), ((8, 7, 9), 3, 12)])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_sigma_gradient_with_walls_matches_oracle(N, w, steps, prec):
+    """The layer backed by reflecting walls (every field zero beyond both ends, Sec. 1.1.4):
+    stage vectors with zero neighbours beyond the ends, no wrap edge."""
+    draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=3 * sum(N) + w)
+    J, grad, gamp, gu = _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, 0, wall=True)
+    Jo, grado, gampo, guo = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps, wall=True)
+    tol = 1e-9 if prec == 64 else 1e-3
+    assert abs(J - Jo) <= tol * Jo, (J, Jo)
+    assert rel_l2(np.concatenate(grad), np.concatenate(grado)) <= tol
+    for a in range(len(N)):
+        assert grad[a][-1] == 0.0   # the wrap edge carries no damping with walls
+    assert rel_l2(gamp, gampo) <= tol
+    assert rel_l2(gu, guo) <= tol
+
+
 def test_checkpoint_interval_does_not_change_the_gradient():
     N, w, steps = (24, 20), 6, 21
     draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=5)
@@ -100,6 +119,25 @@ def test_long_run_with_sqrt_checkpoints():
     Jo, grado, _, _ = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps)
     assert abs(J - Jo) <= 1e-9 * Jo
     assert rel_l2(np.concatenate(grad), np.concatenate(grado)) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_2000_steps_with_sqrt_checkpoints(prec):
+    """2000 steps at the default spacing (45 checkpoints, segments of 45 recomputed) on a
+    small box: J, dJ/dsigma, dJ/da and dJ/dU0 against the oracle, which keeps every state.
+    The run starts at rest (V0 = 0): a random V0 has a nonzero mean, and the undamped
+    constant mode of the periodic box then drifts linearly (U grows to hundreds by step
+    2000), which turns dJ/da into a cancellation of large terms in any precision."""
+    N, w, steps = (26, 22), 6, 2000
+    draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=13)
+    v0 = np.zeros_like(v0)
+    J, grad, gamp, gu = _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, 0)
+    Jo, grado, gampo, guo = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps)
+    tol = 1e-9 if prec == 64 else 1e-3
+    assert abs(J - Jo) <= tol * Jo, (J, Jo)
+    assert rel_l2(np.concatenate(grad), np.concatenate(grado)) <= tol
+    assert rel_l2(gamp, gampo) <= tol
+    assert rel_l2(gu, guo) <= tol
 
 
 def test_autograd_sigma_matches_oracle_and_differences():

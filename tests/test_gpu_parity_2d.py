@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_1804_01390_gb300 import workloads as wk
 
-from ._helpers import TOL, gaussian_u0, make_solver, oracle_grid, rel_l2
+from ._helpers import assert_close, TOL, gaussian_u0, make_solver, oracle_grid, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -61,8 +61,7 @@ CASES = [
 def test_forward_parity(N, w, sigma, prec):
     got, want = _run_both(N, w, prec, 23, sigma, seed=hash((N, w)) % 1000)
     for f, (a, b) in enumerate(zip(got, want)):
-        err = rel_l2(a, b)
-        assert err <= TOL[prec], (f, err)
+        assert_close(a, b, prec, repr((f)))
 
 
 def test_every_interior_variant_matches_oracle():
@@ -86,8 +85,7 @@ def test_every_interior_variant_matches_oracle():
             s.set_initial(torch.from_numpy(u0))
             s.step(13)
             for f in range(6):
-                err = rel_l2(s.read(f).double().cpu().numpy(), want[f])
-                assert err <= TOL[prec], (prec, v, f, err)
+                assert_close(s.read(f).double().cpu().numpy(), want[f], prec, repr((prec, v, f)))
         s.close()
 
 
@@ -135,14 +133,14 @@ def test_cfg1_full_fp64_and_fp32():
         got = [s.read(f).double().cpu().numpy() for f in range(6)]
         s.close()
         for f in range(6):
-            assert rel_l2(got60[f], want60[f]) <= TOL[prec], (prec, f, rel_l2(got60[f], want60[f]))
+            assert_close(got60[f], want60[f], prec, repr((prec, f,)))
         if prec == 64:
             for f in range(6):
-                assert rel_l2(got200[f], want200[f]) <= TOL[64], (f, rel_l2(got200[f], want200[f]))
+                assert_close(got200[f], want200[f], 64, repr((f,)))
                 diff = np.linalg.norm(got[f].reshape(-1) - want[f].reshape(-1))
                 assert diff <= TOL[64] * n0, (f, diff / n0)
         else:
-            assert rel_l2(np.stack(got200), want200) <= TOL[32]
+            assert_close(np.stack(got200), want200, 32)
             for f in range(6):
                 diff = np.linalg.norm(got[f].reshape(-1) - want[f].reshape(-1))
                 assert diff <= TOL[32] * n0, (f, diff / n0)
@@ -204,8 +202,8 @@ def test_sources_and_receivers_fp64():
         y[0] = u0.reshape(-1)
         src = {"idx": [g.flat(c) for c in coords], "amp": amp, "f_peak": f, "t_delay": t0}
         want, wtr = oracle.rk4(g, y, steps, 0.5, sources=src, receivers=[g.flat(c) for c in rec])
-        assert rel_l2(got, want[0]) <= TOL[prec]
-        assert rel_l2(gtr, wtr) <= TOL[prec]
+        assert_close(got, want[0], prec)
+        assert_close(gtr, wtr, prec)
 
 
 def test_sources_must_avoid_layer():
@@ -329,5 +327,4 @@ def test_full_size_cfg2_sampled(prec):
         wu, wv = _patch_oracle(u0, v0, sig, x, y, k, 4 * k + 2)
         got += [U[y, x], V[y, x]]
         want += [wu, wv]
-    err = rel_l2(got, want)
-    assert err <= TOL[prec], err
+    assert_close(got, want, prec, "sampled vertices (U and V)")

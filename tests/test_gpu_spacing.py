@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 
-from ._helpers import TOL, gaussian_u0, oracle_grid, rel_l2
+from ._helpers import assert_close, TOL, gaussian_u0, oracle_grid, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,7 @@ def test_3d_spacing(variant, prec):
     s.close()
     want = _oracle(N, w, h, u0, v0, steps, "constant")
     for f in range(8):
-        assert rel_l2(got[f], want[f]) <= TOL[prec], (f, rel_l2(got[f], want[f]))
+        assert_close(got[f], want[f], prec, repr((f,)))
 
 
 GRIDS = [((150, 90), 12, 1.0 / 80), ((64, 45), 6, 0.37), ((40, 33), 0, 2.5), ((23, 47), 5, 1.0)]
@@ -79,8 +79,7 @@ def test_batch_mixed_spacings(prec):
         want = _oracle(N, w, h, u0, v0, 35)
         assert s.step_count == 35
         for f in range(6):
-            err = rel_l2(s.read(f).double().cpu().numpy(), want[f])
-            assert err <= TOL[prec], (N, h, f, err)
+            assert_close(s.read(f).double().cpu().numpy(), want[f], prec, repr((N, h, f)))
     b.close()
     for s in solvers:
         s.close()

@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_1804_01390_gb300 import workloads as wk
 
-from ._helpers import TOL, gaussian_u0, make_solver, oracle_grid, rel_l2
+from ._helpers import assert_close, TOL, gaussian_u0, make_solver, oracle_grid, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -74,8 +74,7 @@ def test_two_step_variants_match_oracle(N, w, sigma, wall, steps):
         assert s.step_count == steps
         for f in range(6):
             got = s.read(f).double().cpu().numpy()
-            err = rel_l2(got, want[f].reshape(got.shape))
-            assert err <= TOL[32], (v, f, err)
+            assert_close(got, want[f].reshape(got.shape), 32, repr((v, f)))
     s.close()
 
 
@@ -156,7 +155,7 @@ def test_trace_buffer_full_allows_pairs():
     want, _ = oracle.rk4(g, y, 12, 0.5)
     for f in range(6):
         got = s.read(f).double().cpu().numpy()
-        assert rel_l2(got, want[f].reshape(got.shape)) <= TOL[32]
+        assert_close(got, want[f].reshape(got.shape), 32)
     s.close()
 
 
@@ -210,8 +209,7 @@ def test_full_size_cfg2_two_step_sampled(variant_pos):
         wu, wv = _patch_oracle(u0, sig, x, y, k, 4 * k + 2)
         got += [U[y, x], V[y, x]]
         want += [wu, wv]
-    err = rel_l2(got, want)
-    assert err <= TOL[32], err
+    assert_close(got, want, 32, "sampled vertices (U and V)")
 
 
 # ------------------------------------------------------------------------------------
@@ -263,8 +261,7 @@ def test_batch_two_step_odd_parities_match_oracle():
             assert s.step_count == 43
             for f in range(6):
                 got = s.read(f).double().cpu().numpy()
-                err = rel_l2(got, want[f].reshape(got.shape))
-                assert err <= TOL[32], (v, k, f, err)
+                assert_close(got, want[f].reshape(got.shape), 32, repr((v, k, f)))
         b.close()
         for s in solvers:
             s.close()
@@ -326,6 +323,6 @@ def test_two_step_transposed_matches_oracle(N, w, wall):
         g0 = oracle.Grid(g0.T, 1.0, [np.concatenate([s_[:-1], [0.0]]) for s_ in g0.sigmas], wall=True)
     yb, _ = oracle.adjoint(g0, g0.zeros_state(), steps, 0.5, steps, receivers=[g0.flat(c) for c in rec],
                            residual=residual)
-    assert rel_l2(gu.double().cpu().numpy(), yb[0]) <= TOL[32]
+    assert_close(gu.double().cpu().numpy(), yb[0], 32)
     for k, fk in enumerate(fields):
-        assert rel_l2(fk, yb[k]) <= TOL[32], (k, rel_l2(fk, yb[k]))
+        assert_close(fk, yb[k], 32, repr((k,)))

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 
-from ._helpers import TOL, gaussian_u0, rel_l2
+from ._helpers import assert_close, TOL, gaussian_u0, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -57,8 +57,7 @@ def test_wall_forward_parity_2d(N, w, sigma, prec):
     y[1] = v0.reshape(-1)
     want, _ = oracle.rk4(g, y, 23, 0.5)
     for f in range(6):
-        err = rel_l2(got[f], want[f])
-        assert err <= TOL[prec], (f, err)
+        assert_close(got[f], want[f], prec, repr((f)))
 
 
 CASES3 = [((21, 18, 15), 5, "quadratic"), ((30, 14, 12), 0, "constant"), ((16, 27, 20), 4, "random")]
@@ -80,8 +79,7 @@ def test_wall_forward_parity_3d(N, w, sigma, prec):
     y[1] = v0.reshape(-1)
     want, _ = oracle.rk4(g, y, 11, 0.5)
     for f in range(8):
-        err = rel_l2(got[f], want[f])
-        assert err <= TOL[prec], (f, err)
+        assert_close(got[f], want[f], prec, repr((f)))
 
 
 @pytest.mark.parametrize("N,w", [((40, 31), 6), ((18, 16, 14), 4)])
@@ -137,6 +135,5 @@ def test_wall_every_variant_2d(prec):
         s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
         s.step(steps)
         for f in range(6):
-            err = rel_l2(s.read(f).double().cpu().numpy(), want[f])
-            assert err <= TOL[prec], (v, f, err)
+            assert_close(s.read(f).double().cpu().numpy(), want[f], prec, repr((v, f)))
     s.close()
