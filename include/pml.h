@@ -298,7 +298,9 @@ pml_status pml_profile_read(pml_ctx *ctx, double ms[3], int64_t launches[3]);
 /*
  * Kernel variants and autotuning.  The layer-free (interior) kernel of a 2D context
  * exists in several shapes (columns per lane, rows per TMA box, pipeline depth,
- * resident CTAs per SM); 3D contexts have one.  Variants 0 .. n1-1 advance one step per
+ * resident CTAs per SM).  In 3D the variants are the kernels of the layer frame: 0 the
+ * z-streaming tile kernel, 1 level passes, 2 (FP32 only, the default there) slab tiles
+ * whose halo is 4 along axes with damping within reach and 2 along the others.  Variants 0 .. n1-1 advance one step per
  * pass; 2D FP32 contexts add variants n1 .. count-1 that advance two steps per pass
  * (temporal blocking depth 2, see pml_step), selecting one of those keeps the one-step
  * variant last selected for single steps and the adjoint.  pml_get_variant reports the

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace pml {
 
 // Ghost ring width of every padded field array.  The layer kernels read a halo of 4
@@ -439,6 +441,18 @@ constexpr int kLevel3TX = 32, kLevel3TY = 8, kLevel3TZ = 16;
 cudaError_t launch_level3d(int prec, bool adjoint, const Level3Args &a, cudaStream_t st);
 int layer3d_tile_x(int prec);
 int layer3d_tile_y(int prec);
+// The 3D layer frame by slab tiles (slab3d.cuh, FP32 only): tiles of class m (bit a: aux
+// fields of axis a within reach of the tile's outputs) have a region of rx x ry columns,
+// outputs inset by hx, hy (4 along active axes, 2 along the others) and z items of at most
+// kSlabItemZ output planes; tensor maps [class m][field f] with box rx x ry x 1.
+void slab3d_shape(int mask, int *rx, int *ry, int *hx, int *hy);
+// per class: threads, registers, the largest block the registers allow, shared memory
+std::string slab3d_describe(bool adjoint, bool wall);
+constexpr int kSlabItemZ = 64;
+cudaError_t launch_slab3d(bool adjoint, const CUtensorMap *tm /*[8][8]*/, void *const *out /*[8]*/,
+                          const Layer3DArgs &a, cudaStream_t st);
+cudaError_t launch_slab3d_wall(bool adjoint, const CUtensorMap *tm /*[8][8]*/, void *const *out /*[8]*/,
+                               const Layer3DArgs &a, cudaStream_t st);
 // The eight class launches follow each other with programmatic dependent launch (their
 // outputs are disjoint), the first one after all earlier work of the stream.
 cudaError_t launch_layer3d(int prec, bool adjoint, const CUtensorMap *tm /*[8]*/,

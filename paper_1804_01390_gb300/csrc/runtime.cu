@@ -44,6 +44,8 @@ struct Plan {
     size_t lvl[2][8] = {};       // 3D level passes: two scratch states
     size_t ltiles[2][4] = {};    // 3D level passes: tiles of each level, forward / transposed
     size_t max_ltiles = 0;
+    size_t slab_tiles[2] = {};   // 3D slab tiles (FP32), forward / transposed
+    size_t max_slab = 0;
     size_t sig[3] = {};
     size_t tiles = 0, tiles_adj = 0, max_tiles = 0, tiles_l1 = 0, tiles_l2 = 0, tiles_l1_adj = 0, tiles_l2_adj = 0;
     size_t partials = 0, normout = 0, err = 0, queue = 0;
@@ -117,6 +119,17 @@ bool make_plan(const pml_grid *grid, int w, int prec, int flags, Plan *p, std::s
             p->tiles_l2_adj = off; off += align_up(p->max_tiles * sizeof(LayerTile), kAlign);
         }
     }
+    if (p->nd == 3 && prec == 32) {
+        // slab tiles: at least 21 x 8 outputs per tile in (x, y) (after the alignment of the
+        // region's first column), z items of at least a quarter of kSlabItemZ planes or a
+        // whole run of the frame; a few runs of constant class per axis
+        p->max_slab = size_t(4) * size_t(p->T[0] / 21 + 12) * size_t(p->T[1] / 8 + 12) *
+                      size_t(p->T[2] / (kSlabItemZ / 4) + 12);
+        for (int d = 0; d < ((flags & PML_FLAG_ADJOINT) ? 2 : 1); ++d) {
+            p->slab_tiles[d] = off;
+            off += align_up(p->max_slab * sizeof(LayerTile), kAlign);
+        }
+    }
     if (p->nd == 3) {
         p->max_ltiles = size_t(3) * size_t(p->T[0] / kLevel3TX + 2) * size_t(p->T[1] / kLevel3TY + 2) *
                         size_t(p->T[2] / kLevel3TZ + 3);
@@ -182,7 +195,8 @@ struct pml_ctx {
     bool adj_ready = false;
     CUtensorMap tm_int[2][2], tm_lay[2][8], tm_int_adj[2][2], tm_lay_adj[2][8];
     int grid_int = 0, grid_int_adj = 0, sm_count = 0;
-    int ivar = 0;                       // interior kernel variant (2D, one step per pass)
+    int ivar = 0;                       // kernel variant: 2D interior shape (one step per pass); 3D frame
+                                        // kernel (0 tile kernel, 1 level passes, 2 slab tiles)
     // temporal blocking depth 2 (2D FP32): forward steps without sources or receiver rows
     // advance two at a time (layer pass 1 on the frame widened by 6 into mid, layer pass 2
     // on the frame widened by 2, two-step interior kernel on the run shrunk by 2)
@@ -197,6 +211,13 @@ struct pml_ctx {
     void *lvl[2][8] = {};
     LayerTile *dlt[2][4] = {};
     int nlt[2][4] = {};
+    // 3D FP32: variant 2 advances the layer frame by slab tiles (slab3d.cuh): tiles and
+    // class offsets (forward / transposed) and the tensor maps of each class's box,
+    // [forward / transposed][input parity][class * 8 + field]
+    LayerTile *dslab[2] = {};
+    int nslab[2] = {};
+    int slab_off[2][9] = {};
+    CUtensorMap tm_slab[2][2][64];
     // failure detection: limit of every bounded device wait (0: the default 2 s) and the
     // interval in steps of the finiteness scan of U and V (0: off)
     uint64_t wait_ns = 0;
@@ -474,6 +495,73 @@ std::vector<LayerTile> build_tiles_2d(const pml_ctx *c, const Range *ir, int cla
     if (c->nd != 2 || t.empty() || t.size() >= target) return t;
     const double f = double(t.size()) / double(target);
     return build_tiles(c, ir, class_off, std::max<int64_t>(8, int64_t(band0 * f)), std::max<int64_t>(6, int64_t(slab0 * f)));
+}
+
+// Slab tiles of the 3D frame of `ir` (FP32 variant 2).  Along each axis a coordinate is
+// active when aux fields of that axis are active within 4 vertices of it; each frame
+// rectangle is cut into boxes of constant class (the set of active axes), and each box
+// into tiles of its class's shape: regions of rx x ry columns whose first column is a
+// multiple of 4 (TMA alignment), outputs inset by hx, hy, z items of at most kSlabItemZ
+// output planes (z unwrapped across the periodic seam, as in frame_rects).
+std::vector<LayerTile> build_slab_tiles(const pml_ctx *c, const Range *ir, int class_off[9])
+{
+    std::vector<LayerTile> t;
+    std::vector<uint8_t> act[3];
+    for (int a = 0; a < 3; ++a) {
+        act[a].assign(size_t(c->T[a]), 0);
+        for (int64_t i = 0; i < c->T[a]; ++i) act[a][size_t(i)] = axis_active(c, a, i - 4, i + 5) ? 1 : 0;
+    }
+    struct Run {
+        int64_t lo, hi;
+        bool on;
+    };
+    auto runs = [&](int a, int64_t lo, int64_t hi) {   // maximal runs of constant activity (coordinates unwrapped)
+        std::vector<Run> r;
+        for (int64_t i = lo; i <= hi;) {
+            const bool on = act[a][size_t(((i % c->T[a]) + c->T[a]) % c->T[a])] != 0;
+            int64_t j = i;
+            while (j + 1 <= hi && (act[a][size_t((((j + 1) % c->T[a]) + c->T[a]) % c->T[a])] != 0) == on) ++j;
+            r.push_back({i, j, on});
+            i = j + 1;
+        }
+        return r;
+    };
+    auto floor4 = [](int64_t v) { return v >= 0 ? v / 4 * 4 : -((-v + 3) / 4 * 4); };
+    for (const Rect &r : frame_rects(c, ir)) {
+        for (const Run &rz : runs(2, r.lo[2], r.hi[2]))
+            for (const Run &ry : runs(1, r.lo[1], r.hi[1]))
+                for (const Run &rx : runs(0, r.lo[0], r.hi[0])) {
+                    const int mask = (rx.on ? 1 : 0) | (ry.on ? 2 : 0) | (rz.on ? 4 : 0);
+                    int RX, RY, HX, HY;
+                    slab3d_shape(mask, &RX, &RY, &HX, &HY);
+                    const int64_t nz = rz.hi - rz.lo + 1, nzi = (nz + kSlabItemZ - 1) / kSlabItemZ;
+                    int64_t z0 = rz.lo;
+                    for (int64_t zi = 0; zi < nzi; ++zi) {
+                        const int64_t len = nz / nzi + (zi < nz % nzi ? 1 : 0);
+                        for (int64_t ylo = ry.lo; ylo <= ry.hi;) {
+                            const int64_t ry0 = ylo - HY, yhi = std::min<int64_t>(ry0 + RY - 1 - HY, ry.hi);
+                            for (int64_t xlo = rx.lo; xlo <= rx.hi;) {
+                                const int64_t rx0 = floor4(xlo - HX), xhi = std::min<int64_t>(rx0 + RX - 1 - HX, rx.hi);
+                                LayerTile L{};
+                                L.x0 = int32_t(rx0); L.y0 = int32_t(ry0); L.z0 = int32_t(z0);
+                                L.xlo = int32_t(xlo); L.xhi = int32_t(xhi);
+                                L.ylo = int32_t(ylo); L.yhi = int32_t(yhi);
+                                L.zlo = int32_t(z0); L.zhi = int32_t(z0 + len - 1);
+                                L.flags = mask;
+                                t.push_back(L);
+                                xlo = xhi + 1;
+                            }
+                            ylo = yhi + 1;
+                        }
+                        z0 += len;
+                    }
+                }
+    }
+    std::stable_sort(t.begin(), t.end(), [](const LayerTile &a, const LayerTile &b) { return a.flags < b.flags; });
+    for (int m = 0; m <= 8; ++m) class_off[m] = 0;
+    for (const LayerTile &L : t) class_off[L.flags + 1]++;
+    for (int m = 0; m < 8; ++m) class_off[m + 1] += class_off[m];
+    return t;
 }
 
 // Tiles of the 3D level passes over the frame of `ir`: kLevel3TX x kLevel3TY columns by
@@ -775,6 +863,25 @@ pml_status enqueue_step(pml_ctx *c, bool adjoint, int p)
                 if (e != cudaSuccess) return cuda_fail(c, e, "level pass 3D kernel");
                 layer_launched = layer_launched || L.ntiles > 0;
             }
+        } else if (c->ivar == 2) {   // slab tiles (FP32)
+            const int d = adjoint ? 1 : 0;
+            Layer3DArgs l{};
+            l.g = c->g; l.k = layer_const(c);
+            for (int a2 = 0; a2 < 3; ++a2) l.sig[a2] = c->dsig[a2];
+            l.tiles = c->dslab[d];
+            l.ntiles = c->nslab[d];
+            for (int m = 0; m < 9; ++m) l.class_off[m] = c->slab_off[d][m];
+            l.err = c->derr;
+            l.wait_ns = c->wait_ns;
+            long pi = prof_begin(c, 1);
+            e = launch_slab3d(adjoint, c->tm_slab[d][p], out, l, c->st);
+            prof_end(c, pi);
+            if (e != cudaSuccess) {
+                char what[256];
+                std::snprintf(what, sizeof what, "slab 3D kernel (%s)", slab3d_describe(adjoint, c->g.wall != 0).c_str());
+                return cuda_fail(c, e, what);
+            }
+            layer_launched = l.ntiles > 0;
         } else {
             Layer3DArgs l{};
             l.g = c->g; l.k = layer_const(c);
@@ -861,8 +968,9 @@ pml_status enqueue_double_step(pml_ctx *c, bool adjoint, int p)
     return PML_OK;
 }
 
-// 2D: the interior kernel's shapes; 3D: 0 the z-streaming layer tile kernel, 1 level passes
-int one_step_variants(const pml_ctx *c) { return c->nd == 2 ? interior2d_variants(c->prec) : 2; }
+// 2D: the interior kernel's shapes; 3D: 0 the z-streaming layer tile kernel, 1 level passes,
+// 2 (FP32) slab tiles
+int one_step_variants(const pml_ctx *c) { return c->nd == 2 ? interior2d_variants(c->prec) : (c->prec == 32 ? 3 : 2); }
 int two_step_variants(const pml_ctx *c) { return c->plan.tb2 ? interior2d_tb2_variants(c->prec) : 0; }
 
 // Grid sizes of the interior kernels for the current variant: all resident CTAs.
@@ -1095,6 +1203,22 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
                 if (e != cudaSuccess) { cuda_fail(c, e, "upload level tiles"); return bail(PML_ECUDA); }
             }
     }
+    // 3D FP32 slab tiles (variant 2)
+    if (c->nd == 3 && c->prec == 32) {
+        for (int d = 0; d < ((flags & PML_FLAG_ADJOINT) ? 2 : 1); ++d) {
+            std::vector<LayerTile> st = build_slab_tiles(c, d ? c->ir_adj : c->ir, c->slab_off[d]);
+            if (st.size() > plan.max_slab) {
+                fail(c, PML_ENOMEM, "slab tile table exceeds its bound");
+                return bail(PML_ENOMEM);
+            }
+            c->dslab[d] = reinterpret_cast<LayerTile *>(c->ws + plan.slab_tiles[d]);
+            c->nslab[d] = int(st.size());
+            cudaError_t e = st.empty() ? cudaSuccess
+                                       : cudaMemcpy(c->dslab[d], st.data(), st.size() * sizeof(LayerTile),
+                                                    cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { cuda_fail(c, e, "upload slab tiles"); return bail(PML_ECUDA); }
+        }
+    }
     // two-step blocks: the second pass writes the frame of the run shrunk by 2, from first-
     // step values the first pass writes on the frame of the run shrunk by 6 (4 more: the
     // reach of one layer step)
@@ -1168,6 +1292,18 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             }
             for (int f = c->nf; f < 8; ++f) { c->tm_lay[p][f] = c->tm_lay[p][0]; c->tm_lay_adj[p][f] = c->tm_lay_adj[p][0]; }
         }
+        if (c->nd == 3 && c->prec == 32)   // slab tiles: one box shape per class
+            for (int m = 0; m < 8; ++m) {
+                int RX, RY, HX, HY;
+                slab3d_shape(m, &RX, &RY, &HX, &HY);
+                const uint32_t box_s[3] = {uint32_t(RX), uint32_t(RY), 1};
+                for (int d = 0; d < ((flags & PML_FLAG_ADJOINT) ? 2 : 1); ++d)
+                    for (int p = 0; p < 2; ++p)
+                        for (int f = 0; f < 8; ++f)
+                            if ((s = encode_map(c, &c->tm_slab[d][p][m * 8 + f], (d ? c->adj : c->fld)[p][f < c->nf ? f : 0],
+                                                box_s)) != PML_OK)
+                                return bail(s);
+            }
         if (plan.tb2) {
             for (int f = 0; f < c->nf; ++f)
                 if ((s = encode_map(c, &c->tm_mid[f], c->mid[f], box_lay)) != PML_OK) return bail(s);
@@ -1175,6 +1311,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             if ((s = encode_tb_maps(c)) != PML_OK) return bail(s);
         }
     }
+    if (c->nd == 3 && c->prec == 32) c->ivar = 2;   // slab tiles: the fastest 3D frame variant
     if ((s = interior_grids(c)) != PML_OK) return bail(s);
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) { cuda_fail(c, e, "create"); return bail(PML_ECUDA); }

@@ -16,6 +16,8 @@
 //    register rings, x/y neighbours in one shared plane per level; one block barrier per
 //    plane.  Templated on the set of axes whose aux fields are active in the tile, so
 //    face tiles carry 4 fields, edge tiles 6 and corner tiles 8.
+#include <cstdio>
+
 #include "common.cuh"
 
 namespace pml {
@@ -342,8 +344,53 @@ cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, co
 }  // namespace pml
 
 #include "layer3d.cuh"
+#include "slab3d.cuh"
 
 namespace pml {
+
+void slab3d_shape(int mask, int *rx, int *ry, int *hx, int *hy)
+{
+    switch (mask & 7) {
+#define PML_SHAPE(M) \
+    case M: *rx = Slab<M>::RX; *ry = Slab<M>::RY; *hx = Slab<M>::HX; *hy = Slab<M>::HY; break;
+        PML_SHAPE(0) PML_SHAPE(1) PML_SHAPE(2) PML_SHAPE(3) PML_SHAPE(4) PML_SHAPE(5) PML_SHAPE(6)
+        default: *rx = Slab<7>::RX; *ry = Slab<7>::RY; *hx = Slab<7>::HX; *hy = Slab<7>::HY; break;
+#undef PML_SHAPE
+    }
+}
+
+template <bool ADJ, bool WALL, int M> static void describe_one(std::string &out)
+{
+    cudaFuncAttributes fa{};
+    const cudaError_t e = cudaFuncGetAttributes(&fa, k_slab3d<ADJ, M, WALL>);
+    char buf[160];
+    if (e != cudaSuccess) std::snprintf(buf, sizeof buf, "class %d: %s; ", M, cudaGetErrorString(e));
+    else
+        std::snprintf(buf, sizeof buf, "class %d: %d threads, %d regs, max block %d, smem %zu+%zu; ", M, Slab<M>::NT,
+                      fa.numRegs, fa.maxThreadsPerBlock, size_t(fa.sharedSizeBytes), Slab<M>::SMEM);
+    out += buf;
+}
+template <bool ADJ, bool WALL> static std::string describe_all()
+{
+    std::string s;
+    describe_one<ADJ, WALL, 0>(s); describe_one<ADJ, WALL, 1>(s); describe_one<ADJ, WALL, 2>(s);
+    describe_one<ADJ, WALL, 3>(s); describe_one<ADJ, WALL, 4>(s); describe_one<ADJ, WALL, 5>(s);
+    describe_one<ADJ, WALL, 6>(s); describe_one<ADJ, WALL, 7>(s);
+    return s;
+}
+std::string slab3d_describe_wall(bool adjoint);   // layer3d_wall.cu
+std::string slab3d_describe(bool adjoint, bool wall)
+{
+    if (wall) return slab3d_describe_wall(adjoint);
+    return adjoint ? describe_all<true, false>() : describe_all<false, false>();
+}
+
+cudaError_t launch_slab3d(bool adjoint, const CUtensorMap *tm, void *const *outp, const Layer3DArgs &a,
+                          cudaStream_t st)
+{
+    if (a.g.wall) return launch_slab3d_wall(adjoint, tm, outp, a, st);   // layer3d_wall.cu
+    return launch_slab3d_impl<false>(adjoint, tm, outp, a, st);
+}
 
 int layer3d_tile_x(int prec) { return prec == 32 ? kLayer3TXf : kLayer3TXd; }
 int layer3d_tile_y(int prec) { return prec == 32 ? kLayer3TYf : kLayer3TYd; }

@@ -31,7 +31,7 @@ def _gpu(N, w, prec, sigma, draws, u0, v0, steps, variant, wall=False, dt=0.4):
     s = PMLSolver(N, w, dt=dt, sigma=sigma, sigma_max=2.0, draws=draws, precision=prec,
                   device=torch.device("cuda:0"), wall=wall)
     _lib.pml_set_variant(s.ctx, variant)
-    assert _lib.pml_get_variant(s.ctx) == (variant, 2)
+    assert _lib.pml_get_variant(s.ctx) == (variant, 3 if prec == 32 else 2)
     s.set_initial(torch.from_numpy(u0), torch.from_numpy(v0))
     s.step(steps)
     got = [s.read(f).double().cpu().numpy() for f in range(8)]

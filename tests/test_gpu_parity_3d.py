@@ -118,9 +118,12 @@ def _patch3(u0, sig, x, y, z, k, Rp):
 
 
 def test_full_size_cfg3_sampled():
-    """Config 3 size (512^3 + 24-cell layer, FP32) in the benchmark's launch
-    configuration: two steps, sampled vertices recomputed by the oracle on local patches."""
+    """Config 3 size (512^3 + 24-cell layer, FP32) with the z-streaming tile kernel of the
+    frame (variant 0; the slab tiles that FP32 3D contexts use by default have their own
+    full-size check): two steps, sampled vertices recomputed by the oracle on local
+    patches."""
     import torch
+    from paper_1804_01390_gb300 import _lib
     wl = wk.cfg3()
     T = wl.T
     u0 = wk.initial_field(wl)
@@ -128,6 +131,7 @@ def test_full_size_cfg3_sampled():
     u0[:30, :30, :30] += rng.normal(scale=0.2, size=(30, 30, 30))     # corner, across the seams
     u0[-20:, 200:230, -25:] += rng.normal(scale=0.2, size=(20, 30, 25))
     s = make_solver(wl.N, wl.w, 32)
+    _lib.pml_set_variant(s.ctx, 0)
     s.set_initial(torch.from_numpy(u0.astype(np.float32)))
     k = 2
     s.step(k)
