@@ -406,13 +406,47 @@ std::vector<Rect> frame_rects(const pml_ctx *c, const Range *ir)
     return out;
 }
 
+// Activity of axis a per coordinate: aux fields of that axis are active within 4 vertices.
+// Along an inactive stretch the layer kernels need a halo of 2 instead of 4.
+std::vector<uint8_t> axis_activity(const pml_ctx *c, int a)
+{
+    std::vector<uint8_t> act(size_t(c->T[a]), 0);
+    if (a < c->nd)
+        for (int64_t i = 0; i < c->T[a]; ++i) act[size_t(i)] = axis_active(c, a, i - 4, i + 5) ? 1 : 0;
+    return act;
+}
+
+struct ActRun {
+    int64_t lo, hi;
+    bool on;
+};
+
+// Maximal runs of constant activity over the coordinates lo..hi (unwrapped: coordinate i
+// reads act[i mod T]).
+std::vector<ActRun> activity_runs(const std::vector<uint8_t> &act, int64_t lo, int64_t hi)
+{
+    const int64_t T = int64_t(act.size());
+    auto on = [&](int64_t i) { return act[size_t(((i % T) + T) % T)] != 0; };
+    std::vector<ActRun> r;
+    for (int64_t i = lo; i <= hi;) {
+        const bool o = on(i);
+        int64_t j = i;
+        while (j + 1 <= hi && on(j + 1) == o) ++j;
+        r.push_back({i, j, o});
+        i = j + 1;
+    }
+    return r;
+}
+
 // Layer tiles of the frame, sorted by flags (bit a: aux fields of axis a reach the tile's
 // footprint) so that each class runs with its own field count.
-//  2D: strips of layer2d_tile_cols() output columns streamed down the rows by one warp.  The rows
-//      outside ir[1] form one band across the periodic seam of y (unwrapped rows
-//      ir[1].hi + 1 .. T1 + ir[1].lo - 1), cut into near-equal runs of at most
-//      kLayer2BandRows rows over the full width; the columns outside ir[0] (rows ir[1])
-//      are cut into runs of at most kLayer2SlabRows rows.
+//  2D: strips of 32 columns streamed down the rows by one warp, cut from stretches of
+//      constant activity along x and y (see axis_activity): 24 outputs with a halo of 4
+//      where x is active, 28 with a halo of 2 where it is not.  The rows outside ir[1]
+//      form one band across the periodic seam of y (unwrapped rows ir[1].hi + 1 ..
+//      T1 + ir[1].lo - 1), cut into near-equal runs of at most kLayer2BandRows rows over the
+//      full width; the columns outside ir[0] (rows ir[1]) are cut into runs of at most
+//      kLayer2SlabRows rows.
 //  3D: (x, y) column tiles streamed over z segments of at most kLayer3LZ planes (zlo..zhi,
 //      unwrapped).
 std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_off[9],
@@ -420,27 +454,32 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
 {
     std::vector<LayerTile> t;
     if (c->nd == 2) {
-        const int TW = layer2d_tile_cols(c->prec);
+        // strips of 32 columns: 24 outputs along a damped x (halo 4), 28 along an undamped
+        // one (halo 2); the first column of a strip's box is a multiple of 4 (TMA alignment)
+        const int COLS = layer2d_box_cols(c->prec);
+        const std::vector<uint8_t> act0 = axis_activity(c, 0), act1 = axis_activity(c, 1);
         auto add = [&](int64_t xlo, int64_t xhi, int64_t ylo, int64_t yhi, int64_t maxrows) {
-            const int64_t H = yhi - ylo + 1;
-            if (xhi < xlo || H <= 0) return;
-            const int64_t nseg = (H + maxrows - 1) / maxrows;
-            int64_t y0 = ylo;
-            for (int64_t sgi = 0; sgi < nseg; ++sgi) {
-                const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
-                for (int64_t x0 = xlo & ~int64_t(3); x0 <= xhi; x0 += TW) {
-                    LayerTile L{};
-                    L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = 0;
-                    L.xlo = int32_t(xlo); L.xhi = int32_t(xhi);
-                    L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
-                    int fl = 0;
-                    if (axis_active(c, 0, x0 - 4, x0 + TW + 4)) fl |= 1;
-                    if (axis_active(c, 1, L.ylo - 4, L.yhi + 5)) fl |= 2;
-                    L.flags = fl;
-                    t.push_back(L);
+            if (xhi < xlo || yhi < ylo) return;
+            for (const ActRun &ry : activity_runs(act1, ylo, yhi))
+                for (const ActRun &rx : activity_runs(act0, xlo, xhi)) {
+                    const int HX = rx.on ? 4 : 2, OUT = COLS - 2 * HX;
+                    const int64_t H = ry.hi - ry.lo + 1;
+                    const int64_t nseg = (H + maxrows - 1) / maxrows;
+                    int64_t y0 = ry.lo;
+                    for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+                        const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
+                        const int64_t first = rx.lo - ((((rx.lo - HX) % 4) + 4) % 4);
+                        for (int64_t x0 = first; x0 <= rx.hi; x0 += OUT) {
+                            LayerTile L{};
+                            L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = 0;
+                            L.xlo = int32_t(rx.lo); L.xhi = int32_t(rx.hi);
+                            L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
+                            L.flags = (rx.on ? 1 : 0) | (ry.on ? 2 : 0);
+                            t.push_back(L);
+                        }
+                        y0 += len;
+                    }
                 }
-                y0 += len;
-            }
         };
         const int64_t T0 = c->T[0], T1 = c->T[1];
         if (range_empty(ir[0]) || range_empty(ir[1])) {
@@ -506,31 +545,13 @@ std::vector<LayerTile> build_tiles_2d(const pml_ctx *c, const Range *ir, int cla
 std::vector<LayerTile> build_slab_tiles(const pml_ctx *c, const Range *ir, int class_off[9])
 {
     std::vector<LayerTile> t;
-    std::vector<uint8_t> act[3];
-    for (int a = 0; a < 3; ++a) {
-        act[a].assign(size_t(c->T[a]), 0);
-        for (int64_t i = 0; i < c->T[a]; ++i) act[a][size_t(i)] = axis_active(c, a, i - 4, i + 5) ? 1 : 0;
-    }
-    struct Run {
-        int64_t lo, hi;
-        bool on;
-    };
-    auto runs = [&](int a, int64_t lo, int64_t hi) {   // maximal runs of constant activity (coordinates unwrapped)
-        std::vector<Run> r;
-        for (int64_t i = lo; i <= hi;) {
-            const bool on = act[a][size_t(((i % c->T[a]) + c->T[a]) % c->T[a])] != 0;
-            int64_t j = i;
-            while (j + 1 <= hi && (act[a][size_t((((j + 1) % c->T[a]) + c->T[a]) % c->T[a])] != 0) == on) ++j;
-            r.push_back({i, j, on});
-            i = j + 1;
-        }
-        return r;
-    };
+    const std::vector<uint8_t> act[3] = {axis_activity(c, 0), axis_activity(c, 1), axis_activity(c, 2)};
+    auto runs = [&](int a, int64_t lo, int64_t hi) { return activity_runs(act[a], lo, hi); };
     auto floor4 = [](int64_t v) { return v >= 0 ? v / 4 * 4 : -((-v + 3) / 4 * 4); };
     for (const Rect &r : frame_rects(c, ir)) {
-        for (const Run &rz : runs(2, r.lo[2], r.hi[2]))
-            for (const Run &ry : runs(1, r.lo[1], r.hi[1]))
-                for (const Run &rx : runs(0, r.lo[0], r.hi[0])) {
+        for (const ActRun &rz : runs(2, r.lo[2], r.hi[2]))
+            for (const ActRun &ry : runs(1, r.lo[1], r.hi[1]))
+                for (const ActRun &rx : runs(0, r.lo[0], r.hi[0])) {
                     const int mask = (rx.on ? 1 : 0) | (ry.on ? 2 : 0) | (rz.on ? 4 : 0);
                     int RX, RY, HX, HY;
                     slab3d_shape(mask, &RX, &RY, &HX, &HY);

@@ -636,13 +636,16 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     using O = LV<T, W>;
     using V = typename O::V;
     constexpr int NF = F::NF, CH = kL2CH, S = L2Cfg<T>::S, RR = L2Cfg<T>::RR;
+    // halo of 4 along a damped axis, 2 along an undamped one (there U and V of every Horner
+    // level depend on the level above only through the Laplacian of V)
+    constexpr int HX = (MASK & 1) ? 4 : 2, HY = (MASK & 2) ? 4 : 2, OUT = COLS - 2 * HX;
     const Geom &g = a.g;
     const int T1 = int(g.T[1]);
-    const int nout = tile.yhi - tile.ylo + 1, nin = nout + 8;
+    const int nout = tile.yhi - tile.ylo + 1, nin = nout + 2 * HY;
     const int nch = (nin + CH - 1) / CH;          // boxes that hold input rows
-    const int32_t tx = tile.x0 - 4 + G;
+    const int32_t tx = tile.x0 - HX + G;
     auto box_y = [&](int c) -> int32_t {          // box row of box c (rows stay in -4 .. T1 + 3)
-        int y = tile.ylo - 4 + c * CH;
+        int y = tile.ylo - HY + c * CH;
         if (!WALL && y > T1) y -= T1;              // with a wall, items never cross the seam and
         return int32_t(y + G);                     // rows beyond the ghost ring load as zeros
     };
@@ -657,7 +660,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     if (MASK & 2) {   // sigma_y[row], sigma_y[row - 1] of every input row
         const T *sgy = static_cast<const T *>(a.sig[1]);
         for (int q = lane; q < nin; q += 32) {
-            int yi = tile.ylo - 4 + q;
+            int yi = tile.ylo - HY + q;
             yi += yi < 0 ? T1 : 0;
             yi -= yi >= T1 ? T1 : 0;
             yi -= yi >= T1 ? T1 : 0;
@@ -667,7 +670,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     }
     __syncwarp();
 
-    const int64_t gx0 = int64_t(tile.x0) - 4 + W * lane;   // first column of the lane
+    const int64_t gx0 = int64_t(tile.x0) - HX + W * lane;   // first column of the lane
     Sig2<V> sgx;
     {
         const T *sgxp = static_cast<const T *>(a.sig[0]);
@@ -701,7 +704,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     bool out_col[W];
 #pragma unroll
     for (int k = 0; k < W; ++k)
-        out_col[k] = gx0 + k >= tile.x0 && gx0 + k < tile.x0 + L2Cfg<T>::OUT && gx0 + k >= tile.xlo &&
+        out_col[k] = gx0 + k >= tile.x0 && gx0 + k < tile.x0 + OUT && gx0 + k >= tile.xlo &&
                      gx0 + k <= tile.xhi;
     bool any_out = false;
 #pragma unroll
@@ -721,7 +724,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
     }
     auto wall_mask = [&](V v, int q) -> V {        // level value at input row q
         if (!WALL) return v;
-        const int y = tile.ylo - 4 + q;
+        const int y = tile.ylo - HY + q;
         return (y >= 0 && y < T1) ? O::sel(xmask, v) : O::bc(T(0));
     };
     const int qmax = nch * CH - 1;                 // last row the boxes brought in
@@ -738,8 +741,22 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
 #pragma unroll
         for (int f = 0; f < NF; ++f) z4[k][f] = z3[k][f] = z2[k][f] = O::bc(T(0));
 
+    // ghost images of the lane's columns (a vertex within G of the box edge is also stored
+    // at its periodic image in the ghost ring; 0: none, and with a wall the ring stays zero)
+    int64_t dxk[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const int64_t x = gx0 + k;
+        dxk[k] = g.wrap[0] == 0 ? 0 : (x < G ? g.wrap[0] : (x >= g.T[0] - G ? -g.wrap[0] : 0));
+    }
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < W; ++k) all = all && out_col[k];
+
+    // iteration p reads input rows p .. p - 7; the output row of input row r is formed in
+    // iteration r + 7
 #pragma unroll 1
-    for (int p = 0; p < nin + 3; ++p) {
+    for (int p = 0; p < nin + 7 - HY; ++p) {
         if ((p & (CH - 1)) == 0) {
             const int c = p / CH;
             // box c - 3 was last read in iteration p - 2: refill its slot with box c - 3 + S
@@ -847,28 +864,33 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
                 }
             };
             apply_A2<O, ADJ, MASK>(N, sig_at(p - 7), ih, ih2, i2h, r);
-            const int ro = p - 11;
+            const int ro = p - 7 - HY;
             if (any_out && ro >= 0 && ro < nout) {
                 int64_t y = int64_t(tile.ylo) + ro;
                 if (y >= T1) y -= T1;
-                bool edge = false;
-#pragma unroll
-                for (int k = 0; k < W; ++k) edge = edge || near_edge(g, gx0 + k, y, 0);
-                bool all = true;
-#pragma unroll
-                for (int k = 0; k < W; ++k) all = all && out_col[k];
+                const int64_t dy = g.wrap[1] == 0 ? 0 : (y < G ? g.wrap[1] : (y >= T1 - G ? -g.wrap[1] : 0)) * g.P;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     const V val = O::fma(c1, r[f], O::ld(y7 + f * FS));
-                    T *dst = static_cast<T *>(out.p[F::gid(f)]);
-                    if (!edge && all) {
-                        *reinterpret_cast<V *>(dst + g.origin + gx0 + y * g.P) = val;
+                    T *b = static_cast<T *>(out.p[F::gid(f)]) + g.origin + gx0 + y * g.P;
+                    const T *vv = reinterpret_cast<const T *>(&val);
+                    if (all) {
+                        *reinterpret_cast<V *>(b) = val;
+                        if (dy) *reinterpret_cast<V *>(b + dy) = val;
                     } else {
-                        const T *vv = reinterpret_cast<const T *>(&val);
 #pragma unroll
                         for (int k = 0; k < W; ++k)
-                            if (out_col[k]) store_wrapped(dst, g, gx0 + k, y, 0, vv[k]);
+                            if (out_col[k]) {
+                                b[k] = vv[k];
+                                if (dy) b[k + dy] = vv[k];
+                            }
                     }
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+                        if (out_col[k] && dxk[k]) {
+                            b[k + dxk[k]] = vv[k];
+                            if (dy) b[k + dxk[k] + dy] = vv[k];
+                        }
                 }
             }
         }
