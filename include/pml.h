@@ -273,6 +273,10 @@ pml_status pml_adjoint_step(pml_ctx *ctx, int64_t n, const void *residual, void 
  */
 pml_status pml_sigma_gradient(pml_ctx *ctx, int64_t n, const void *target, const void *residual,
                               int64_t interval, double *grad_sigma, double *misfit, double *grad_amp);
+/* Device bytes pml_sigma_gradient(ctx, n, ..., interval, ...) allocates for its duration
+ * (checkpoints, the states of one segment, six stage states and small tables), with the
+ * context's current receivers. */
+pml_status pml_sigma_gradient_bytes(const pml_ctx *ctx, int64_t n, int64_t interval, size_t *bytes);
 
 /* Copy field PML_FIELD_* of the adjoint state into a dense T-grid (host or device). */
 pml_status pml_adjoint_read_field(pml_ctx *ctx, int field, void *dst, int on_device);

@@ -48,7 +48,7 @@ EXPORTED = (
     "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
     "pml_set_check_interval", "pml_set_wait_limit",
     "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
-    "pml_adjoint_read_field", "pml_sigma_gradient", "pml_state_bytes", "pml_save_state", "pml_load_state",
+    "pml_adjoint_read_field", "pml_sigma_gradient", "pml_sigma_gradient_bytes", "pml_state_bytes", "pml_save_state", "pml_load_state",
     "pml_get_variant", "pml_set_variant", "pml_get_time_block", "pml_autotune",
     "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
     "pml_batch_create", "pml_batch_step", "pml_batch_get_variant", "pml_batch_set_variant",
@@ -111,6 +111,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_adjoint_step": [P, i64, P, P, P],
         "pml_adjoint_read_field": [P, ctypes.c_int, P, ctypes.c_int],
         "pml_sigma_gradient": [P, i64, P, P, i64, P, P, P],
+        "pml_sigma_gradient_bytes": [P, i64, i64, ctypes.POINTER(ctypes.c_size_t)],
         "pml_state_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
         "pml_save_state": [P, P, ctypes.c_int],
         "pml_load_state": [P, P, ctypes.c_int],
@@ -253,6 +254,12 @@ def pml_sigma_gradient(ctx, n, target, residual, interval, grad_sigma, grad_amp=
     _check(load().pml_sigma_gradient(ctx, int(n), target, residual, int(interval), grad_sigma.ctypes.data,
                                      ctypes.byref(J), None if grad_amp is None else grad_amp.ctypes.data), ctx)
     return float(J.value)
+
+
+def pml_sigma_gradient_bytes(ctx, n, interval=0) -> int:
+    v = ctypes.c_size_t(0)
+    _check(load().pml_sigma_gradient_bytes(ctx, int(n), int(interval), ctypes.byref(v)), ctx)
+    return int(v.value)
 
 
 def pml_state_bytes(ctx) -> int:

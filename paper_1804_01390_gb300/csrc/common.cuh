@@ -480,9 +480,10 @@ inline cudaError_t launch_pdl(K kernel, int grid, int threads, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Damping gradient (grad_sigma.cu): explicit stage evaluations on lists of row segments
-// {x0, x1, y, z} (inclusive x range of row (y, z)) and the per-edge contraction
-// kbar^T (dA/dsigma_a[e]) Y of the four stage pairs of a step.
+// Damping gradient (grad_sigma.cu): explicit stage evaluations on lists of row chunks
+// {x0, x1, y, z} (inclusive x range of row (y, z), at most kStageChunkMax vertices each) and
+// the per-edge contraction kbar^T (dA/dsigma_a[e]) Y of the four stage pairs of a step.
+constexpr int kStageChunkMax = 64;
 struct SigmaPtrs {
     const void *p[3];          // device sigma per axis (context precision)
 };

@@ -38,77 +38,62 @@ template <typename T> struct FldW {
     T *f[8];
 };
 
-// Neighbour of flat offset o along axis a (s = +1 / -1) at coordinate c_a: the periodic
-// image, or with a wall no vertex at all beyond the ends (the value there is zero).
-struct Nb {
-    int64_t off;
-    bool ok;
-};
-__device__ __forceinline__ Nb neighbour(const Idx &ix, int64_t o, int a, int64_t ca, int s, bool wall)
-{
-    const int64_t st = a == 0 ? 1 : (a == 1 ? ix.P : ix.PS);
-    const int64_t Ta = ix.T[a];
-    int64_t c = ca + s;
-    if (c < 0 || c >= Ta) {
-        if (wall) return {o, false};
-        c = c < 0 ? c + Ta : c - Ta;
-    }
-    return {o + (c - ca) * st, true};
-}
+// out = alpha base + cop Op(in) (Op = A, the forward operator of Eq. 3, or its
+// transpose) on chunks {x0, x1, y, z} of at most kStageChunk consecutive vertices of a row,
+// one block per chunk and one thread per vertex.  Every value of `in` the stencil reads
+// must be valid: the caller's chunks for `out` lie one vertex inside those on which `in`
+// was formed.  Neighbours by offset, wrapped only at the ends of an axis (or zero beyond
+// them with a wall); the ghost ring is never read.
+constexpr int kStageChunk = kStageChunkMax;
 
-// out = alpha base + cop Op(in) on the row segments seg[0..nseg) (Op = A, the forward
-// operator of Eq. 3, or its transpose), one warp per segment in turn.  Every value of
-// `in` the stencil reads must be valid: the caller's segments for `out` lie one vertex
-// inside those on which `in` was formed.
-template <typename T, bool ADJ>
-__global__ void __launch_bounds__(256) k_stage(const Fld<T> in, const Fld<T> base, const FldW<T> out, const Idx ix,
-                                               SigmaPtrs s, T ih, T ih2, T i2h, T alpha, T cop, const int4 *seg,
-                                               int nseg, int wall)
+template <typename T, bool ADJ, int ND>
+__global__ void __launch_bounds__(kStageChunk) k_stage(const Fld<T> in, const Fld<T> base, const FldW<T> out,
+                                                       const Idx ix, SigmaPtrs s, T ih, T ih2, T i2h, T alpha,
+                                                       T cop, const int4 *seg, int wall)
 {
-    const int lane = threadIdx.x & 31;
-    const int nwarp = int(gridDim.x * blockDim.x) >> 5;
-    for (int k = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nseg; k += nwarp) {
-        const int4 sg4 = seg[k];
-        const int64_t y = sg4.z, z = sg4.w;
-        for (int64_t x = sg4.x + lane; x <= sg4.y; x += 32) {
-            const int64_t c[3] = {x, y, z};
-            const int64_t o = ix.off(x, y, z);
-            T acc = T(0);   // V row (forward) or U row (transpose)
-            for (int a = 0; a < ix.nd; ++a) {
-                const Nb p = neighbour(ix, o, a, c[a], +1, wall != 0), m = neighbour(ix, o, a, c[a], -1, wall != 0);
-                const T *sgm = static_cast<const T *>(s.p[a]);
-                const int64_t Ta = ix.T[a];
-                const T si = sgm[c[a]], sm = sgm[c[a] == 0 ? Ta - 1 : c[a] - 1];
-                const T *L = in.f[ADJ ? 1 : 0];
-                const T Lp = p.ok ? L[p.off] : T(0), Lm = m.ok ? L[m.off] : T(0);
-                acc += (Lp - T(2) * L[o] + Lm) * ih2;
-                const T *Ph = in.f[2 + 2 * a], *Ps = in.f[3 + 2 * a];
-                const T php = p.ok ? Ph[p.off] : T(0), phm = m.ok ? Ph[m.off] : T(0);
-                const T psp = p.ok ? Ps[p.off] : T(0), psm = m.ok ? Ps[m.off] : T(0);
-                T oph, ops;
-                if (!ADJ) {
-                    const T *U = in.f[0];
-                    const T dU = ((p.ok ? U[p.off] : T(0)) - (m.ok ? U[m.off] : T(0))) * i2h;
-                    acc += (si * psp - sm * phm) * ih;
-                    oph = si != T(0) ? -T(0.5) * (sm * phm + si * Ph[o]) - dU : T(0);
-                    ops = sm != T(0) ? -T(0.5) * (sm * Ps[o] + si * psp) - dU : T(0);
-                } else {
-                    const T *Vb = in.f[1];
-                    acc += ((php - phm) + (psp - psm)) * i2h;
-                    oph = si != T(0) ? -si * (p.ok ? Vb[p.off] : T(0)) * ih - T(0.5) * si * (php + Ph[o]) : T(0);
-                    ops = sm != T(0) ? sm * (m.ok ? Vb[m.off] : T(0)) * ih - T(0.5) * sm * (Ps[o] + psm) : T(0);
-                }
-                out.f[2 + 2 * a][o] = alpha * base.f[2 + 2 * a][o] + cop * oph;
-                out.f[3 + 2 * a][o] = alpha * base.f[3 + 2 * a][o] + cop * ops;
-            }
-            if (!ADJ) {
-                out.f[0][o] = alpha * base.f[0][o] + cop * in.f[1][o];
-                out.f[1][o] = alpha * base.f[1][o] + cop * acc;
-            } else {
-                out.f[0][o] = alpha * base.f[0][o] + cop * acc;
-                out.f[1][o] = alpha * base.f[1][o] + cop * in.f[0][o];
-            }
+    const int4 sg4 = seg[blockIdx.x];
+    const int64_t x = sg4.x + int64_t(threadIdx.x);
+    if (x > sg4.y) return;
+    const int64_t c[3] = {x, sg4.z, sg4.w};
+    const int64_t st[3] = {1, ix.P, ix.PS};
+    const int64_t o = ix.off(c[0], c[1], c[2]);
+    T acc = T(0);   // V row (forward) or U row (transpose)
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        const int64_t Ta = ix.T[a];
+        const bool okp = c[a] + 1 < Ta || !wall, okm = c[a] > 0 || !wall;
+        const int64_t op = o + (c[a] + 1 < Ta ? st[a] : -(Ta - 1) * st[a]);
+        const int64_t om = o + (c[a] > 0 ? -st[a] : (Ta - 1) * st[a]);
+        const T *sgm = static_cast<const T *>(s.p[a]);
+        const T si = sgm[c[a]], sm = sgm[c[a] > 0 ? c[a] - 1 : Ta - 1];
+        const T *L = in.f[ADJ ? 1 : 0];
+        const T Lc = L[o];
+        acc += ((okp ? L[op] : T(0)) - T(2) * Lc + (okm ? L[om] : T(0))) * ih2;
+        const T *Ph = in.f[2 + 2 * a], *Ps = in.f[3 + 2 * a];
+        const T php = okp ? Ph[op] : T(0), phm = okm ? Ph[om] : T(0);
+        const T psp = okp ? Ps[op] : T(0), psm = okm ? Ps[om] : T(0);
+        T oph, ops;
+        if (!ADJ) {
+            const T *U = in.f[0];
+            const T dU = ((okp ? U[op] : T(0)) - (okm ? U[om] : T(0))) * i2h;
+            acc += (si * psp - sm * phm) * ih;
+            oph = si != T(0) ? -T(0.5) * (sm * phm + si * Ph[o]) - dU : T(0);
+            ops = sm != T(0) ? -T(0.5) * (sm * Ps[o] + si * psp) - dU : T(0);
+        } else {
+            const T *Vb = in.f[1];
+            acc += ((php - phm) + (psp - psm)) * i2h;
+            oph = si != T(0) ? -si * (okp ? Vb[op] : T(0)) * ih - T(0.5) * si * (php + Ph[o]) : T(0);
+            ops = sm != T(0) ? sm * (okm ? Vb[om] : T(0)) * ih - T(0.5) * sm * (Ps[o] + psm) : T(0);
         }
+        out.f[2 + 2 * a][o] = alpha * base.f[2 + 2 * a][o] + cop * oph;
+        out.f[3 + 2 * a][o] = alpha * base.f[3 + 2 * a][o] + cop * ops;
+    }
+    if (!ADJ) {
+        out.f[0][o] = alpha * base.f[0][o] + cop * in.f[1][o];
+        out.f[1][o] = alpha * base.f[1][o] + cop * acc;
+    } else {
+        out.f[0][o] = alpha * base.f[0][o] + cop * acc;
+        out.f[1][o] = alpha * base.f[1][o] + cop * in.f[0][o];
     }
 }
 
@@ -226,26 +211,31 @@ cudaError_t launch_stage(int prec, bool adjoint, void *const *in, void *const *b
 {
     if (nseg <= 0) return cudaSuccess;
     const Idx ix = make_idx(g);
-    const int grid = nseg / 8 + 1 < 2048 ? nseg / 8 + 1 : 2048;   // 8 warps per block, a warp per segment
     const int wall = g.wall;
+#define PML_STAGE(TT, AA, DD, IH, IH2, I2H, AL, CO)                                                              \
+    k_stage<TT, AA, DD><<<nseg, kStageChunk, 0, st>>>(fld<TT>(in, nf), fld<TT>(base, nf), fldw<TT>(out, nf), ix, s, \
+                                                      IH, IH2, I2H, AL, CO, seg, wall)
     if (prec == 32) {
-        const float ih = float(1.0 / h), ih2 = float(1.0 / (h * h)), i2h = float(0.5 / h);
-        if (adjoint)
-            k_stage<float, true><<<grid, 256, 0, st>>>(fld<float>(in, nf), fld<float>(base, nf), fldw<float>(out, nf), ix,
-                                                      s, ih, ih2, i2h, float(alpha), float(cop), seg, nseg, wall);
-        else
-            k_stage<float, false><<<grid, 256, 0, st>>>(fld<float>(in, nf), fld<float>(base, nf), fldw<float>(out, nf), ix,
-                                                       s, ih, ih2, i2h, float(alpha), float(cop), seg, nseg, wall);
+        const float ih = float(1.0 / h), ih2 = float(1.0 / (h * h)), i2h = float(0.5 / h), al = float(alpha),
+                    co = float(cop);
+        if (g.ndim == 2) {
+            if (adjoint) PML_STAGE(float, true, 2, ih, ih2, i2h, al, co);
+            else PML_STAGE(float, false, 2, ih, ih2, i2h, al, co);
+        } else {
+            if (adjoint) PML_STAGE(float, true, 3, ih, ih2, i2h, al, co);
+            else PML_STAGE(float, false, 3, ih, ih2, i2h, al, co);
+        }
     } else {
         const double ih = 1.0 / h, ih2 = 1.0 / (h * h), i2h = 0.5 / h;
-        if (adjoint)
-            k_stage<double, true><<<grid, 256, 0, st>>>(fld<double>(in, nf), fld<double>(base, nf), fldw<double>(out, nf),
-                                                       ix, s, ih, ih2, i2h, alpha, cop, seg, nseg, wall);
-        else
-            k_stage<double, false><<<grid, 256, 0, st>>>(fld<double>(in, nf), fld<double>(base, nf),
-                                                        fldw<double>(out, nf), ix, s, ih, ih2, i2h, alpha, cop, seg,
-                                                        nseg, wall);
+        if (g.ndim == 2) {
+            if (adjoint) PML_STAGE(double, true, 2, ih, ih2, i2h, alpha, cop);
+            else PML_STAGE(double, false, 2, ih, ih2, i2h, alpha, cop);
+        } else {
+            if (adjoint) PML_STAGE(double, true, 3, ih, ih2, i2h, alpha, cop);
+            else PML_STAGE(double, false, 3, ih, ih2, i2h, alpha, cop);
+        }
     }
+#undef PML_STAGE
     return cudaGetLastError();
 }
 

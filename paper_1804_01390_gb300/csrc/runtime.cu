@@ -755,11 +755,11 @@ pml_status maybe_check_finite(pml_ctx *c, void *const *state, int64_t before, in
     return PML_OK;
 }
 
-// Row segments {x0, x1, y, z} of C_r: the vertices within r stencil steps of those the
-// damping-gradient contraction reads (along each axis a, the coordinates e and e + 1 of
-// every edge e with sigma_a[e] != 0).  The stencil is a cross, so C_r is the union over
-// the axes of those slabs widened by r along their own axis (periodic distance, or plain
-// distance with walls).
+// Row chunks {x0, x1, y, z} (at most kStageChunkMax vertices) of C_r: the vertices within r
+// stencil steps of those the damping-gradient contraction reads (along each axis a, the
+// coordinates e and e + 1 of every edge e with sigma_a[e] != 0).  The stencil is a cross,
+// so C_r is the union over the axes of those slabs widened by r along their own axis
+// (periodic distance, or plain distance with walls).
 void gradient_segments(const pml_ctx *c, int r, std::vector<int4> *out)
 {
     std::vector<uint8_t> m[3];
@@ -790,18 +790,33 @@ void gradient_segments(const pml_ctx *c, int r, std::vector<int4> *out)
     const int64_t T0 = c->T[0], T1 = c->T[1], T2 = c->nd == 3 ? c->T[2] : 1;
     for (int64_t z = 0; z < T2; ++z)
         for (int64_t y = 0; y < T1; ++y) {
+            auto push = [&](int64_t x0, int64_t x1) {   // chunks of at most kStageChunkMax vertices
+                for (int64_t a0 = x0; a0 <= x1; a0 += kStageChunkMax)
+                    out->push_back(make_int4(int(a0), int(std::min<int64_t>(a0 + kStageChunkMax - 1, x1)), int(y), int(z)));
+            };
             if (m[1][size_t(y)] || (c->nd == 3 && m[2][size_t(z)])) {
-                out->push_back(make_int4(0, int(T0 - 1), int(y), int(z)));
+                push(0, T0 - 1);
                 continue;
             }
             for (int64_t x = 0; x < T0;) {
                 if (!m[0][size_t(x)]) { ++x; continue; }
                 int64_t x1 = x;
                 while (x1 + 1 < T0 && m[0][size_t(x1 + 1)]) ++x1;
-                out->push_back(make_int4(int(x), int(x1), int(y), int(z)));
+                push(x, x1);
                 x = x1 + 1;
             }
         }
+}
+
+// Steps between checkpoints of the damping gradient: `interval`, or ceil(sqrt(n)) for 0.
+int64_t checkpoint_interval(int64_t n, int64_t interval)
+{
+    int64_t K = interval;
+    if (K <= 0) {
+        K = int64_t(std::ceil(std::sqrt(double(n))));
+        while (K * K < n) ++K;
+    }
+    return K > n ? n : K;
 }
 
 pml_status clear_device_error(pml_ctx *c)
@@ -1725,6 +1740,28 @@ pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *g
     return PML_OK;
 }
 
+pml_status pml_sigma_gradient_bytes(const pml_ctx *c, int64_t n, int64_t interval, size_t *bytes)
+{
+    if (!c || !bytes) return fail(nullptr, PML_EINVAL, "NULL argument");
+    if (n < 1) return fail(const_cast<pml_ctx *>(c), PML_EINVAL, "n must be >= 1");
+    const size_t fb = align_up(size_t(c->g.elems) * c->esz, kAlign);
+    const size_t sb = fb * size_t(c->nf);
+    const int64_t K = checkpoint_interval(n, interval);
+    const int64_t nck = (n + K - 1) / K;
+    int64_t tot = 0;
+    for (int a = 0; a < c->nd; ++a) tot += c->T[a];
+    size_t off = sb * size_t(nck) + sb + sb * size_t(K) + sb * 6;
+    off += align_up(size_t(n) * size_t(c->nr > 0 ? c->nr : 1) * c->esz, kAlign);
+    off += align_up(size_t(tot) * sizeof(double), kAlign) + kAlign;
+    for (int r = 0; r < 3; ++r) {
+        std::vector<int4> sg;
+        gradient_segments(c, r, &sg);
+        off += align_up(std::max<size_t>(sg.size(), 1) * sizeof(int4), kAlign);
+    }
+    *bytes = off;
+    return PML_OK;
+}
+
 pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const void *residual, int64_t interval,
                               double *grad_sigma, double *misfit, double *grad_amp)
 {
@@ -1740,12 +1777,7 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
     const int nf = c->nf;
     const size_t fb = align_up(size_t(c->g.elems) * c->esz, kAlign);
     const size_t sb = fb * size_t(nf);   // one state (the fields of one ping-pong half are contiguous)
-    int64_t K = interval;
-    if (K <= 0) {
-        K = int64_t(std::ceil(std::sqrt(double(n))));
-        while (K * K < n) ++K;
-    }
-    if (K > n) K = n;
+    const int64_t K = checkpoint_interval(n, interval);
     const int64_t nck = (n + K - 1) / K;
     int64_t tot = 0;
     for (int a = 0; a < c->nd; ++a) tot += c->T[a];

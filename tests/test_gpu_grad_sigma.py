@@ -131,9 +131,20 @@ def test_2000_steps_with_sqrt_checkpoints(prec):
     only: the checkpoint logic does not depend on the precision, and an FP32 gradient over
     2000 steps carries 2000 steps of FP32 rounding (about 1e-3 relative here), beyond the
     1e-3 asked of the short FP32 runs."""
+    import torch
+    from paper_1804_01390_gb300 import _lib
+    from paper_1804_01390_gb300.solver import PMLSolver
     N, w, steps = (26, 22), 6, 2000
     draws, sig, u0, v0, rec, src, amp, tgt = _case(N, w, steps, seed=13)
     v0 = np.zeros_like(v0)
+    # the scratch the call allocates: 45 checkpoints + 45 segment states + 7 more states
+    s = PMLSolver(N, w, sigma="random", sigma_max=2.0, draws=draws, precision=prec,
+                  device=torch.device("cuda:0"), adjoint=True)
+    s.set_receivers(rec, steps)
+    state = s.state_bytes() - 64
+    nbytes = _lib.pml_sigma_gradient_bytes(s.ctx, steps, 0)
+    s.close()
+    assert (45 + 45 + 7) * state <= nbytes <= 1.05 * (45 + 45 + 7) * state + (1 << 20), (nbytes, state)
     J, grad, gamp, gu = _gpu(N, w, prec, draws, u0, v0, rec, src, amp, tgt, steps, 0)
     Jo, grado, gampo, guo = _oracle(N, w, sig, u0, v0, rec, src, amp, tgt, steps)
     tol = 1e-9 if prec == 64 else 1e-3
