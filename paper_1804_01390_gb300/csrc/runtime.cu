@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -740,6 +741,13 @@ void prof_end(pml_ctx *c, long i)
     if (i >= 0) cudaEventRecord(c->prof_ev[2 * size_t(i) + 1], c->st);
 }
 
+// NVTX range over one library call (header-only NVTX: without an attached tool the push
+// and pop cost a branch each).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 // Finiteness scan of the given state's U and V when the step counter went from `before`
 // to `after` across a multiple of the scan interval.
 pml_status maybe_check_finite(pml_ctx *c, void *const *state, int64_t before, int64_t after)
@@ -1401,6 +1409,7 @@ pml_status pml_get_time_block(const pml_ctx *c, int *depth)
 
 pml_status pml_autotune(pml_ctx *c, int steps, double *times_ms, int *chosen)
 {
+    const NvtxRange nvtx_range("pml_autotune");
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (steps < 1) return fail(c, PML_EINVAL, "steps must be >= 1");
     const int n1 = one_step_variants(c), n = n1 + two_step_variants(c);
@@ -1579,6 +1588,7 @@ pml_status pml_set_receivers(pml_ctx *c, int nr, const int64_t *coords, void *tr
 
 pml_status pml_step(pml_ctx *c, int64_t n)
 {
+    const NvtxRange nvtx_range("pml_step");
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, PML_EINVAL, "n must be >= 0");
     const PointArgs pa = point_args(c);
@@ -1696,6 +1706,7 @@ pml_status pml_adjoint_reset(pml_ctx *c)
 
 pml_status pml_adjoint_step(pml_ctx *c, int64_t n, const void *residual, void *grad_u, double *grad_amp)
 {
+    const NvtxRange nvtx_range("pml_adjoint_step");
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (!c->adj_ready) return fail(c, PML_ESTATE, "call pml_adjoint_reset first");
     if (n < 0) return fail(c, PML_EINVAL, "n must be >= 0");
@@ -1765,6 +1776,7 @@ pml_status pml_sigma_gradient_bytes(const pml_ctx *c, int64_t n, int64_t interva
 pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const void *residual, int64_t interval,
                               double *grad_sigma, double *misfit, double *grad_amp)
 {
+    const NvtxRange nvtx_range("pml_sigma_gradient");
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     if (!(c->flags & PML_FLAG_ADJOINT)) return fail(c, PML_ESTATE, "context was created without PML_FLAG_ADJOINT");
     if (n < 1) return fail(c, PML_EINVAL, "n must be >= 1");
@@ -1829,13 +1841,15 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
 
     // forward run with a checkpoint every K steps
     const int64_t s0 = c->step, tk0 = c->trace_k;
+    nvtxRangePushA("forward with checkpoints");
     for (int64_t k = 0; k < n; ++k) {
         if (k % K == 0)
             PML_CU(c, cudaMemcpyAsync(mem + o_ck + size_t(k / K) * sb, c->fld[c->cur][0], sb, cudaMemcpyDeviceToDevice,
                                       c->st), "checkpoint");
         pml_status s = pml_step(c, 1);
-        if (s != PML_OK) return s;
+        if (s != PML_OK) { nvtxRangePop(); return s; }
     }
+    nvtxRangePop();
     PML_CU(c, cudaMemcpyAsync(mem + o_end, c->fld[c->cur][0], sb, cudaMemcpyDeviceToDevice, c->st), "final state");
     if (c->nr > 0 && target)
         PML_CU(c, launch_residual(c->prec, static_cast<const char *>(c->trace) + size_t(tk0) * size_t(c->nr) * c->esz,
@@ -1852,6 +1866,7 @@ pml_status pml_sigma_gradient(pml_ctx *c, int64_t n, const void *target, const v
     const int nr_saved = c->nr;
     const double dt = c->dt;
     for (int64_t seg = nck - 1; seg >= 0; --seg) {
+        const NvtxRange seg_range("segment: recompute, adjoint, contraction");
         const int64_t sa = seg * K, se = std::min<int64_t>(n, sa + K);
         PML_CU(c, cudaMemcpyAsync(c->fld[c->cur][0], mem + o_ck + size_t(seg) * sb, sb, cudaMemcpyDeviceToDevice,
                                   c->st), "restore checkpoint");
@@ -2355,6 +2370,7 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
 
 pml_status pml_batch_step(pml_batch *b, int64_t n)
 {
+    const NvtxRange nvtx_range("pml_batch_step");
     if (!b) return bfail(PML_EINVAL, "pml_batch_step: batch is NULL");
     if (n < 0) return bfail(PML_EINVAL, "pml_batch_step: n must be >= 0");
     const int p0 = b->ctx[0]->cur;
