@@ -450,7 +450,11 @@ def run_ours(args, ws, rank, local):
         wl3 = wk.cfg3() if args.n3 is None else wk.cfg3(N=args.n3)
         K3 = max(K // 20, 10)
         s = PMLSolver(wl3.N, wl3.w, dt=wl3.dt, precision=32, device=dev)
-        var3, tune3 = autotune.tune(s, steps=5, use_cache=not args.retune)   # tile kernel or level passes
+        if args.variant3 is None:   # frame kernel: tile kernel, level passes or slab tiles
+            var3, tune3 = autotune.tune(s, steps=5, use_cache=not args.retune)
+        else:                       # a fixed frame kernel (profiling): no tuning launches
+            var3, tune3 = args.variant3, None
+            autotune.select(s.ctx, var3)
         u3 = torch.from_numpy(wk.initial_field(wl3, dtype=np.float32)).to(dev)
         s.set_initial(u3)
         src = wl3.sources
@@ -466,7 +470,7 @@ def run_ours(args, ws, rank, local):
         d3 = {"workload": "3D %d^3 interior + %d-cell quadratic PML (T = %d^3), Gaussian s=6 + 8 Ricker sources, FP32"
                           % (wl3.N[0], wl3.w, wl3.T[0]),
               "value": pts3 * K3 * ws / (ms3 / 1e3) / 1e9, "unit": UNIT, "steps": K3, "ms_per_step": ms3 / K3,
-              "layer_variant": {0: "z-streaming tile kernel", 1: "level passes"}.get(var3, var3),
+              "layer_variant": {0: "z-streaming tile kernel", 1: "level passes", 2: "slab tiles"}.get(var3, var3),
               "autotune_ms_per_step": tune3,
               "roofline": {"bound": "hbm", "kernel": "k_interior3d<float>", "achieved": ach3, "peak": hbm_peak,
                            "unit": "GB/s", "frac": ach3 / hbm_peak, "avg_launch_ms": t_int3 * 1e3,
@@ -774,6 +778,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--n3", type=int, default=None, help="3D physical side (default 512)")
+    ap.add_argument("--variant3", type=int, default=None,
+                    help="use this 3D frame kernel (0 tile kernel, 1 level passes, 2 slab tiles) instead of "
+                         "the autotuned one (profiling)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--no-grad-sigma", action="store_true")
