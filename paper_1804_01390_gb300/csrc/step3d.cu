@@ -183,8 +183,16 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
         const bool out_lane = lane >= 1 && lane <= 30;
         const bool full_vec =
             out_lane && x0 >= a.xr.lo && x0 + NC - 1 <= a.xr.hi && x0 >= G && x0 + NC - 1 < g.T[0] - G;
+        // the lane's columns and row lie more than G from every box edge: no ghost images
+        const bool row_inner = x0 >= G && x0 + NC - 1 < g.T[0] - G && y >= G && y < g.T[1] - G;
         const bool d_row = k >= 1 && k <= kBY3 + 2;
         const bool o_row = k >= 2 && k <= kBY3 + 1 && y <= a.yr.hi;
+        // the thread's offsets in a stage plane (rows k, k - 1, k + 1) and in a difference plane
+        // (rows k - 1, k - 2, k), and its output offset without the plane term
+        const int lo = NC * lane;
+        const int o_c = k * ROW + lo, o_m = (k - 1) * ROW + lo, o_p = (k + 1) * ROW + lo;
+        const int d_c = (k - 1) * ROW + lo, d_m = (k - 2) * ROW + lo, d_p = k * ROW + lo;
+        const int64_t obase = g.origin + y * g.P + x0;
         VT u[3], v[3], du[3], dv[3];
         bool ok = true;
         int pfail = n_in;   // first plane whose wait gave up
@@ -201,20 +209,18 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
                     } else {
                         const T *sU = reinterpret_cast<const T *>(smem + st * C::STAGE);
                         const T *sV = sU + NW * ROW;
-                        u[PH] = ldsN<T, NC>(sU + k * ROW + NC * lane);
-                        v[PH] = ldsN<T, NC>(sV + k * ROW + NC * lane);
+                        u[PH] = ldsN<T, NC>(sU + o_c);
+                        v[PH] = ldsN<T, NC>(sV + o_c);
                         const int J1 = (PH + 2) % 3, J2 = (PH + 1) % 3;   // planes p-1, p-2
                         if (p >= 2 && d_row) {
                             const int sp = (use + p - 1) % S;
                             const T *pU = reinterpret_cast<const T *>(smem + sp * C::STAGE);
                             const T *pV = pU + NW * ROW;
-                            du[J1] = diff7(u[J1], ldsN<T, NC>(pU + (k - 1) * ROW + NC * lane),
-                                           ldsN<T, NC>(pU + (k + 1) * ROW + NC * lane), u[J2], u[PH]);
-                            dv[J1] = diff7(v[J1], ldsN<T, NC>(pV + (k - 1) * ROW + NC * lane),
-                                           ldsN<T, NC>(pV + (k + 1) * ROW + NC * lane), v[J2], v[PH]);
-                            T *db = dbuf + size_t((p - 1) % 3) * 2 * DR * ROW;
-                            stN(db + (k - 1) * ROW + NC * lane, du[J1]);
-                            stN(db + DR * ROW + (k - 1) * ROW + NC * lane, dv[J1]);
+                            du[J1] = diff7(u[J1], ldsN<T, NC>(pU + o_m), ldsN<T, NC>(pU + o_p), u[J2], u[PH]);
+                            dv[J1] = diff7(v[J1], ldsN<T, NC>(pV + o_m), ldsN<T, NC>(pV + o_p), v[J2], v[PH]);
+                            T *db = dbuf + ((PH + 2) % 3) * 2 * DR * ROW;   // plane p - 1 (p0 is a multiple of 3)
+                            stN(db + d_c, du[J1]);
+                            stN(db + DR * ROW + d_c, dv[J1]);
                         }
                     }
                 }
@@ -231,11 +237,10 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
                     }
                     if (p >= 4 && o_row) {
                         const int J1 = (PH + 2) % 3, J2 = (PH + 1) % 3;
-                        const T *db = dbuf + size_t((p - 2) % 3) * 2 * DR * ROW;
-                        const VT d2u = diff7(du[J2], ldsN<T, NC>(db + (k - 2) * ROW + NC * lane),
-                                             ldsN<T, NC>(db + k * ROW + NC * lane), du[PH], du[J1]);
-                        const VT d2v = diff7(dv[J2], ldsN<T, NC>(db + DR * ROW + (k - 2) * ROW + NC * lane),
-                                             ldsN<T, NC>(db + DR * ROW + k * ROW + NC * lane), dv[PH], dv[J1]);
+                        const T *db = dbuf + ((PH + 1) % 3) * 2 * DR * ROW;   // plane p - 2
+                        const VT d2u = diff7(du[J2], ldsN<T, NC>(db + d_m), ldsN<T, NC>(db + d_p), du[PH], du[J1]);
+                        const VT d2v = diff7(dv[J2], ldsN<T, NC>(db + DR * ROW + d_m), ldsN<T, NC>(db + DR * ROW + d_p),
+                                             dv[PH], dv[J1]);
                         const VT &uc = u[J2], &vc = v[J2], &duc = du[J2], &dvc = dv[J2];
                         VT uo, vo;
                         if constexpr (sizeof(T) == 4 && NC == 2) {   // packed FP32x2
@@ -265,10 +270,18 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
                             }
                         }
                         const int64_t z = z0 + p - 4;
-                        if (full_vec && y >= G && y < g.T[1] - G && z >= G && z < g.T[2] - G) {
-                            const int64_t off = g.origin + z * g.PS + y * g.P + x0;
+                        const bool inner = row_inner && z >= G && z < g.T[2] - G;
+                        const int64_t off = obase + z * g.PS;
+                        if (full_vec && inner) {
                             stN(Uo + off, uo);
                             stN(Vo + off, vo);
+                        } else if (out_lane && inner) {   // a strip's end: plain stores of its columns in the run
+#pragma unroll
+                            for (int q = 0; q < NC; ++q)
+                                if (x0 + q >= a.xr.lo && x0 + q <= a.xr.hi) {
+                                    Uo[off + q] = uo.c[q];
+                                    Vo[off + q] = vo.c[q];
+                                }
                         } else if (out_lane) {
 #pragma unroll
                             for (int q = 0; q < NC; ++q) {
