@@ -400,12 +400,13 @@ struct Interior3DArgs {
     uint64_t wait_ns;          // limit of every bounded wait (0: the default 2 s)
     int *queue;                // work counters (this launch: queue[parity])
     int parity;
+    float2 pf[11];             // FP32 kernel: a1..a5, b1..b5, -6 as pairs (set by the launcher)
 };
 cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, const CUtensorMap *tmV,
                               void *Uo, void *Vo, const Interior3DArgs &a, int grid, bool overlap_previous,
                               cudaStream_t st);
 int interior3d_box_rows(int prec);
-int interior3d_tile_y();
+int interior3d_tile_y(int prec);   // output rows of a CTA tile
 int interior3d_box_cols(int prec);   // box width of the 3D interior kernel (one strip plus halo)
 int interior3d_max_blocks_per_sm(int prec, bool adjoint);
 

@@ -1317,7 +1317,7 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
             box_lay[0] = uint32_t(layer2d_box_cols(precision)); box_lay[1] = uint32_t(layer2d_box_rows());
             box_lay[2] = 1;   // one warp's strip
         } else {
-            box_int[0] = uint32_t(interior3d_box_cols(precision)); box_int[1] = uint32_t(interior3d_tile_y() + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
+            box_int[0] = uint32_t(interior3d_box_cols(precision)); box_int[1] = uint32_t(interior3d_tile_y(precision) + 4); box_int[2] = uint32_t(interior3d_box_rows(precision));
             box_lay[0] = uint32_t(layer3d_tile_x(precision) + 8); box_lay[1] = uint32_t(layer3d_tile_y(precision) + 8);
             box_lay[2] = 1;
         }

@@ -3,7 +3,9 @@
 // layer-free region, Horner form with the full operator in the layer frame), with the
 // 7-point difference and streaming along z.
 //
-//  * k_interior3d: a CTA owns a 30 NC-column x strip by kBY3 output rows and streams z.
+//  * k_interior3d_rows (FP32, interior3d_rows.cuh): several rows per warp, see there.
+//
+//  * k_interior3d (FP64): a CTA owns a 30 NC-column x strip by kBY3 output rows and streams z.
 //    One warp per region row (kBY3 + 4 rows: halo 2 in y); TMA brings one z-plane box of
 //    U and V per stage; each lane keeps three planes of U, V, DU, DV in registers (z
 //    neighbours; NC = 2 columns per lane, so two CTAs fit on an SM), y neighbours come
@@ -31,7 +33,7 @@ template <typename T> struct I3Cfg {
 };
 
 int interior3d_box_rows(int) { return 1; }
-int interior3d_tile_y() { return kBY3; }
+int interior3d_tile_y(int prec);   // defined after the FP32 kernel's shape
 int interior3d_box_cols(int prec) { return 32 * (prec == 32 ? I3Cfg<float>::NC : I3Cfg<double>::NC); }
 
 // NC adjacent columns of one lane
@@ -309,6 +311,34 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
     wait_prerequisite_grid();
 }
 
+}  // namespace pml
+
+#include "interior3d_rows.cuh"
+
+namespace pml {
+
+int interior3d_tile_y(int prec) { return prec == 32 ? I3Rf::TY : kBY3; }
+
+template <bool ADJ> static cudaError_t prep_interior3d_rows()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_interior3d_rows<ADJ, kI3R, kI3W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(I3Rf::SMEM));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <bool ADJ> static int occ_interior3d_rows()
+{
+    if (prep_interior3d_rows<ADJ>() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interior3d_rows<ADJ, kI3R, kI3W>, 32 * kI3W, I3Rf::SMEM) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
 template <typename T, bool ADJ> static cudaError_t prep_interior3d()
 {
     static bool done = false;
@@ -331,7 +361,7 @@ template <typename T, bool ADJ> static int occ_interior3d()
 
 int interior3d_max_blocks_per_sm(int prec, bool adjoint)
 {
-    if (prec == 32) return adjoint ? occ_interior3d<float, true>() : occ_interior3d<float, false>();
+    if (prec == 32) return adjoint ? occ_interior3d_rows<true>() : occ_interior3d_rows<false>();
     return adjoint ? occ_interior3d<double, true>() : occ_interior3d<double, false>();
 }
 
@@ -347,7 +377,18 @@ cudaError_t launch_interior3d(int prec, bool adjoint, const CUtensorMap *tmU, co
     return launch_pdl(k_interior3d<TT, AA>, grid, threads, I3<TT>::SMEM, st, overlap_previous, *tmU, *tmV, \
                       (TT *)Uo, (TT *)Vo, a);
     if (prec == 32) {
-        if (adjoint) { PML_LAUNCH(float, true) } else { PML_LAUNCH(float, false) }
+        Interior3DArgs b = a;
+        const StepCoefT<float> &k = a.c.f;
+        const float cf[11] = {k.a1, k.a2, k.a3, k.a4, k.a5, k.b1, k.b2, k.b3, k.b4, k.b5, -6.f};
+        for (int i = 0; i < 11; ++i) b.pf[i] = make_float2(cf[i], cf[i]);
+        if (adjoint) {
+            if ((e = prep_interior3d_rows<true>()) != cudaSuccess) return e;
+            return launch_pdl(k_interior3d_rows<true, kI3R, kI3W>, grid, 32 * kI3W, I3Rf::SMEM, st, overlap_previous,
+                              *tmU, *tmV, (float *)Uo, (float *)Vo, b);
+        }
+        if ((e = prep_interior3d_rows<false>()) != cudaSuccess) return e;
+        return launch_pdl(k_interior3d_rows<false, kI3R, kI3W>, grid, 32 * kI3W, I3Rf::SMEM, st, overlap_previous,
+                          *tmU, *tmV, (float *)Uo, (float *)Vo, b);
     } else {
         if (adjoint) { PML_LAUNCH(double, true) } else { PML_LAUNCH(double, false) }
     }
