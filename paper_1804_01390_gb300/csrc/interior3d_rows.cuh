@@ -133,6 +133,13 @@ __global__ void __launch_bounds__(32 * NWP, 2)
             if (col_inner && y >= G && y < g.T[1] - G) imask |= 1u << j;
         }
         const int64_t obase = g.origin + (y0 - 2 + b0) * g.P + x0;
+        // every own row and both columns of the lane stored by one vector store, no images
+        const bool lane_fast = full_vec && imask == (1u << R) - 1u;
+        // input planes whose output plane (z = z0 + p - 4) lies more than G from the z box edges
+        const int pin_lo = int(G - z0 + 4), pin_hi = int(g.T[2] - G - z0 + 4);
+        // the lane's output pointers at input plane p = 0 (z = z0 - 4), advanced by one plane
+        // per iteration
+        float *ou = Uo + (obase + (z0 - 4) * g.PS), *ov = Vo + (obase + (z0 - 4) * g.PS);
         float2 U[3][R], V[3][R], DU[3][R], DV[3][R];
         bool ok = true;
         int pfail = n_in;   // first plane whose wait gave up
@@ -192,9 +199,8 @@ __global__ void __launch_bounds__(32 * NWP, 2)
                         const float *db = dbuf + s2 * (2 * FS) + o_own;   // slot of plane p - 2
                         const float2 gum = ld2(db - ROW), gup = ld2(db + R * ROW);
                         const float2 gvm = ld2(db + FS - ROW), gvp = ld2(db + FS + R * ROW);
-                        const int64_t z = z0 + p - 4;
-                        const bool zin = z >= G && z < g.T[2] - G;
-                        const int64_t offz = obase + z * g.PS;
+                        const bool zin = p >= pin_lo && p < pin_hi;
+                        const bool fast = lane_fast && zin;
 #pragma unroll
                         for (int j = 0; j < R; ++j) {
                             if (!(omask >> j & 1u)) continue;
@@ -212,22 +218,27 @@ __global__ void __launch_bounds__(32 * NWP, 2)
                                 tv = __ffma2_rn(cp[5], uc, __ffma2_rn(cp[6], duc, __ffma2_rn(cp[7], dvc, __fmul2_rn(cp[9], d2v))));
                             }
                             const float2 uo = __fadd2_rn(uc, tu), vo = __fadd2_rn(vc, tv);
-                            const int64_t off = offz + int64_t(j) * g.P;
+                            float *pu = ou + int64_t(j) * g.P, *pv = ov + int64_t(j) * g.P;
+                            if (fast) {
+                                st2(pu, uo);
+                                st2(pv, vo);
+                                continue;
+                            }
                             const bool inner = zin && (imask >> j & 1u);
                             if (full_vec && inner) {
-                                st2(Uo + off, uo);
-                                st2(Vo + off, vo);
+                                st2(pu, uo);
+                                st2(pv, vo);
                             } else if (out_lane && inner) {   // a strip's end: plain stores of its columns in the run
                                 if (x0 >= a.xr.lo && x0 <= a.xr.hi) {
-                                    Uo[off] = uo.x;
-                                    Vo[off] = vo.x;
+                                    pu[0] = uo.x;
+                                    pv[0] = vo.x;
                                 }
                                 if (x0 + 1 >= a.xr.lo && x0 + 1 <= a.xr.hi) {
-                                    Uo[off + 1] = uo.y;
-                                    Vo[off + 1] = vo.y;
+                                    pu[1] = uo.y;
+                                    pv[1] = vo.y;
                                 }
                             } else if (out_lane) {
-                                const int64_t y = y0 - 2 + b0 + j;
+                                const int64_t y = y0 - 2 + b0 + j, z = z0 + p - 4;
                                 if (x0 >= a.xr.lo && x0 <= a.xr.hi) {
                                     store_wrapped(Uo, g, x0, y, z, uo.x);
                                     store_wrapped(Vo, g, x0, y, z, vo.x);
@@ -240,6 +251,8 @@ __global__ void __launch_bounds__(32 * NWP, 2)
                         }
                     }
                 }
+                ou += g.PS;
+                ov += g.PS;
             }
         }
         __syncthreads();
