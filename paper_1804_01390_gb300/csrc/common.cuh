@@ -99,6 +99,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// The dynamic shared memory `base` rounded up to a 128-byte boundary (TMA destinations).  The
+// result is an offset from `base`, not a round trip through an integer, so the compiler still
+// knows that accesses through it are shared-memory accesses (32-bit addresses).
+template <typename T> __device__ __forceinline__ T *smem_align128(unsigned char *base)
+{
+    return reinterpret_cast<T *>(base + ((128u - (smem_u32(base) & 127u)) & 127u));
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(32 * NWP, 2)
     __shared__ __align__(8) uint64_t bars[S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+        smem_align128<unsigned char>(smem_dyn);
     float *dbuf = reinterpret_cast<float *>(smem + S * C::STAGE);   // [3][2][BY][ROW]
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;

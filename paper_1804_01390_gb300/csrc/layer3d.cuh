@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(L3<T>::PL, 1)
     using F = Fields<MASK>;
     constexpr int NF = F::NF, RX = L3<T>::RX, RY = L3<T>::RY, PL = L3<T>::PL, PLS = L3<T>::PLS, S = L3<T>::stages(F::NF);
     extern __shared__ unsigned char smem_dyn[];
-    T *stage = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *stage = smem_align128<T>(smem_dyn);
     T *Zb = stage + S * NF * PLS;   // [3 levels][2 slots][NF][PLS]
     __shared__ T sx[RX + 1], sy[RY + 1], sz[kLayer3LZ + 9];
     __shared__ __align__(8) uint64_t bars[S];

@@ -173,7 +173,7 @@ __global__ void __maxnreg__(Slab<MASK>::MAXREG)
     constexpr int NF = SH::NF, RX = SH::RX, RY = SH::RY, TPR = SH::TPR, NT = SH::NT, PLS = SH::PLS, S = SH::S;
     constexpr int FPL = NF * PLS;   // one plane of all fields
     extern __shared__ unsigned char smem_dyn[];
-    float *stage = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    float *stage = smem_align128<float>(smem_dyn);
     float *lvl = stage + S * FPL;   // [3 levels: 4, 3, 2][2 plane parities][NF][PLS]
     __shared__ float sz[kSlabMaxZ + 10], mz[kSlabMaxZ + 10];
     __shared__ __align__(8) uint64_t bars[S];

@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(32 * BY, MINB)
     __shared__ __align__(8) uint64_t bars[NCH];
     __shared__ int item_sh;
     extern __shared__ unsigned char smem_dyn[];
-    T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *ring = smem_align128<T>(smem_dyn);
     T *const ringU = ring, *const ringV = ring + RR * ROW, *const ringDU = ring + 2 * RR * ROW,
           *const ringDV = ring + (2 * RR + RD) * ROW;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -1121,7 +1121,7 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB)
     __shared__ __align__(8) uint64_t bars[4][S];
     __shared__ T sig_sh[4][2 * kL2SigRows];
     extern __shared__ unsigned char smem_dyn[];
-    T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *smem = smem_align128<T>(smem_dyn);
     allow_dependent_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -1217,7 +1217,7 @@ __global__ void __launch_bounds__(128, MINB)
     __shared__ __align__(8) uint64_t bars[4][S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+        smem_align128<unsigned char>(smem_dyn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wbase = smem + warp * WB;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.queue[1 - a.parity] = 0;
@@ -1377,7 +1377,7 @@ __global__ void __launch_bounds__(128, MINB)
     __shared__ __align__(8) uint64_t bars[4][S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+        smem_align128<unsigned char>(smem_dyn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wbase = smem + warp * WB;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.queue[1 - a.parity] = 0;
@@ -1534,7 +1534,7 @@ __global__ void __launch_bounds__(128, MINB) k_interior2d_batch(const Batch2DArg
     __shared__ __align__(8) uint64_t bars[4][S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+        smem_align128<unsigned char>(smem_dyn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wbase = smem + warp * WB;
     if (blockIdx.x == 0 && threadIdx.x == 0) b.queue[1 - b.parity] = 0;
@@ -1578,7 +1578,7 @@ __global__ void __launch_bounds__(128, L2Cfg<T>::MINB) k_layer2d_batch(const Bat
     __shared__ __align__(8) uint64_t bars[4][S];
     __shared__ T sig_sh[4][2 * kL2SigRows];
     extern __shared__ unsigned char smem_dyn[];
-    T *smem = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    T *smem = smem_align128<T>(smem_dyn);
     allow_dependent_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -1716,7 +1716,7 @@ __global__ void __launch_bounds__(128, MINB) k_interior2d_tb2_batch(const Batch2
     __shared__ __align__(8) uint64_t bars[4][S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+        smem_align128<unsigned char>(smem_dyn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wbase = smem + warp * WB;
     if (blockIdx.x == 0 && threadIdx.x == 0) b.queue[1 - b.parity] = 0;

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(32 * (kBY3 + 4), I3Cfg<T>::MINB)
     __shared__ __align__(8) uint64_t bars[S];
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+        smem_align128<unsigned char>(smem_dyn);
     T *dbuf = reinterpret_cast<T *>(smem + S * C::STAGE);   // [3][2][DR][ROW]
 
     const int tid = threadIdx.x, k = tid >> 5, lane = tid & 31;
