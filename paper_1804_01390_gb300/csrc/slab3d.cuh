@@ -24,6 +24,8 @@
 #ifndef PML_SLAB3D_CUH_
 #define PML_SLAB3D_CUH_
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "layer3d.cuh"
 
@@ -277,163 +279,185 @@ __global__ void __maxnreg__(Slab<MASK>::MAXREG)
 
     bool ok = true;
     int pfail = nin;   // first plane whose wait gave up
-    for (int p0 = 0; p0 < nin && ok; p0 += 3) {
+    // One iteration per input plane p.  Every shared-memory read of an iteration sees planes
+    // written in earlier iterations (the level planes alternate by plane parity), so in the
+    // one-axis classes the stores of levels 4, 3 and 2 are made after all four levels are
+    // formed: the loads of a later level then need not wait behind the stores of an earlier
+    // one, and their STEADY iterations (p >= 8: every level has its planes) run as one block
+    // without the start-up guards.  The multi-axis classes keep one guarded body that
+    // stores each level at once (a second body, or values held to the end, spill there).
+    // Level planes: [3 levels: 4, 3, 2][2 plane parities][NF][PLS].
+    auto store_level = [&](int lv, int q, const float2 *v) {
+        float *zo = lvl + ((lv * 2 + (q & 1)) * NF) * PLS;
 #pragma unroll
-        for (int PH = 0; PH < 3; ++PH) {
-            const int p = p0 + PH;
-            const int sp = p % S;   // slot of input plane p; plane p - k sits in slot (sp - k) mod S
-            auto slot = [&](int k) { return sp - k < 0 ? sp - k + S : sp - k; };
-            if (p < nin) {
-                if (!mbar_wait(&bars[sp], (p / S) & 1, a.err, 7, a.wait_ns)) ok = false;
-                if (ok) {
-                    // level 4 at plane q = p-1 from the input planes (stage slots)
-                    if (p >= 2) {
-                        const int q = p - 1;
-                        const float *Pc = stage + slot(1) * FPL, *Pm = stage + slot(2) * FPL, *Pp = stage + sp * FPL;
-                        float2 cen[NF];
+        for (int f = 0; f < NF; ++f) P::st(zo + f * PLS + e, v[f]);
+    };
+    auto iter = [&](const int p, auto phc, auto stc) -> bool {
+        constexpr int PH = decltype(phc)::value;   // p mod 3: position in the register rings
+        constexpr bool STEADY = decltype(stc)::value;
+        constexpr bool DEFER = SH::NAX <= 1;        // multi-axis classes store each level at once
+        const int sp = p % S;   // slot of input plane p; plane p - k sits in slot (sp - k) mod S
+        auto slot = [&](int k) { return sp - k < 0 ? sp - k + S : sp - k; };
+        if (p < nin) {
+            if (!mbar_wait(&bars[sp], (p / S) & 1, a.err, 7, a.wait_ns)) ok = false;
+            if (ok) {
+                // level 4 at plane q = p-1 from the input planes (stage slots)
+                if (STEADY || p >= 2) {
+                    const int q = p - 1;
+                    const float *Pc = stage + slot(1) * FPL, *Pm = stage + slot(2) * FPL, *Pp = stage + sp * FPL;
+                    float2 cen[NF];
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) cen[f] = P::ld(Pc + f * PLS + e);
-                        auto N = [&](int f, int d) -> float2 {
-                            switch (d) {
-                            case 0: return cen[f];
-                            case 1: return xm(Pc, f, cen[f]);
-                            case 2: return xp(Pc, f, cen[f]);
-                            case 3: return ym(Pc, f);
-                            case 4: return yp(Pc, f);
-                            case 5: return P::ld(Pm + f * PLS + e);
-                            default: return P::ld(Pp + f * PLS + e);
-                            }
-                        };
-                        float2 rr[NF];
-                        slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
-                        float *zb = lvl + ((0 * 2 + (q & 1)) * NF) * PLS;
-#pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            const float2 v = keep(P::fma(c4, rr[f], cen[f]), q);
-                            z4r[(PH + 2) % 3][f] = v;
-                            P::st(zb + f * PLS + e, v);
+                    for (int f = 0; f < NF; ++f) cen[f] = P::ld(Pc + f * PLS + e);
+                    auto N = [&](int f, int d) -> float2 {
+                        switch (d) {
+                        case 0: return cen[f];
+                        case 1: return xm(Pc, f, cen[f]);
+                        case 2: return xp(Pc, f, cen[f]);
+                        case 3: return ym(Pc, f);
+                        case 4: return yp(Pc, f);
+                        case 5: return P::ld(Pm + f * PLS + e);
+                        default: return P::ld(Pp + f * PLS + e);
                         }
-                    }
-                    // level 3 at plane q = p-2 (z neighbours: own ring; x, y: level-4 plane)
-                    if (p >= 4) {
-                        const int q = p - 2;
-                        const float *zb = lvl + ((0 * 2 + (q & 1)) * NF) * PLS;
-                        auto N = [&](int f, int d) -> float2 {
-                            switch (d) {
-                            case 0: return z4r[(PH + 1) % 3][f];
-                            case 1: return xm(zb, f, z4r[(PH + 1) % 3][f]);
-                            case 2: return xp(zb, f, z4r[(PH + 1) % 3][f]);
-                            case 3: return ym(zb, f);
-                            case 4: return yp(zb, f);
-                            case 5: return z4r[PH][f];
-                            default: return z4r[(PH + 2) % 3][f];
-                            }
-                        };
-                        float2 rr[NF];
-                        slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
-                        const float *Y = stage + slot(2) * FPL;
-                        float *zo = lvl + ((1 * 2 + (q & 1)) * NF) * PLS;
+                    };
+                    float2 rr[NF];
+                    slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            const float2 v = keep(P::fma(c3, rr[f], P::ld(Y + f * PLS + e)), q);
-                            z3r[(PH + 1) % 3][f] = v;
-                            P::st(zo + f * PLS + e, v);
+                    for (int f = 0; f < NF; ++f) z4r[(PH + 2) % 3][f] = keep(P::fma(c4, rr[f], cen[f]), q);
+                    if (!DEFER) store_level(0, q, z4r[(PH + 2) % 3]);
+                }
+                // level 3 at plane q = p-2 (z neighbours: own ring; x, y: level-4 plane)
+                if (STEADY || p >= 4) {
+                    const int q = p - 2;
+                    const float *zb = lvl + ((0 * 2 + (q & 1)) * NF) * PLS;
+                    auto N = [&](int f, int d) -> float2 {
+                        switch (d) {
+                        case 0: return z4r[(PH + 1) % 3][f];
+                        case 1: return xm(zb, f, z4r[(PH + 1) % 3][f]);
+                        case 2: return xp(zb, f, z4r[(PH + 1) % 3][f]);
+                        case 3: return ym(zb, f);
+                        case 4: return yp(zb, f);
+                        case 5: return z4r[PH][f];
+                        default: return z4r[(PH + 2) % 3][f];
                         }
-                    }
-                    // level 2 at plane q = p-3
-                    if (p >= 6) {
-                        const int q = p - 3;
-                        const float *zb = lvl + ((1 * 2 + (q & 1)) * NF) * PLS;
-                        auto N = [&](int f, int d) -> float2 {
-                            switch (d) {
-                            case 0: return z3r[PH][f];
-                            case 1: return xm(zb, f, z3r[PH][f]);
-                            case 2: return xp(zb, f, z3r[PH][f]);
-                            case 3: return ym(zb, f);
-                            case 4: return yp(zb, f);
-                            case 5: return z3r[(PH + 2) % 3][f];
-                            default: return z3r[(PH + 1) % 3][f];
-                            }
-                        };
-                        float2 rr[NF];
-                        slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
-                        const float *Y = stage + slot(3) * FPL;
-                        float *zo = lvl + ((2 * 2 + (q & 1)) * NF) * PLS;
+                    };
+                    float2 rr[NF];
+                    slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
+                    const float *Y = stage + slot(2) * FPL;
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            const float2 v = keep(P::fma(c2, rr[f], P::ld(Y + f * PLS + e)), q);
-                            z2r[PH][f] = v;
-                            P::st(zo + f * PLS + e, v);
+                    for (int f = 0; f < NF; ++f)
+                        z3r[(PH + 1) % 3][f] = keep(P::fma(c3, rr[f], P::ld(Y + f * PLS + e)), q);
+                    if (!DEFER) store_level(1, q, z3r[(PH + 1) % 3]);
+                }
+                // level 2 at plane q = p-3
+                if (STEADY || p >= 6) {
+                    const int q = p - 3;
+                    const float *zb = lvl + ((1 * 2 + (q & 1)) * NF) * PLS;
+                    auto N = [&](int f, int d) -> float2 {
+                        switch (d) {
+                        case 0: return z3r[PH][f];
+                        case 1: return xm(zb, f, z3r[PH][f]);
+                        case 2: return xp(zb, f, z3r[PH][f]);
+                        case 3: return ym(zb, f);
+                        case 4: return yp(zb, f);
+                        case 5: return z3r[(PH + 2) % 3][f];
+                        default: return z3r[(PH + 1) % 3][f];
                         }
-                    }
-                    // level 1 (the output) at plane q = p-4
-                    if (p >= 8 && (ox0 || ox1)) {
-                        const int q = p - 4;
-                        const float *zb = lvl + ((2 * 2 + (q & 1)) * NF) * PLS;
-                        auto N = [&](int f, int d) -> float2 {
-                            switch (d) {
-                            case 0: return z2r[(PH + 2) % 3][f];
-                            case 1: return xm(zb, f, z2r[(PH + 2) % 3][f]);
-                            case 2: return xp(zb, f, z2r[(PH + 2) % 3][f]);
-                            case 3: return ym(zb, f);
-                            case 4: return yp(zb, f);
-                            case 5: return z2r[(PH + 1) % 3][f];
-                            default: return z2r[PH][f];
-                            }
-                        };
-                        float2 rr[NF];
-                        slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
-                        const float *Y = stage + slot(4) * FPL;
-                        int64_t z = zin0 + q;
-                        z += z < 0 ? g.T[2] : (z >= g.T[2] ? -g.T[2] : 0);
-                        const int64_t off = off_xy + z * g.PS, dz = img(z, 2) * g.PS;
+                    };
+                    float2 rr[NF];
+                    slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
+                    const float *Y = stage + slot(3) * FPL;
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            const float2 v = P::fma(c1, rr[f], P::ld(Y + f * PLS + e));
-                            float *b = static_cast<float *>(out.p[slab_gid<MASK>(f)]) + off;
-                            auto put = [&](float *q2) {
-                                if (ox0 && ox1) P::st(q2, v);
-                                else if (ox0) q2[0] = v.x;
-                                else q2[1] = v.y;
-                            };
-                            put(b);
-                            if (dy) put(b + dy);
+                    for (int f = 0; f < NF; ++f) z2r[PH][f] = keep(P::fma(c2, rr[f], P::ld(Y + f * PLS + e)), q);
+                    if (!DEFER) store_level(2, q, z2r[PH]);
+                }
+                // level 1 (the output) at plane q = p-4
+                if ((STEADY || p >= 8) && (ox0 || ox1)) {
+                    const int q = p - 4;
+                    const float *zb = lvl + ((2 * 2 + (q & 1)) * NF) * PLS;
+                    auto N = [&](int f, int d) -> float2 {
+                        switch (d) {
+                        case 0: return z2r[(PH + 2) % 3][f];
+                        case 1: return xm(zb, f, z2r[(PH + 2) % 3][f]);
+                        case 2: return xp(zb, f, z2r[(PH + 2) % 3][f]);
+                        case 3: return ym(zb, f);
+                        case 4: return yp(zb, f);
+                        case 5: return z2r[(PH + 1) % 3][f];
+                        default: return z2r[PH][f];
+                        }
+                    };
+                    float2 rr[NF];
+                    slab_apply<ADJ, MASK>(N, zsig(q), ih, ih2, i2h, rr);
+                    const float *Y = stage + slot(4) * FPL;
+                    int64_t z = zin0 + q;
+                    z += z < 0 ? g.T[2] : (z >= g.T[2] ? -g.T[2] : 0);
+                    const int64_t off = off_xy + z * g.PS, dz = img(z, 2) * g.PS;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const float2 v = P::fma(c1, rr[f], P::ld(Y + f * PLS + e));
+                        float *b = static_cast<float *>(out.p[slab_gid<MASK>(f)]) + off;
+                        auto put = [&](float *q2) {
+                            if (ox0 && ox1) P::st(q2, v);
+                            else if (ox0) q2[0] = v.x;
+                            else q2[1] = v.y;
+                        };
+                        put(b);
+                        if (dy) put(b + dy);
+                        if (dz) {
+                            put(b + dz);
+                            if (dy) put(b + dy + dz);
+                        }
+                        if (ox0 && dx0) {
+                            b[dx0] = v.x;
+                            if (dy) b[dx0 + dy] = v.x;
                             if (dz) {
-                                put(b + dz);
-                                if (dy) put(b + dy + dz);
+                                b[dx0 + dz] = v.x;
+                                if (dy) b[dx0 + dy + dz] = v.x;
                             }
-                            if (ox0 && dx0) {
-                                b[dx0] = v.x;
-                                if (dy) b[dx0 + dy] = v.x;
-                                if (dz) {
-                                    b[dx0 + dz] = v.x;
-                                    if (dy) b[dx0 + dy + dz] = v.x;
-                                }
-                            }
-                            if (ox1 && dx1) {
-                                b[1 + dx1] = v.y;
-                                if (dy) b[1 + dx1 + dy] = v.y;
-                                if (dz) {
-                                    b[1 + dx1 + dz] = v.y;
-                                    if (dy) b[1 + dx1 + dy + dz] = v.y;
-                                }
+                        }
+                        if (ox1 && dx1) {
+                            b[1 + dx1] = v.y;
+                            if (dy) b[1 + dx1 + dy] = v.y;
+                            if (dz) {
+                                b[1 + dx1 + dz] = v.y;
+                                if (dy) b[1 + dx1 + dy + dz] = v.y;
                             }
                         }
                     }
                 }
-            }
-            ok = __syncthreads_and(ok);
-            if (!ok) {
-                pfail = p;
-                break;
-            }
-            // input plane p-4 was last read in this iteration: refill its slot
-            if (p < nin && tid == 0 && p >= 4 && p - 4 + S < nin) {
-                fence_proxy_async();
-                const int st = slot(4);
-                slab_issue<MASK, WALL>(stage + st * FPL, maps, bx, by, zin0 + p - 4 + S, g, &bars[st]);
+                // x and y neighbours for the next iteration: levels 4, 3, 2 of planes p-1, p-2, p-3
+                if (DEFER && (STEADY || p >= 2)) store_level(0, p - 1, z4r[(PH + 2) % 3]);
+                if (DEFER && (STEADY || p >= 4)) store_level(1, p - 2, z3r[(PH + 1) % 3]);
+                if (DEFER && (STEADY || p >= 6)) store_level(2, p - 3, z2r[PH]);
             }
         }
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            pfail = p;
+            return false;
+        }
+        // input plane p-4 was last read in this iteration: refill its slot
+        if (p < nin && tid == 0 && p >= 4 && p - 4 + S < nin) {
+            fence_proxy_async();
+            const int st = slot(4);
+            slab_issue<MASK, WALL>(stage + st * FPL, maps, bx, by, zin0 + p - 4 + S, g, &bars[st]);
+        }
+        return true;
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using Fs = std::false_type;
+    using Ts = std::true_type;
+    if constexpr (SH::NAX <= 1) {
+        int p0 = 0;
+        for (; p0 < 9 && p0 < nin; p0 += 3)   // start-up: planes 0 .. 8
+            if (!iter(p0, I0{}, Fs{}) || !iter(p0 + 1, I1{}, Fs{}) || !iter(p0 + 2, I2{}, Fs{})) break;
+        if (ok)
+            for (; p0 < nin; p0 += 3)
+                if (!iter(p0, I0{}, Ts{}) || !iter(p0 + 1, I1{}, Ts{}) || !iter(p0 + 2, I2{}, Ts{})) break;
+    } else {   // the multi-axis classes keep one guarded body (two copies spill)
+        for (int p0 = 0; p0 < nin; p0 += 3)
+            if (!iter(p0, I0{}, Fs{}) || !iter(p0 + 1, I1{}, Fs{}) || !iter(p0 + 2, I2{}, Fs{})) break;
     }
     if (!ok && tid == 0)   // let the copies in flight land (planes pfail .. pfail + S - 1 at most)
         for (int q = pfail; q < nin && q < pfail + S; ++q)
