@@ -340,6 +340,7 @@ constexpr int kLayer2BandRows = 32;  // most output rows of one item of the y ba
 constexpr int kLayer2SlabRows = 24;  // most output rows of one item of an x slab
 constexpr int kLayer2BandRowsTB = 32;  // the same for the frames of two-step blocks
 constexpr int kLayer2SlabRowsTB = 24;
+constexpr int kLayer2MinOffRows = 8;   // shorter inactive row runs next to active rows join them
 int layer2d_grid(int prec, int ntiles, int sm_count);   // CTAs of one layer launch (warps loop over items)
 int layer2d_box_rows();               // rows of the layer kernel's TMA box
 int layer2d_box_cols(int prec);       // columns of the layer kernel's TMA box (one strip)

@@ -459,28 +459,67 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
         // one (halo 2); the first column of a strip's box is a multiple of 4 (TMA alignment)
         const int COLS = layer2d_box_cols(c->prec);
         const std::vector<uint8_t> act0 = axis_activity(c, 0), act1 = axis_activity(c, 1);
+        // Row runs of one class: a short inactive run next to an active one joins it (an
+        // item over active rows is exact anywhere; a few inactive rows of their own would
+        // cost a whole item's start-up for little output).
+        auto row_runs = [&](int64_t ylo, int64_t yhi) {
+            std::vector<ActRun> r = activity_runs(act1, ylo, yhi), m;
+            for (size_t i = 0; i < r.size(); ++i) {
+                ActRun q = r[i];
+                const bool next_on = (i > 0 && r[i - 1].on) || (i + 1 < r.size() && r[i + 1].on);
+                if (!q.on && next_on && q.hi - q.lo + 1 < kLayer2MinOffRows) q.on = true;
+                if (!m.empty() && m.back().on == q.on) m.back().hi = q.hi;
+                else m.push_back(q);
+            }
+            return m;
+        };
+        // Strips over the columns xlo..xhi, greedily from the left: an inactive-class strip
+        // (28 outputs) where the inactive run from its first column reaches at least as far
+        // as an active-class strip (24 outputs) would; otherwise an active-class strip, which
+        // may run on into inactive columns (exact there too).
+        struct Strip {
+            int64_t x0, lo, hi;
+            bool on;
+        };
+        auto strips = [&](int64_t xlo, int64_t xhi) {
+            std::vector<Strip> s;
+            const std::vector<ActRun> runs = activity_runs(act0, xlo, xhi);
+            size_t k = 0;
+            for (int64_t x = xlo; x <= xhi;) {
+                while (runs[k].hi < x) ++k;
+                const int64_t x0on = x - ((((x - 4) % 4) + 4) % 4);
+                const int64_t endon = std::min<int64_t>(x0on + (COLS - 8) - 1, xhi);
+                Strip st{x0on, x, endon, true};
+                if (!runs[k].on) {
+                    const int64_t x0off = x - ((((x - 2) % 4) + 4) % 4);
+                    const int64_t endoff = std::min<int64_t>(x0off + (COLS - 4) - 1, runs[k].hi);
+                    if (endoff >= endon) st = Strip{x0off, x, endoff, false};
+                }
+                s.push_back(st);
+                x = st.hi + 1;
+            }
+            return s;
+        };
         auto add = [&](int64_t xlo, int64_t xhi, int64_t ylo, int64_t yhi, int64_t maxrows) {
             if (xhi < xlo || yhi < ylo) return;
-            for (const ActRun &ry : activity_runs(act1, ylo, yhi))
-                for (const ActRun &rx : activity_runs(act0, xlo, xhi)) {
-                    const int HX = rx.on ? 4 : 2, OUT = COLS - 2 * HX;
-                    const int64_t H = ry.hi - ry.lo + 1;
-                    const int64_t nseg = (H + maxrows - 1) / maxrows;
-                    int64_t y0 = ry.lo;
-                    for (int64_t sgi = 0; sgi < nseg; ++sgi) {
-                        const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
-                        const int64_t first = rx.lo - ((((rx.lo - HX) % 4) + 4) % 4);
-                        for (int64_t x0 = first; x0 <= rx.hi; x0 += OUT) {
-                            LayerTile L{};
-                            L.x0 = int32_t(x0); L.y0 = int32_t(y0); L.z0 = 0;
-                            L.xlo = int32_t(rx.lo); L.xhi = int32_t(rx.hi);
-                            L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
-                            L.flags = (rx.on ? 1 : 0) | (ry.on ? 2 : 0);
-                            t.push_back(L);
-                        }
-                        y0 += len;
+            const std::vector<Strip> sx = strips(xlo, xhi);
+            for (const ActRun &ry : row_runs(ylo, yhi)) {
+                const int64_t H = ry.hi - ry.lo + 1;
+                const int64_t nseg = (H + maxrows - 1) / maxrows;
+                int64_t y0 = ry.lo;
+                for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+                    const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
+                    for (const Strip &st : sx) {
+                        LayerTile L{};
+                        L.x0 = int32_t(st.x0); L.y0 = int32_t(y0); L.z0 = 0;
+                        L.xlo = int32_t(st.lo); L.xhi = int32_t(st.hi);
+                        L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
+                        L.flags = (st.on ? 1 : 0) | (ry.on ? 2 : 0);
+                        t.push_back(L);
                     }
+                    y0 += len;
                 }
+            }
         };
         const int64_t T0 = c->T[0], T1 = c->T[1];
         if (range_empty(ir[0]) || range_empty(ir[1])) {
