@@ -41,8 +41,10 @@ template <int MASK> struct Slab {
     static constexpr int RX = AX ? 36 : (AY && NAX == 1 ? 28 : 32);
     // rows: as many as the shared memory of 13 planes per field (NF = 4: up to ~1100
     // columns, NF = 6: ~740, NF = 8: ~550) and the registers of one CTA per SM allow
-    // without spilling; the y-active one-axis class covers a 25-row layer slab with one tile
-    static constexpr int RY = NF == 2 ? 32 : NF == 4 ? (AY ? 33 : (AX ? 26 : 32)) : NF == 6 ? (AX ? 18 : 20) : 14;
+    // without spilling; the y-active one-axis class covers a 25-row layer slab with one tile;
+    // the x-active one takes 21 rows (378 threads, 152 registers) rather than 26 (468
+    // threads, 128 registers with spills): 17 % more halo rows, but no spills
+    static constexpr int RY = NF == 2 ? 32 : NF == 4 ? (AY ? 33 : (AX ? 21 : 32)) : NF == 6 ? (AX ? 18 : 20) : 14;
     static constexpr int TPR = RX / 2;                    // threads per region row
     static constexpr int NT = TPR * RY;                   // threads
     // registers per thread of one resident CTA: the warps spread over the SM's four
@@ -281,11 +283,12 @@ __global__ void __maxnreg__(Slab<MASK>::MAXREG)
     int pfail = nin;   // first plane whose wait gave up
     // One iteration per input plane p.  Every shared-memory read of an iteration sees planes
     // written in earlier iterations (the level planes alternate by plane parity), so in the
-    // one-axis classes the stores of levels 4, 3 and 2 are made after all four levels are
-    // formed: the loads of a later level then need not wait behind the stores of an earlier
-    // one, and their STEADY iterations (p >= 8: every level has its planes) run as one block
-    // without the start-up guards.  The multi-axis classes keep one guarded body that
-    // stores each level at once (a second body, or values held to the end, spill there).
+    // x- and z-active classes (and the class without damping) the stores of levels 4, 3 and
+    // 2 are made after all four levels are formed: the loads of a later level then need not
+    // wait behind the stores of an earlier one, and their STEADY iterations (p >= 8: every
+    // level has its planes) run as one block without the start-up guards.  The other
+    // classes keep one guarded body that stores each level at once (a second body, or values
+    // held to the end, spill there).
     // Level planes: [3 levels: 4, 3, 2][2 plane parities][NF][PLS].
     auto store_level = [&](int lv, int q, const float2 *v) {
         float *zo = lvl + ((lv * 2 + (q & 1)) * NF) * PLS;
@@ -295,7 +298,7 @@ __global__ void __maxnreg__(Slab<MASK>::MAXREG)
     auto iter = [&](const int p, auto phc, auto stc) -> bool {
         constexpr int PH = decltype(phc)::value;   // p mod 3: position in the register rings
         constexpr bool STEADY = decltype(stc)::value;
-        constexpr bool DEFER = SH::NAX <= 1;        // multi-axis classes store each level at once
+        constexpr bool DEFER = SH::NAX <= 1 && !SH::AY;   // the other classes store each level at once
         const int sp = p % S;   // slot of input plane p; plane p - k sits in slot (sp - k) mod S
         auto slot = [&](int k) { return sp - k < 0 ? sp - k + S : sp - k; };
         if (p < nin) {
@@ -448,14 +451,14 @@ __global__ void __maxnreg__(Slab<MASK>::MAXREG)
     using I2 = std::integral_constant<int, 2>;
     using Fs = std::false_type;
     using Ts = std::true_type;
-    if constexpr (SH::NAX <= 1) {
+    if constexpr (SH::NAX <= 1 && !SH::AY) {
         int p0 = 0;
         for (; p0 < 9 && p0 < nin; p0 += 3)   // start-up: planes 0 .. 8
             if (!iter(p0, I0{}, Fs{}) || !iter(p0 + 1, I1{}, Fs{}) || !iter(p0 + 2, I2{}, Fs{})) break;
         if (ok)
             for (; p0 < nin; p0 += 3)
                 if (!iter(p0, I0{}, Ts{}) || !iter(p0 + 1, I1{}, Ts{}) || !iter(p0 + 2, I2{}, Ts{})) break;
-    } else {   // the multi-axis classes keep one guarded body (two copies spill)
+    } else {   // the y-active and multi-axis classes keep one guarded body (two copies spill)
         for (int p0 = 0; p0 < nin; p0 += 3)
             if (!iter(p0, I0{}, Fs{}) || !iter(p0 + 1, I1{}, Fs{}) || !iter(p0 + 2, I2{}, Fs{})) break;
     }

@@ -18,6 +18,8 @@
 //    y' = y + dt A (y + dt/2 A (y + dt/3 A (y + dt/4 A y)))
 //    with the full operator (Laplacian + damping terms + Phi/Psi recurrences), four
 //    applications of A on a shrinking shared-memory region (halo 4).
+#include <utility>
+
 #include "common.cuh"
 
 namespace pml {
@@ -553,6 +555,31 @@ template <> struct LV<float, 2> {
     static __device__ __forceinline__ V ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 };
 
+// Whether apply_A2 reads field f at the x neighbour d (1: x-, 2: x+): only those
+// neighbours are fetched by shuffles.  Forward: U on both sides, Phi_x on the left, Psi_x
+// on the right; transposed: V, Phi_x and Psi_x on both sides.
+template <bool ADJ, int MASK> __device__ __forceinline__ constexpr bool need_x2(int f, int d)
+{
+    if (f == 0) return !ADJ;
+    if (f == 1) return ADJ;
+    if (Fields2<MASK>::axis((f - 2) >> 1) != 0) return false;
+    if (ADJ) return true;
+    return ((f - 2) & 1) == 0 ? d == 1 : d == 2;
+}
+template <typename O, bool ADJ, int MASK, int F, typename V>
+__device__ __forceinline__ void x_neighbour(const V *c, V *xm, V *xp)
+{
+    if constexpr (need_x2<ADJ, MASK>(F, 1)) xm[F] = O::left(c[F]);
+    else xm[F] = c[F];
+    if constexpr (need_x2<ADJ, MASK>(F, 2)) xp[F] = O::right(c[F]);
+    else xp[F] = c[F];
+}
+template <typename O, bool ADJ, int MASK, typename V, int... F>
+__device__ __forceinline__ void x_neighbours(const V *c, V *xm, V *xp, std::integer_sequence<int, F...>)
+{
+    (x_neighbour<O, ADJ, MASK, F>(c, xm, xp), ...);
+}
+
 template <typename V> struct Sig2 {
     V si[2], sm[2];   // sigma_a[i_a], sigma_a[i_a - 1]
 };
@@ -786,11 +813,8 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
         {
             V cen[NF], xm[NF], xp[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                cen[f] = O::ld(y1 + f * FS);
-                xm[f] = O::left(cen[f]);
-                xp[f] = O::right(cen[f]);
-            }
+            for (int f = 0; f < NF; ++f) cen[f] = O::ld(y1 + f * FS);
+            x_neighbours<O, ADJ, MASK>(cen, xm, xp, std::make_integer_sequence<int, NF>{});
             auto N = [&](int f, int d) -> V {
                 switch (d) {
                 case 0: return cen[f];
@@ -807,11 +831,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
         // level 3 at row p-3 (z4 rows p-4, p-3, p-2)
         {
             V xm[NF], xp[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                xm[f] = O::left(z4[1][f]);
-                xp[f] = O::right(z4[1][f]);
-            }
+            x_neighbours<O, ADJ, MASK>(z4[1], xm, xp, std::make_integer_sequence<int, NF>{});
             auto N = [&](int f, int d) -> V {
                 switch (d) {
                 case 0: return z4[1][f];
@@ -828,11 +848,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
         // level 2 at row p-5 (z3 rows p-6, p-5, p-4)
         {
             V xm[NF], xp[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                xm[f] = O::left(z3[1][f]);
-                xp[f] = O::right(z3[1][f]);
-            }
+            x_neighbours<O, ADJ, MASK>(z3[1], xm, xp, std::make_integer_sequence<int, NF>{});
             auto N = [&](int f, int d) -> V {
                 switch (d) {
                 case 0: return z3[1][f];
@@ -849,11 +865,7 @@ __device__ __forceinline__ bool layer2d_item(const Maps6 &maps, const Out6 &out,
         // level 1 at row p-7 (z2 rows p-8, p-7, p-6): output row p-11 of the item
         {
             V xm[NF], xp[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                xm[f] = O::left(z2[1][f]);
-                xp[f] = O::right(z2[1][f]);
-            }
+            x_neighbours<O, ADJ, MASK>(z2[1], xm, xp, std::make_integer_sequence<int, NF>{});
             auto N = [&](int f, int d) -> V {
                 switch (d) {
                 case 0: return z2[1][f];
