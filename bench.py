@@ -472,7 +472,7 @@ def run_ours(args, ws, rank, local):
               "value": pts3 * K3 * ws / (ms3 / 1e3) / 1e9, "unit": UNIT, "steps": K3, "ms_per_step": ms3 / K3,
               "layer_variant": {0: "z-streaming tile kernel", 1: "level passes", 2: "slab tiles"}.get(var3, var3),
               "autotune_ms_per_step": tune3,
-              "roofline": {"bound": "hbm", "kernel": "k_interior3d<float>", "achieved": ach3, "peak": hbm_peak,
+              "roofline": {"bound": "hbm", "kernel": "k_interior3d_rows<float> (FP32 layer-free kernel)", "achieved": ach3, "peak": hbm_peak,
                            "unit": "GB/s", "frac": ach3 / hbm_peak, "avg_launch_ms": t_int3 * 1e3,
                            "bytes_per_launch": int3 * 16},
               "kernel_ms_per_step": {"interior": m3[0] / max(n3[0], 1), "layer": m3[1] / max(n3[0], 1),
