@@ -1253,8 +1253,9 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
     }
     // layer tiles
     {
-        std::vector<LayerTile> tf = build_tiles_2d(c, c->ir, c->class_off),
-                               ta = build_tiles_2d(c, c->ir_adj, c->class_off_adj);
+        const int64_t slab1 = c->g.wall ? kLayer2SlabRowsWall : kLayer2SlabRows;
+        std::vector<LayerTile> tf = build_tiles_2d(c, c->ir, c->class_off, kLayer2BandRows, slab1),
+                               ta = build_tiles_2d(c, c->ir_adj, c->class_off_adj, kLayer2BandRows, slab1);
         if (tf.size() > plan.max_tiles || ta.size() > plan.max_tiles) {
             fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
             return bail(PML_ENOMEM);
@@ -1315,8 +1316,9 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
         // interior kernel, so a pass lasts as long as its longest item; about one short item
         // per warp of a full launch
         int dummy[9];
-        std::vector<LayerTile> t1 = build_tiles_2d(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
-                               t2 = build_tiles_2d(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+        const int64_t slab2 = c->g.wall ? kLayer2SlabRowsWall : kLayer2SlabRowsTB;
+        std::vector<LayerTile> t1 = build_tiles_2d(c, r6, dummy, kLayer2BandRowsTB, slab2),
+                               t2 = build_tiles_2d(c, r2, dummy, kLayer2BandRowsTB, slab2);
         if (t1.size() > plan.max_tiles || t2.size() > plan.max_tiles) {
             fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
             return bail(PML_ENOMEM);
@@ -1333,8 +1335,8 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width, 
                 r6[a] = shrink_run(c->ir_adj[a], c->T[a], 6);
                 r2[a] = c->ir_tb_adj[a] = shrink_run(c->ir_adj[a], c->T[a], 2);
             }
-            std::vector<LayerTile> a1 = build_tiles_2d(c, r6, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB),
-                                   a2 = build_tiles_2d(c, r2, dummy, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+            std::vector<LayerTile> a1 = build_tiles_2d(c, r6, dummy, kLayer2BandRowsTB, slab2),
+                                   a2 = build_tiles_2d(c, r2, dummy, kLayer2BandRowsTB, slab2);
             if (a1.size() > plan.max_tiles || a2.size() > plan.max_tiles) {
                 fail(c, PML_ENOMEM, "layer tile table exceeds its bound");
                 return bail(PML_ENOMEM);
@@ -2317,7 +2319,8 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
     std::vector<int> tile_grid;
     for (int i = 0; i < count; ++i) {
         int co[9];
-        std::vector<LayerTile> t = build_tiles(b->ctx[size_t(i)], b->ctx[size_t(i)]->ir, co);
+        std::vector<LayerTile> t =
+            build_tiles(b->ctx[size_t(i)], b->ctx[size_t(i)]->ir, co, kLayer2BandRowsBatch, kLayer2SlabRowsBatch);
         tiles.insert(tiles.end(), t.begin(), t.end());
         tile_grid.insert(tile_grid.end(), t.size(), i);
     }
@@ -2347,8 +2350,8 @@ pml_status pml_batch_create(int count, pml_ctx *const *ctxs, pml_batch **out)
             Range r6[3];
             for (int a = 0; a < 3; ++a) r6[a] = shrink_run(c->ir[a], c->T[a], 6);
             int co[9];
-            std::vector<LayerTile> t1 = build_tiles(c, r6, co, kLayer2BandRowsTB, kLayer2SlabRowsTB),
-                                   t2 = build_tiles(c, c->ir_tb, co, kLayer2BandRowsTB, kLayer2SlabRowsTB);
+            std::vector<LayerTile> t1 = build_tiles(c, r6, co, kLayer2BandRowsBatch, kLayer2SlabRowsBatch),
+                                   t2 = build_tiles(c, c->ir_tb, co, kLayer2BandRowsBatch, kLayer2SlabRowsBatch);
             tiles1.insert(tiles1.end(), t1.begin(), t1.end());
             grid1.insert(grid1.end(), t1.size(), i);
             tiles2.insert(tiles2.end(), t2.begin(), t2.end());
