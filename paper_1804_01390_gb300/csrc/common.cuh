@@ -343,7 +343,7 @@ constexpr int kLayer2SlabRowsTB = 24;
 constexpr int kLayer2MinOffRows = 8;   // shorter inactive row runs next to active rows join them
 constexpr int kLayer2SlabRowsWall = 32;    // x-slab items of a wall-backed box (two short bands, no seam)
 constexpr int kLayer2BandRowsBatch = 40;   // items of a batch (many frames, many items per warp)
-constexpr int kLayer2SlabRowsBatch = 32;
+constexpr int kLayer2SlabRowsBatch = 40;
 int layer2d_grid(int prec, int ntiles, int sm_count);   // CTAs of one layer launch (warps loop over items)
 int layer2d_box_rows();               // rows of the layer kernel's TMA box
 int layer2d_box_cols(int prec);       // columns of the layer kernel's TMA box (one strip)
