@@ -505,19 +505,26 @@ std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_
             const std::vector<Strip> sx = strips(xlo, xhi);
             for (const ActRun &ry : row_runs(ylo, yhi)) {
                 const int64_t H = ry.hi - ry.lo + 1;
-                const int64_t nseg = (H + maxrows - 1) / maxrows;
-                int64_t y0 = ry.lo;
-                for (int64_t sgi = 0; sgi < nseg; ++sgi) {
-                    const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
-                    for (const Strip &st : sx) {
-                        LayerTile L{};
-                        L.x0 = int32_t(st.x0); L.y0 = int32_t(y0); L.z0 = 0;
-                        L.xlo = int32_t(st.lo); L.xhi = int32_t(st.hi);
-                        L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
-                        L.flags = (st.on ? 1 : 0) | (ry.on ? 2 : 0);
-                        t.push_back(L);
+                // strips active along both axes (the corners: six fields and both damping
+                // terms, about 1.5 times the work per row) get proportionally shorter runs,
+                // so that they do not outlast the other items of a launch
+                for (int corner = 0; corner < 2; ++corner) {
+                    const int64_t mr = corner ? std::max<int64_t>(8, maxrows * 2 / 5) : maxrows;
+                    const int64_t nseg = (H + mr - 1) / mr;
+                    int64_t y0 = ry.lo;
+                    for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+                        const int64_t len = H / nseg + (sgi < H % nseg ? 1 : 0);
+                        for (const Strip &st : sx) {
+                            if ((st.on && ry.on) != (corner != 0)) continue;
+                            LayerTile L{};
+                            L.x0 = int32_t(st.x0); L.y0 = int32_t(y0); L.z0 = 0;
+                            L.xlo = int32_t(st.lo); L.xhi = int32_t(st.hi);
+                            L.ylo = int32_t(y0); L.yhi = int32_t(y0 + len - 1);
+                            L.flags = (st.on ? 1 : 0) | (ry.on ? 2 : 0);
+                            t.push_back(L);
+                        }
+                        y0 += len;
                     }
-                    y0 += len;
                 }
             }
         };
