@@ -441,13 +441,14 @@ std::vector<ActRun> activity_runs(const std::vector<uint8_t> &act, int64_t lo, i
 
 // Layer tiles of the frame, sorted by flags (bit a: aux fields of axis a reach the tile's
 // footprint) so that each class runs with its own field count.
-//  2D: strips of 32 columns streamed down the rows by one warp, cut from stretches of
-//      constant activity along x and y (see axis_activity): 24 outputs with a halo of 4
-//      where x is active, 28 with a halo of 2 where it is not.  The rows outside ir[1]
-//      form one band across the periodic seam of y (unwrapped rows ir[1].hi + 1 ..
-//      T1 + ir[1].lo - 1), cut into near-equal runs of at most kLayer2BandRows rows over the
-//      full width; the columns outside ir[0] (rows ir[1]) are cut into runs of at most
-//      kLayer2SlabRows rows.
+//  2D: strips of 32 columns streamed down the rows by one warp, laid over the stretches
+//      of constant activity along x (see axis_activity): 24 outputs with a halo of 4 where
+//      x is active, 28 with a halo of 2 where it is not (an active-x strip may run on into
+//      inactive columns).  The rows outside ir[1] form one band across the periodic seam
+//      of y (unwrapped rows ir[1].hi + 1 .. T1 + ir[1].lo - 1), cut into near-equal runs of
+//      at most band_rows rows over the full width; the columns outside ir[0] (rows ir[1])
+//      are cut into runs of at most slab_rows rows; strips active along both axes take
+//      2/5 of those lengths.  With a wall there is no seam: two bands.
 //  3D: (x, y) column tiles streamed over z segments of at most kLayer3LZ planes (zlo..zhi,
 //      unwrapped).
 std::vector<LayerTile> build_tiles(const pml_ctx *c, const Range *ir, int class_off[9],
