@@ -221,6 +221,30 @@ pml_status pml_query_layout(const pml_ctx *ctx, int axis, uint8_t *phi_active,
 pml_status pml_query_sigma(const pml_ctx *ctx, int axis, double *sigma);
 
 /*
+ * Layer work items of a box, planned on the host without a GPU or a context.  The paper
+ * has no counterpart: how the layer frame (every vertex outside the layer-free run of
+ * pml_query_layout) is cut into work items is this library's choice; this query lets a
+ * caller (or a test) inspect the items the layer kernels of such a box would take.
+ *   grid, pml_width, profile, precision, flags  as for pml_create
+ *   sm_count   streaming multiprocessors the plan assumes (2D frames that give fewer items
+ *              than 8 per SM get proportionally shorter ones), >= 1
+ *   which      0: the frame of one step (2D); 1 / 2: the first / second layer pass of a
+ *              two-step block, the frames of the run shrunk by 6 / by 2 (2D FP32);
+ *              3: the slab tiles of the 3D frame (3D FP32); 4: the items of this box in
+ *              a batch (2D FP32)
+ *   out        NULL or a host int32 array [cap][10]: x0, y0, z0 (region origin), xlo, xhi,
+ *              ylo, yhi, zlo, zhi (inclusive output range; y (2D) and z (3D) ranges of
+ *              the band across the periodic seam run past T - 1 and wrap), flags (bit a:
+ *              the aux fields of axis a are active within the item's reach); the first
+ *              min(cap, count) items are written
+ *   count      number of items of the set
+ * PML_EINVAL for invalid arguments or an item set that does not belong to the box.
+ */
+pml_status pml_plan_layer_items(const pml_grid *grid, int pml_width, const pml_sigma_profile *profile,
+                                int precision, int flags, int sm_count, int which, int32_t *out, int64_t cap,
+                                int64_t *count);
+
+/*
  * Discrete adjoint of the RK4 scheme (the transpose of one step is P(dt A)^T =
  * P(dt A^T), A^T written out from the entries of Eq. 3).  Requires PML_FLAG_ADJOINT.
  *

@@ -47,7 +47,7 @@ EXPORTED = (
     "pml_workspace_bytes", "pml_create", "pml_set_initial", "pml_set_sources",
     "pml_set_receivers", "pml_step", "pml_read_field", "pml_norms", "pml_get_step", "pml_sync",
     "pml_set_check_interval", "pml_set_wait_limit",
-    "pml_query_layout", "pml_query_sigma", "pml_adjoint_reset", "pml_adjoint_step",
+    "pml_query_layout", "pml_query_sigma", "pml_plan_layer_items", "pml_adjoint_reset", "pml_adjoint_step",
     "pml_adjoint_read_field", "pml_sigma_gradient", "pml_sigma_gradient_bytes", "pml_state_bytes", "pml_save_state", "pml_load_state",
     "pml_get_variant", "pml_set_variant", "pml_get_time_block", "pml_autotune",
     "pml_profile_enable", "pml_profile_read", "pml_norms_dense_static",
@@ -106,6 +106,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pml_set_check_interval": [P, i64],
         "pml_set_wait_limit": [P, ctypes.c_uint64],
         "pml_query_layout": [P, ctypes.c_int, P, P, P],
+        "pml_plan_layer_items": [ctypes.POINTER(pml_grid), ctypes.c_int, ctypes.POINTER(pml_sigma_profile),
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_int64)],
         "pml_query_sigma": [P, ctypes.c_int, P],
         "pml_adjoint_reset": [P],
         "pml_adjoint_step": [P, i64, P, P, P],
@@ -225,6 +228,25 @@ def pml_set_check_interval(ctx, steps):
 
 def pml_set_wait_limit(ctx, ns):
     _check(load().pml_set_wait_limit(ctx, int(ns)), ctx)
+
+
+def pml_plan_layer_items(ndim, n, pml_width, kind, sigma_max, order, user, precision, flags, sm_count, which):
+    """Layer work items of a box (host only, no context): an int32 array [count][10] of
+    x0, y0, z0, xlo, xhi, ylo, yhi, zlo, zhi, flags.  user: host pointers (int) or None."""
+    import numpy as np
+    g = pml_grid(ndim, (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))))
+    u = [None, None, None]
+    if user is not None:
+        for a, p in enumerate(user):
+            u[a] = p
+    prof = pml_sigma_profile(int(kind), float(sigma_max), float(order), (ctypes.c_void_p * 3)(*u))
+    count = ctypes.c_int64(0)
+    args = (ctypes.byref(g), int(pml_width), ctypes.byref(prof), int(precision), int(flags), int(sm_count),
+            int(which))
+    _check(load().pml_plan_layer_items(*args, None, 0, ctypes.byref(count)))
+    out = np.zeros((max(count.value, 1), 10), dtype=np.int32)
+    _check(load().pml_plan_layer_items(*args, out.ctypes.data, int(count.value), ctypes.byref(count)))
+    return out[:count.value]
 
 
 def pml_query_layout(ctx, axis, phi, psi, interior):

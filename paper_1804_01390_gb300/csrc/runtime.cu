@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -1151,6 +1152,58 @@ pml_status pml_workspace_bytes(const pml_grid *grid, int pml_width, int precisio
     if (!bytes) return fail(nullptr, PML_EINVAL, "bytes is NULL");
     if (!make_plan(grid, pml_width, precision, flags, &p, &why)) return fail(nullptr, PML_EINVAL, "%s", why.c_str());
     *bytes = p.total;
+    return PML_OK;
+}
+
+pml_status pml_plan_layer_items(const pml_grid *grid, int pml_width, const pml_sigma_profile *profile,
+                                int precision, int flags, int sm_count, int which, int32_t *out, int64_t cap,
+                                int64_t *count)
+{
+    if (!count) return fail(nullptr, PML_EINVAL, "count is NULL");
+    *count = 0;
+    Plan plan;
+    std::string why;
+    if (!make_plan(grid, pml_width, precision, flags, &plan, &why)) return fail(nullptr, PML_EINVAL, "%s", why.c_str());
+    if (sm_count < 1) return fail(nullptr, PML_EINVAL, "sm_count must be >= 1");
+    if (which < 0 || which > 4) return fail(nullptr, PML_EINVAL, "which must be 0..4");
+    if ((which == 1 || which == 2 || which == 4) && !(plan.nd == 2 && precision == 32))
+        return fail(nullptr, PML_EINVAL, "item sets 1, 2 and 4 belong to 2D FP32 boxes");
+    if (which == 3 && !(plan.nd == 3 && precision == 32))
+        return fail(nullptr, PML_EINVAL, "item set 3 belongs to 3D FP32 boxes");
+    if (which == 0 && plan.nd != 2) return fail(nullptr, PML_EINVAL, "item set 0 belongs to 2D boxes");
+    if (cap < 0 || (cap > 0 && !out)) return fail(nullptr, PML_EINVAL, "out is NULL or cap < 0");
+    // a host-side context: the damping, its supports and the layer-free runs, no device state
+    std::unique_ptr<pml_ctx> c(new pml_ctx());
+    c->plan = plan;
+    c->nd = plan.nd; c->prec = precision; c->esz = plan.esz; c->nf = plan.nf; c->flags = flags;
+    c->w = pml_width; c->g = plan.g; c->sm_count = sm_count;
+    for (int a = 0; a < 3; ++a) { c->N[a] = a < c->nd ? grid->n[a] : 1; c->T[a] = plan.T[a]; }
+    pml_status s = build_sigma(c.get(), profile);
+    if (s != PML_OK) return s;
+    build_layout(c.get());
+    int co[9];
+    std::vector<LayerTile> t;
+    Range r[3];
+    switch (which) {
+    case 0: {
+        const int64_t slab1 = c->g.wall ? kLayer2SlabRowsWall : kLayer2SlabRows;
+        t = build_tiles_2d(c.get(), c->ir, co, kLayer2BandRows, slab1);
+        break;
+    }
+    case 1:
+    case 2:
+        for (int a = 0; a < 3; ++a) r[a] = shrink_run(c->ir[a], c->T[a], which == 1 ? 6 : 2);
+        t = build_tiles_2d(c.get(), r, co, kLayer2BandRowsTB, c->g.wall ? kLayer2SlabRowsWall : kLayer2SlabRowsTB);
+        break;
+    case 3: t = build_slab_tiles(c.get(), c->ir, co); break;
+    default: t = build_tiles(c.get(), c->ir, co, kLayer2BandRowsBatch, kLayer2SlabRowsBatch); break;
+    }
+    *count = int64_t(t.size());
+    for (int64_t i = 0; i < cap && i < *count; ++i) {
+        const LayerTile &L = t[size_t(i)];
+        const int32_t v[10] = {L.x0, L.y0, L.z0, L.xlo, L.xhi, L.ylo, L.yhi, L.zlo, L.zhi, L.flags};
+        for (int k = 0; k < 10; ++k) out[10 * i + k] = v[k];
+    }
     return PML_OK;
 }
 
