@@ -231,7 +231,7 @@ pml_status pml_query_sigma(const pml_ctx *ctx, int axis, double *sigma);
  *   which      0: the frame of one step (2D); 1 / 2: the first / second layer pass of a
  *              two-step block, the frames of the run shrunk by 6 / by 2 (2D FP32);
  *              3: the slab tiles of the 3D frame (3D FP32); 4: the items of this box in
- *              a batch (2D FP32)
+ *              a batch's one-step layer launch (2D FP32)
  *   out        NULL or a host int32 array [cap][10]: x0, y0, z0 (region origin), xlo, xhi,
  *              ylo, yhi, zlo, zhi (inclusive output range; y (2D) and z (3D) ranges of
  *              the band across the periodic seam run past T - 1 and wrap), flags (bit a:
