@@ -130,7 +130,10 @@ pml_status pml_create(const pml_grid *grid, double h, double dt, int pml_width,
 /*
  * Set the state: U = u0, V = v0 (NULL -> 0), Phi = Psi = 0, step counter = 0
  * (the paper's runs start at rest in the layer, Sec. 1.1.3).  u0 / v0 are dense
- * T-grids of the context's precision.
+ * T-grids of the context's precision (host memory for on_device = 0, else device).
+ * Asynchronous on the context's stream; the clearing of the fields the copies do not fill
+ * runs on a side stream the library creates at the first call, joined back before the
+ * call's last work on the context's stream.
  */
 pml_status pml_set_initial(pml_ctx *ctx, const void *u0, const void *v0, int on_device);
 

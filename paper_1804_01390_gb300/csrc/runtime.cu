@@ -227,6 +227,11 @@ struct pml_ctx {
     // kernel timing (pml_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs
+    // pml_set_initial clears the fields its copies do not fill on a side stream, so that the
+    // clearing overlaps the host-to-device copies (created at the first call; none: serial)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_tried = false;
     std::vector<int> prof_kind;
     size_t prof_n = 0;
     std::string err;
@@ -1575,6 +1580,12 @@ void pml_destroy(pml_ctx *c)
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
@@ -1584,7 +1595,40 @@ pml_status pml_set_initial(pml_ctx *c, const void *u0, const void *v0, int on_de
 {
     if (!c) return fail(nullptr, PML_EINVAL, "ctx is NULL");
     const size_t fb = align_up(size_t(c->g.elems) * c->esz, kAlign);
-    PML_CU(c, cudaMemsetAsync(c->ws, 0, fb * size_t(2 * c->nf), c->st), "clear state");
+    // The copies below fill every value of U (V) of the new state when given and the box is
+    // periodic (the ghost ring is then filled from the copy); everything else of both
+    // ping-pong states is cleared, on a side stream that runs beside the copies.
+    const bool fill_u = u0 && !c->g.wall, fill_v = v0 && !c->g.wall;
+    if ((fill_u || fill_v) && !c->side_tried) {
+        c->side_tried = true;
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (c->side) cudaStreamDestroy(c->side);
+            if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+            if (c->ev_join) cudaEventDestroy(c->ev_join);
+            c->side = nullptr;
+            c->ev_fork = c->ev_join = nullptr;
+        }
+    }
+    const bool forked = (fill_u || fill_v) && c->side;
+    if (forked) {   // the side stream starts after all work already queued on the context's stream
+        PML_CU(c, cudaEventRecord(c->ev_fork, c->st), "fork");
+        PML_CU(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+    }
+    cudaStream_t zs = forked ? c->side : c->st;
+    char *s0 = static_cast<char *>(c->fld[0][0]);   // the two states' fields, nf each, contiguous
+    if (fill_u && fill_v) {
+        PML_CU(c, cudaMemsetAsync(s0 + 2 * fb, 0, fb * size_t(2 * c->nf - 2), zs), "clear state");
+    } else if (fill_u) {
+        PML_CU(c, cudaMemsetAsync(s0 + fb, 0, fb * size_t(2 * c->nf - 1), zs), "clear state");
+    } else if (fill_v) {
+        PML_CU(c, cudaMemsetAsync(s0, 0, fb, zs), "clear state");
+        PML_CU(c, cudaMemsetAsync(s0 + 2 * fb, 0, fb * size_t(2 * c->nf - 2), zs), "clear state");
+    } else {
+        PML_CU(c, cudaMemsetAsync(s0, 0, fb * size_t(2 * c->nf), c->st), "clear state");
+    }
     c->cur = 0;
     if (u0) {
         pml_status s = copy_dense(c, c->fld[0][0], u0, on_device != 0, true);
@@ -1593,6 +1637,10 @@ pml_status pml_set_initial(pml_ctx *c, const void *u0, const void *v0, int on_de
     if (v0) {
         pml_status s = copy_dense(c, c->fld[0][1], v0, on_device != 0, true);
         if (s != PML_OK) return s;
+    }
+    if (forked) {   // the context's stream goes on once the clearing is done
+        PML_CU(c, cudaEventRecord(c->ev_join, c->side), "join");
+        PML_CU(c, cudaStreamWaitEvent(c->st, c->ev_join, 0), "join");
     }
     if (!c->g.wall) {   // with a wall the ghost ring stays zero
         PML_CU(c, launch_fill_ghosts(c->prec, c->fld[0][0], c->g, c->st), "ghost fill");
